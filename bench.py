@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Throughput of the fast-bilateral-stereo path on GB300.
+
+A step is one stereo pair through the whole path (cost volume, bilateral
+aggregation of every disparity slice, WTA, Eq. (10) refinement) via the C ABI
+entry point fbs_compute_disparity, with the pair already resident in HBM.
+The workload is the 640x480 RGB pair with D = 64, radius 7 (15x15 window),
+sigma_s = 7, sigma_r = 12, rendered by the seeded synthetic scene generator
+(fractal texture, slanted planes, occlusions).  The metric is aggregated
+taps per second, Gtaps/s = H * W * D * (2 radius + 1)^2 / t, with fps and
+Mde/s (Eq. (13)) beside it.
+
+Timing: W untimed warm-up steps, then exactly K steps between a barrier and a
+device synchronisation on both sides.  L2 is flushed (a 512 MiB write) before
+every step, outside the CUDA-event pair that times the step; ms_per_step is
+the mean of the per-step event times, max over ranks.  With --gpus N (under
+torchrun) every rank runs an independent replica on its own pair: the path
+does not shard, so there is no collective on the data path ("weak" scaling).
+
+--impl reference times the FP64 CPU oracle on the host (bounded row bands of
+the same workload) and prints the same JSON line with "impl": "reference".
+"""
+
+from __future__ import annotations
+
+import argparse
+import datetime as _dt
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FBS aggregated Gtaps/s and fps; plain FP32 vs chosen form at fixed error"
+UNIT = "Gtaps/s"
+DEFAULT_WORKLOAD = "rgb640x480_d64_r7"
+FLUSH_BYTES = 512 << 20
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+GB300_SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--prec", default="f32", choices=["f32"])
+    ap.add_argument("--cost", default="ncc", choices=["ncc", "tad"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
+    return ap.parse_args()
+
+
+def _peaks():
+    src = "measured"
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+    except (OSError, ValueError):
+        p, src = dict(FALLBACK_PEAKS), "fallback"
+    for k, v in FALLBACK_PEAKS.items():
+        p.setdefault(k, v)
+    return p, src
+
+
+def _taps(p):
+    return p.H * p.W * p.D * (2 * p.radius + 1) ** 2
+
+
+# ---------------------------------------------------------------------------
+# clocks: nvidia-smi sampled during the run
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index, path):
+        self.path = path
+        self.proc = None
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(index), "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, t0, t1):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = _dt.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+                except ValueError:
+                    continue
+        except OSError:
+            return None
+        if not rows:
+            return None
+        inwin = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05]
+        window = "timed region"
+        if len(inwin) < 3:
+            inwin = [r for r in rows if r[0] <= t1 + 0.05][-20:]
+            window = "last samples up to the end of the timed region (timed region shorter than the sampling period)"
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in inwin for n, v in zip(names, r[3]) if v.lower().startswith("active")})
+        mhz = sorted(r[1] for r in inwin)
+        return {"sm_mhz": mhz[len(mhz) // 2], "sm_max_mhz": max(r[2] for r in inwin), "reasons": reasons,
+                "samples": len(inwin), "window": window}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline and reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_band(p, y0, rows, mode):
+    import oracle
+    t = time.perf_counter()
+    oracle.fbs(p.left, p.right, p.D, p.radius, p.sigma_s, p.sigma_r, p.tau, mode=mode, rows=(y0, y0 + rows))
+    return time.perf_counter() - t
+
+
+def cpu_baseline(p, seconds, mode):
+    """The oracle as it stands, single-threaded, on a row band sized to about
+    ``seconds`` of work; Gtaps/s counts the taps of the rows it aggregated
+    (its cost rows, including the 2*radius halo rows, are inside the time)."""
+    probe = min(8, p.H)
+    y0 = max(0, p.H // 2 - probe // 2)
+    t = _oracle_band(p, y0, probe, mode)
+    rows = int(max(probe, min(p.H, probe * seconds / max(t, 1e-6))))
+    y0 = max(0, (p.H - rows) // 2)
+    t = _oracle_band(p, y0, rows, mode)
+    taps = rows * p.W * p.D * (2 * p.radius + 1) ** 2
+    return {"value": taps / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"rows {y0}..{y0 + rows - 1} of the {p.W}x{p.H} frame ({rows} of {p.H} rows), "
+                      f"single-threaded FP64 C oracle, {t:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from synth import make_pair
+    oracle.build()
+    p = make_pair(args.workload, args.seed)
+    mode = 0 if args.cost == "ncc" else 1
+    steps = args.steps if args.steps is not None else 5
+    warmup = args.warmup if args.warmup is not None else 1
+    # size each step's row band so the whole run stays near two minutes
+    t8 = _oracle_band(p, p.H // 2 - 4, 8, mode) / 8
+    rows = int(max(1, min(p.H, 120.0 / max(1, steps + warmup) / max(t8, 1e-6))))
+    for i in range(warmup):
+        _oracle_band(p, (i * rows) % max(1, p.H - rows + 1), rows, mode)
+    total = 0.0
+    for i in range(steps):
+        total += _oracle_band(p, (i * rows) % max(1, p.H - rows + 1), rows, mode)
+    taps = steps * rows * p.W * p.D * (2 * p.radius + 1) ** 2
+    value = taps / total / 1e9
+    sample = f"{rows} rows of the {p.W}x{p.H} frame per step, single-threaded FP64 C oracle"
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * total / steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": _config(p, args, "ours"),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def _config(p, args, impl):
+    return {"workload": args.workload, "H": p.H, "W": p.W, "C": p.C, "D": p.D, "radius": p.radius,
+            "window": f"{2 * p.radius + 1}x{2 * p.radius + 1}", "sigma_s": p.sigma_s, "sigma_r": p.sigma_r,
+            "tau": p.tau, "cost": args.cost, "precision": args.prec, "seed": args.seed,
+            "pairs_per_step_per_gpu": 1, "parallelism": f"replicas x{args.gpus}",
+            "l2": "512 MiB flush write before every step, outside the per-step CUDA-event timing",
+            "inputs": "resident in HBM before the timed region"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def _traffic_for(kernel_file, kernel_name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        with open(kernel_file, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+    except (OSError, ValueError):
+        return None
+    ent = t.get(kernel_name)
+    if not ent or ent.get("source_sha256_16") != h:
+        return None
+    return ent.get("dram_bytes_per_launch_full_size")
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1807_02044_gb300 as fbs
+    from synth import make_pair
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    steps = args.steps if args.steps is not None else 3000
+    warmup = max(3, args.warmup if args.warmup is not None else 20)
+
+    p = make_pair(args.workload, args.seed + rank)
+    mode = fbs.FBS_COST_NCC if args.cost == "ncc" else fbs.FBS_COST_TAD
+    ctx = fbs.Context(dev.index, cost=mode)
+    stream = torch.cuda.Stream(dev)
+    dl = torch.from_numpy(p.left).to(dev)
+    dr = torch.from_numpy(p.right).to(dev)
+    di = torch.empty((p.H, p.W), dtype=torch.int32, device=dev)
+    ds = torch.empty((p.H, p.W), dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    call = lambda: fbs.fbs_compute_disparity(ctx.ctx, dl, dr, p.H, p.W, p.C, p.D, p.radius, p.sigma_s, p.sigma_r,
+                                             p.tau, di, ds, stream)
+    torch.cuda.synchronize()
+    sampler = None if args.no_clocks else ClockSampler(dev.index, os.path.join(ROOT, "_bench_clocks.csv"))
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            flush.fill_(1)
+            call()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        fbs.fbs_profile(ctx.ctx, 1)
+        t0 = time.time()
+        for a, b in evs:
+            flush.fill_(1)
+            a.record(stream)
+            call()
+            b.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t1 = time.time()
+        fbs.fbs_profile(ctx.ctx, 0)
+    step_ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    if dist:
+        t = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    kt = {fbs.KERNEL_NAMES[k]: fbs.fbs_profile_read(ctx.ctx, k) for k in range(fbs.FBS_KERNEL_KINDS)}
+    launches = sum(n for _, n in kt.values())
+    clocks = None
+    if sampler is not None:
+        sampler.stop()
+        clocks = sampler.summary(t0, t1)
+        try:
+            os.remove(sampler.path)
+        except OSError:
+            pass
+
+    taps = _taps(p)
+    value = world * taps / (step_ms * 1e-3) / 1e9
+    peaks, peak_src = _peaks()
+    agg_ms, agg_n = kt["aggregate_f32"]
+    cost_ms, cost_n = kt["cost_build"]
+    agg_launch_ms = agg_ms / max(1, agg_n)
+    cost_launch_ms = cost_ms / max(1, cost_n)
+    fp32_peak = GB300_SMS * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    flops = 2.0 * taps
+    roofline = {"kernel": "aggregate_f32_kernel", "bound": "alu", "achieved": flops / (agg_launch_ms * 1e-3) / 1e12,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "peak_source": f"derived: {GB300_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                               f"{peaks['sm_max_mhz']:.0f} MHz (max SM clock, {peak_src})",
+                "algorithmic": "2 flop per tap (one FMA per window tap per disparity), H*W*D*(2r+1)^2 taps",
+                "avg_launch_ms": agg_launch_ms, "launches": agg_n}
+    roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    roofline["traffic"] = _traffic_for(os.path.join(ROOT, "paper_1807_02044_gb300", "csrc", "fbs_aggregate_f32.cu"),
+                                       "aggregate_f32_kernel")
+    ld = (p.D + 3) // 4 * 4
+    cost_bytes = 2 * p.H * p.W * p.C + 4 * p.H * p.W * ld
+    roofline_cost = {"kernel": "cost_build_kernel", "bound": "hbm",
+                     "achieved": cost_bytes / (cost_launch_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": None, "avg_launch_ms": cost_launch_ms, "launches": cost_n,
+                     "algorithmic": "read both images once, write the FP32 cost volume once",
+                     "traffic": _traffic_for(os.path.join(ROOT, "paper_1807_02044_gb300", "csrc", "fbs_cost.cu"),
+                                             "cost_build_kernel")}
+    roofline_cost["frac"] = roofline_cost["achieved"] / roofline_cost["peak"]
+
+    e2e = None
+    if not args.no_e2e:
+        n_e2e = min(steps, 200)
+        hl = torch.from_numpy(p.left).pin_memory()
+        hr = torch.from_numpy(p.right).pin_memory()
+        hi = torch.empty((p.H, p.W), dtype=torch.int32).pin_memory()
+        hs = torch.empty((p.H, p.W), dtype=torch.float32).pin_memory()
+        host_call = lambda: fbs.fbs_compute_disparity_host(ctx.ctx, hl.data_ptr(), hr.data_ptr(), p.H, p.W, p.C, p.D,
+                                                           p.radius, p.sigma_s, p.sigma_r, p.tau, hi.data_ptr(),
+                                                           hs.data_ptr())
+        for _ in range(3):
+            host_call()
+        tot = 0.0
+        for _ in range(n_e2e):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            host_call()
+            tot += time.perf_counter() - t
+        e2e_s = tot / n_e2e
+        if dist:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        # the host path must agree with the device path
+        assert np.array_equal(hi.numpy(), di.cpu().numpy())
+        e2e = {"value": world * taps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * p.H * p.W * p.C,
+               "d2h_bytes_per_step": 8 * p.H * p.W, "steps": n_e2e,
+               "call": "fbs_compute_disparity_host (pinned host buffers, copies and sync inside the timed call)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p, args.cpu_seconds, mode)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
+           "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic", "config": _config(p, args, "ours"),
+           "fps": world * 1e3 / step_ms, "mde_per_s": world * p.W * p.H * p.D / (step_ms * 1e-3) * 1e-6,
+           "roofline": roofline, "roofline_cost_build": roofline_cost, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": launches, "kernel_ms_per_step": {k: v[0] / steps for k, v in kt.items() if v[1]},
+           "clocks": clocks, "wall_s_timed_region": t1 - t0}
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,159 @@
+/*
+ * fbs.h -- C ABI of libfbs, fast bilateral stereo (FBS) on one GB300 GPU.
+ *
+ * The method ("Real-Time Subpixel Fast Bilateral Stereo", Sec. II):
+ *   1. matching cost:  normalised cross-correlation of 3x3 blocks, Eq. (1)-(3),
+ *                      stored as C = 1 - c in [0, 2];
+ *   2. aggregation:    C_agg(p, d) = sum_q w(p,q) C(q,d) / sum_q w(p,q) over the
+ *                      (2 radius + 1)^2 window, w = omega_d * omega_r, Eq. (6)-(8);
+ *   3. optimisation:   winner-take-all over d, Sec. II-C / III;
+ *   4. refinement:     parabola through C_agg(d*-1), C_agg(d*), C_agg(d*+1), Eq. (10).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an fbs_status and never aborts the process.  After a
+ *     non-OK status, fbs_last_error() gives a one-line message.
+ *   - Images are uint8, row-major HWC (pitch W*C bytes), C = 1 or 3, in DEVICE
+ *     memory owned by the caller unless the entry point says "host".
+ *   - Cost and aggregated volumes are float32, layout [H][W][D] (D innermost).
+ *   - Disparity maps are H*W, int32 (integer winner) and float32 (subpixel).
+ *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed
+ *     as void*; NULL selects the context's own stream).  Errors raised by
+ *     kernels surface at the next call or at fbs_sync().
+ *   - Arguments are validated on the host before any launch; a violation
+ *     returns FBS_ERR_INVALID_ARG and launches nothing.
+ *   - Limits: 1 <= H, W <= 16384; C in {1, 3}; 1 <= D <= 1024;
+ *     0 <= radius <= 31; sigma_s > 0; sigma_r > 0; tau >= 0 (TAD mode).
+ *   - A context is bound to one device and is not thread-safe: use one per
+ *     host thread.
+ */
+#ifndef FBS_H
+#define FBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fbs_ctx fbs_ctx;
+
+typedef enum {
+    FBS_OK = 0,
+    FBS_ERR_INVALID_ARG = 1,   /* bad pointer, size or parameter */
+    FBS_ERR_OOM = 2,           /* device allocation failed or workspace cap reached */
+    FBS_ERR_CUDA = 3,          /* a CUDA call or kernel failed; see fbs_last_error */
+    FBS_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
+    FBS_ERR_UNSUPPORTED = 5    /* valid request this build cannot serve */
+} fbs_status;
+
+/* Matching cost.  NCC is the paper's, Eq. (1)-(3) with varrho = 1.  TAD is a
+ * truncated mean absolute difference min(mean_c |I_l - I_r|, tau), not in the
+ * paper, offered for comparison. */
+typedef enum { FBS_COST_NCC = 0, FBS_COST_TAD = 1 } fbs_cost_mode;
+
+/* Arithmetic of the aggregation, Eq. (6).  F32: FP32 FMA.  BF16 / F16: cost
+ * and weight tiles rounded to 16 bits, products on the tensor cores with FP32
+ * accumulation; normalisation, WTA and Eq. (10) stay FP32. */
+typedef enum { FBS_PREC_F32 = 0, FBS_PREC_BF16 = 1, FBS_PREC_F16 = 2 } fbs_precision;
+
+typedef struct {
+    int cost;                   /* fbs_cost_mode */
+    int prec;                   /* fbs_precision */
+    int fused;                  /* reserved, 0 */
+    size_t workspace_cap;       /* bytes of scratch the context may hold; 0 = unlimited */
+    const char *autotune_cache_path; /* reserved, may be NULL */
+} fbs_options;
+
+/* Fill *opt with the defaults: NCC, F32, unfused, no cap. */
+void fbs_default_options(fbs_options *opt);
+
+/* Create a context on CUDA device `device`.  opt may be NULL (defaults).
+ * The context owns its stream and scratch memory; *out receives it. */
+fbs_status fbs_create(fbs_ctx **out, const fbs_options *opt, int device);
+
+/* Release everything the context owns.  NULL-safe.  Synchronises its stream. */
+fbs_status fbs_destroy(fbs_ctx *ctx);
+
+/* Replace the options of an existing context (cost mode, precision, cap). */
+fbs_status fbs_set_options(fbs_ctx *ctx, const fbs_options *opt);
+
+/* Block until all work issued through ctx (on any stream) has finished and
+ * report any kernel error. */
+fbs_status fbs_sync(fbs_ctx *ctx);
+
+/* Message for the last non-OK status of this context ("" if none). */
+const char *fbs_last_error(const fbs_ctx *ctx);
+
+/*
+ * The whole path (Sec. II-A..II-D; implementation Sec. III): cost volume of
+ * the left view, bilateral aggregation guided by the left image, WTA and
+ * Eq. (10).  left, right: device images.  disp_int, disp_subpix: device
+ * outputs of H*W elements; either may be NULL but not both.  sigma_s is
+ * gamma_d of Eq. (7), sigma_r is gamma_r of Eq. (8); tau is used only by the
+ * TAD cost mode.  Scratch: one cost volume (H*W*D*4 bytes) held by ctx.
+ */
+fbs_status fbs_compute_disparity(fbs_ctx *ctx, const uint8_t *left, const uint8_t *right,
+                                 int H, int W, int C, int D, int radius,
+                                 float sigma_s, float sigma_r, float tau,
+                                 int32_t *disp_int, float *disp_subpix, void *cuda_stream);
+
+/*
+ * Same as fbs_compute_disparity with HOST buffers: left/right are read from
+ * host memory (pinned memory gives the fastest copies), results are written
+ * to host memory, and the call returns after the results have arrived.  The
+ * host-to-device and device-to-host copies run on the context's stream.
+ */
+fbs_status fbs_compute_disparity_host(fbs_ctx *ctx, const uint8_t *left, const uint8_t *right,
+                                      int H, int W, int C, int D, int radius,
+                                      float sigma_s, float sigma_r, float tau,
+                                      int32_t *disp_int, float *disp_subpix);
+
+/*
+ * Step 1 alone, Eq. (1)-(3) (or TAD): writes cost_out[H][W][D] (device,
+ * float32, caller-owned).  For u - d < 0 the cost is the maximum (2 for NCC,
+ * tau for TAD); a zero-variance block gives c = 0.
+ */
+fbs_status fbs_cost_volume(fbs_ctx *ctx, const uint8_t *left, const uint8_t *right,
+                           int H, int W, int C, int D, float tau, float *cost_out,
+                           void *cuda_stream);
+
+/*
+ * Steps 2-4 on a given cost volume, Eq. (6)-(8) and Eq. (10): cost[H][W][D]
+ * (device float32), guide = the left image (device uint8 HWC).  agg_out
+ * (nullable) receives the aggregated volume [H][W][D]; disp_int / disp_subpix
+ * as above (all three may not be NULL together).  The cost values are taken
+ * as given, so a test can feed any volume (e.g. an exact quadratic in d).
+ */
+fbs_status fbs_aggregate(fbs_ctx *ctx, const float *cost, const uint8_t *guide,
+                         int H, int W, int C, int D, int radius,
+                         float sigma_s, float sigma_r,
+                         float *agg_out, int32_t *disp_int, float *disp_subpix,
+                         void *cuda_stream);
+
+/*
+ * Kernel accounting (not a step of the method).  The context counts every
+ * kernel it launches, per kind.  With profiling enabled it also brackets each
+ * launch with a CUDA event pair recorded on the launch stream, so the device
+ * time of each kernel kind can be read back.  fbs_profile(ctx, 1) clears the
+ * counters and starts recording; fbs_profile(ctx, 0) stops.  fbs_profile_read
+ * synchronises on the recorded events and returns, for one kind, the summed
+ * device milliseconds (0 when profiling was off) and the launch count since
+ * the last fbs_profile(ctx, 1).
+ */
+typedef enum {
+    FBS_KERNEL_COST = 0,        /* cost-volume build, Eq. (1)-(3) / TAD */
+    FBS_KERNEL_AGG_F32 = 1,     /* FP32 aggregation + WTA + Eq. (10) */
+    FBS_KERNEL_AGG_TC = 2,      /* tensor-core aggregation + WTA + Eq. (10) */
+    FBS_KERNEL_OTHER = 3,       /* every other kernel of the library */
+    FBS_KERNEL_KINDS = 4
+} fbs_kernel_kind;
+
+fbs_status fbs_profile(fbs_ctx *ctx, int enable);
+fbs_status fbs_profile_read(fbs_ctx *ctx, int kind, double *total_ms, long long *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FBS_H */

@@ -1,0 +1,263 @@
+"""Python binding of libfbs, fast bilateral stereo on one GB300 GPU.
+
+The binding only marshals arguments: every step of the path runs in the CUDA
+kernels of ``libfbs.so`` (built by ``build.py``).  Functions carry the names
+of the C ABI in ``include/fbs.h``.  Pointer arguments accept a CUDA tensor
+(its ``data_ptr()``), a plain integer address, or None for NULL.  Streams
+accept a ``torch.cuda.Stream``, a raw ``cudaStream_t`` integer, or None (the
+context's own stream).  A non-OK status raises FBSError with the library's
+message.  There is no CPU fallback: the library is loaded on first use, and
+if it is missing that first call raises ImportError.  (Loading is deferred
+only so that ``paper_1807_02044_gb300.build`` can be imported to build it.)
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfbs.so")
+
+FBS_OK = 0
+FBS_ERR_INVALID_ARG = 1
+FBS_ERR_OOM = 2
+FBS_ERR_CUDA = 3
+FBS_ERR_TIMEOUT = 4
+FBS_ERR_UNSUPPORTED = 5
+STATUS_NAMES = {0: "FBS_OK", 1: "FBS_ERR_INVALID_ARG", 2: "FBS_ERR_OOM", 3: "FBS_ERR_CUDA",
+                4: "FBS_ERR_TIMEOUT", 5: "FBS_ERR_UNSUPPORTED"}
+
+FBS_COST_NCC = 0
+FBS_COST_TAD = 1
+FBS_PREC_F32 = 0
+FBS_PREC_BF16 = 1
+FBS_PREC_F16 = 2
+
+FBS_KERNEL_COST = 0
+FBS_KERNEL_AGG_F32 = 1
+FBS_KERNEL_AGG_TC = 2
+FBS_KERNEL_OTHER = 3
+FBS_KERNEL_KINDS = 4
+KERNEL_NAMES = {0: "cost_build", 1: "aggregate_f32", 2: "aggregate_tc", 3: "other"}
+
+# Every function the header declares, with (restype, argtypes).
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_F = ctypes.c_float
+_Z = ctypes.c_size_t
+
+
+class fbs_options(ctypes.Structure):
+    _fields_ = [("cost", _I), ("prec", _I), ("fused", _I), ("workspace_cap", _Z),
+                ("autotune_cache_path", ctypes.c_char_p)]
+
+
+SIGNATURES = {
+    "fbs_default_options": (None, [ctypes.POINTER(fbs_options)]),
+    "fbs_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(fbs_options), _I]),
+    "fbs_destroy": (_I, [_P]),
+    "fbs_set_options": (_I, [_P, ctypes.POINTER(fbs_options)]),
+    "fbs_sync": (_I, [_P]),
+    "fbs_last_error": (ctypes.c_char_p, [_P]),
+    "fbs_compute_disparity": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _F, _P, _P, _P]),
+    "fbs_compute_disparity_host": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _F, _P, _P]),
+    "fbs_cost_volume": (_I, [_P, _P, _P, _I, _I, _I, _I, _F, _P, _P]),
+    "fbs_aggregate": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _P, _P, _P, _P]),
+    "fbs_profile": (_I, [_P, _I]),
+    "fbs_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+}
+
+
+class FBSError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libfbs.so is not built ({LIB_PATH}); run paper_1807_02044_gb300.build.build() "
+                          "or __graft_entry__.build() first. There is no CPU fallback.")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    return _lib
+
+
+def _addr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):          # numpy array (host entry point)
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+_CUDA_STREAM_LEGACY = 0x1   # cudaStreamLegacy: the device's legacy default stream
+
+
+def _stream(s):
+    """None -> NULL (the context's own stream).  A torch stream whose handle is
+    0 is torch's legacy default stream; it is passed as cudaStreamLegacy so the
+    library does not read it as NULL."""
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    h = s.cuda_stream
+    return h if h else _CUDA_STREAM_LEGACY
+
+
+def _check(ctx, status):
+    if status != FBS_OK:
+        msg = lib().fbs_last_error(ctx).decode() if ctx else ""
+        raise FBSError(status, msg)
+
+
+def fbs_default_options():
+    o = fbs_options()
+    lib().fbs_default_options(ctypes.byref(o))
+    return o
+
+
+def make_options(cost=FBS_COST_NCC, prec=FBS_PREC_F32, fused=0, workspace_cap=0):
+    o = fbs_default_options()
+    o.cost, o.prec, o.fused, o.workspace_cap = cost, prec, fused, workspace_cap
+    return o
+
+
+def fbs_create(options=None, device=0):
+    ctx = _P()
+    st = lib().fbs_create(ctypes.byref(ctx), ctypes.byref(options) if options is not None else None, device)
+    if st != FBS_OK:
+        raise FBSError(st, f"fbs_create(device={device}) failed")
+    return ctx.value
+
+
+def fbs_destroy(ctx):
+    _check(None, lib().fbs_destroy(ctx))
+
+
+def fbs_set_options(ctx, options):
+    _check(ctx, lib().fbs_set_options(ctx, ctypes.byref(options)))
+
+
+def fbs_sync(ctx):
+    _check(ctx, lib().fbs_sync(ctx))
+
+
+def fbs_last_error(ctx):
+    return lib().fbs_last_error(ctx).decode()
+
+
+def fbs_compute_disparity(ctx, left, right, H, W, C, D, radius, sigma_s, sigma_r, tau, disp_int, disp_subpix,
+                          stream=None):
+    _check(ctx, lib().fbs_compute_disparity(ctx, _addr(left), _addr(right), H, W, C, D, radius, sigma_s, sigma_r,
+                                           tau, _addr(disp_int), _addr(disp_subpix), _stream(stream)))
+
+
+def fbs_compute_disparity_host(ctx, left, right, H, W, C, D, radius, sigma_s, sigma_r, tau, disp_int,
+                               disp_subpix):
+    _check(ctx, lib().fbs_compute_disparity_host(ctx, _addr(left), _addr(right), H, W, C, D, radius, sigma_s,
+                                                sigma_r, tau, _addr(disp_int), _addr(disp_subpix)))
+
+
+def fbs_cost_volume(ctx, left, right, H, W, C, D, tau, cost_out, stream=None):
+    _check(ctx, lib().fbs_cost_volume(ctx, _addr(left), _addr(right), H, W, C, D, tau, _addr(cost_out),
+                                     _stream(stream)))
+
+
+def fbs_aggregate(ctx, cost, guide, H, W, C, D, radius, sigma_s, sigma_r, agg_out, disp_int, disp_subpix,
+                  stream=None):
+    _check(ctx, lib().fbs_aggregate(ctx, _addr(cost), _addr(guide), H, W, C, D, radius, sigma_s, sigma_r,
+                                   _addr(agg_out), _addr(disp_int), _addr(disp_subpix), _stream(stream)))
+
+
+def fbs_profile(ctx, enable):
+    _check(ctx, lib().fbs_profile(ctx, int(bool(enable))))
+
+
+def fbs_profile_read(ctx, kind):
+    """(summed device milliseconds, launch count) of one kernel kind."""
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    _check(ctx, lib().fbs_profile_read(ctx, kind, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+class Context:
+    """Owning handle around fbs_create / fbs_destroy with tensor-level helpers."""
+
+    def __init__(self, device=0, cost=FBS_COST_NCC, prec=FBS_PREC_F32, workspace_cap=0):
+        self.device = device
+        self.ctx = fbs_create(make_options(cost=cost, prec=prec, workspace_cap=workspace_cap), device)
+
+    def close(self):
+        if self.ctx:
+            fbs_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, cost=FBS_COST_NCC, prec=FBS_PREC_F32, workspace_cap=0):
+        fbs_set_options(self.ctx, make_options(cost=cost, prec=prec, workspace_cap=workspace_cap))
+
+    def compute_disparity(self, left, right, D, radius, sigma_s, sigma_r, tau=0.0, stream=None):
+        """left, right: CUDA uint8 tensors (H, W, C) or (H, W).  Returns (disp_int, disp_subpix)."""
+        import torch
+        H, W = left.shape[0], left.shape[1]
+        C = left.shape[2] if left.dim() == 3 else 1
+        di = torch.empty((H, W), dtype=torch.int32, device=left.device)
+        ds = torch.empty((H, W), dtype=torch.float32, device=left.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(left.device)
+        fbs_compute_disparity(self.ctx, left, right, H, W, C, D, radius, sigma_s, sigma_r, tau, di, ds, stream)
+        return di, ds
+
+    def cost_volume(self, left, right, D, tau=0.0, stream=None):
+        import torch
+        H, W = left.shape[0], left.shape[1]
+        C = left.shape[2] if left.dim() == 3 else 1
+        out = torch.empty((H, W, D), dtype=torch.float32, device=left.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(left.device)
+        fbs_cost_volume(self.ctx, left, right, H, W, C, D, tau, out, stream)
+        return out
+
+    def aggregate(self, cost, guide, radius, sigma_s, sigma_r, want_agg=True, stream=None):
+        import torch
+        H, W, D = cost.shape
+        C = guide.shape[2] if guide.dim() == 3 else 1
+        agg = torch.empty_like(cost) if want_agg else None
+        di = torch.empty((H, W), dtype=torch.int32, device=cost.device)
+        ds = torch.empty((H, W), dtype=torch.float32, device=cost.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(cost.device)
+        fbs_aggregate(self.ctx, cost, guide, H, W, C, D, radius, sigma_s, sigma_r, agg, di, ds, stream)
+        return agg, di, ds

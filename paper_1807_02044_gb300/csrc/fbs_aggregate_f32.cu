@@ -1,0 +1,361 @@
+// Steps 2-4 of fast bilateral stereo in FP32: bilateral aggregation of every
+// disparity slice (Sec. II-B, Eq. (6)-(8)), winner-take-all (Sec. II-C) and
+// the parabola refinement of Eq. (10) (Sec. II-D), in one kernel.
+//
+//   Agg(p, d) = sum_q w(p, q) C(q, d) / sum_q w(p, q),
+//   w(p, q)   = exp(-|q - p|^2 / gamma_d^2) * exp(-|I(q) - I(p)|^2 / gamma_r^2),
+// q over the (2 rho + 1)^2 window clipped to the image; I is the left image
+// (for RGB the squared Euclidean colour distance).  The two exponentials are
+// evaluated as one exp2 of the summed exponent.
+//
+// Work decomposition (one CTA = a 32 x 4 pixel tile and a chunk of DC
+// disparities; 8 warps):
+//   * Cost rows r = y0-rho .. y0+3+rho are streamed through a 3-deep ring of
+//     shared-memory buffers with cp.async (zero-filled outside the image), and
+//     the guide row r through a matching ring.
+//   * For each streamed row, the CTA computes the weights w(p, q) of every
+//     tile pixel p whose window contains row r -- once per (p, q), shared by
+//     all DC disparities -- into a double-buffered shared array.
+//   * Warp g owns tile columns 4g..4g+3; lane = (row yi, disparity group k).
+//     A thread accumulates 4 pixels x KD disparities.  Along the window the
+//     four cost columns it needs at tap dx are held in a rotating register
+//     window, so each cost column is read from shared memory once and used
+//     for up to 4 pixels, and each weight is a broadcast read used for KD
+//     disparities.  Lanes of different rows read the same cost address
+//     (broadcast), so a warp's cost read is one 128-byte wavefront.
+//   * One __syncthreads per streamed row.
+//   * After the last row the sums are normalised, staged in shared memory and
+//     reduced per pixel: WTA with the smallest d on ties, plus the values at
+//     d*-1 and d*+1 carried across chunks for Eq. (10).
+#include "fbs_internal.cuh"
+
+namespace fbs {
+namespace {
+
+constexpr int kTX = 32;        // tile width (pixels)
+constexpr int kTY = 4;         // tile height (rows)
+constexpr int kPX = 4;         // pixels per thread along x
+constexpr int kThreads = 256;  // 8 warps
+constexpr int kNPix = kTX * kTY;
+
+__host__ __device__ inline int weight_stride(int rho)
+{
+    // per-row stride of the weight buffer [dx][kTX]; == 8 (mod 32) so that
+    // the four rows of a warp read four different bank groups
+    int n = (2 * rho + 1) * kTX;
+    n = (n + 31) & ~31;
+    return n + 8;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int src_bytes)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <int DC>
+__host__ __device__ inline size_t smem_bytes(int rho)
+{
+    const int NC = kTX + 2 * rho;
+    const size_t ring = (size_t)3 * NC * DC;
+    const size_t stage = (size_t)kNPix * (DC + 1);
+    const size_t a = ring > stage ? ring : stage;
+    return sizeof(float) * (a + 2 * (size_t)kTY * weight_stride(rho) + 2 * kNPix) + sizeof(float4) * 3 * NC;
+}
+
+// Load cost row r, columns x0-rho .. x0-rho+NC-1, disparities dc0 .. dc0+DC-1.
+template <int DC, bool VEC>
+__device__ __forceinline__ void load_cost_row(float* dst, const float* __restrict__ cost, int ld, int W,
+                                              int D, int r, int x0, int rho, int NC, int dc0)
+{
+    if (VEC) {
+        constexpr int NQ4 = DC / 4;
+        for (int it = threadIdx.x; it < NC * NQ4; it += kThreads) {
+            const int col = it / NQ4, q = it - col * NQ4;
+            const int gx = x0 - rho + col;
+            const int d = dc0 + 4 * q;
+            const bool in = gx >= 0 && gx < W && d < D;
+            const int gxc = in ? gx : 0;
+            const int dcl = in ? d : 0;
+            const float* src = cost + ((size_t)r * W + gxc) * ld + dcl;
+            const int bytes = in ? 4 * min(4, D - d) : 0;
+            cp_async16(dst + col * DC + 4 * q, src, bytes);
+        }
+    } else {
+        for (int it = threadIdx.x; it < NC * DC; it += kThreads) {
+            const int col = it / DC, q = it - col * DC;
+            const int gx = x0 - rho + col;
+            const int d = dc0 + q;
+            const bool in = gx >= 0 && gx < W && d < D;
+            const float* src = cost + ((size_t)r * W + (in ? gx : 0)) * ld + (in ? d : 0);
+            cp_async4(dst + col * DC + q, src, in ? 4 : 0);
+        }
+    }
+}
+
+__device__ __forceinline__ void load_guide_row(float4* dst, const uint8_t* __restrict__ guide, int W,
+                                               int C, int r, int x0, int rho, int NC)
+{
+    for (int col = threadIdx.x; col < NC; col += kThreads) {
+        const int gx = x0 - rho + col;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gx >= 0 && gx < W) {
+            const uint8_t* p = guide + ((size_t)r * W + gx) * C;
+            v.x = (float)p[0];
+            if (C == 3) {
+                v.y = (float)p[1];
+                v.z = (float)p[2];
+            }
+        }
+        dst[col] = v;
+    }
+}
+
+template <int KD, bool VEC>
+__global__ void __launch_bounds__(kThreads, 2)
+aggregate_f32_kernel(const float* __restrict__ cost, int ld, const uint8_t* __restrict__ guide, int H,
+                     int W, int C, int D, int rho, float neg_ks, float neg_kr,
+                     float* __restrict__ agg_out, int32_t* __restrict__ disp_int,
+                     float* __restrict__ disp_sub)
+{
+    constexpr int DC = 8 * KD;   // disparities per chunk
+    constexpr int NQ = KD / 4;   // float4 groups per thread
+    extern __shared__ float4 smem_f4[];
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, g = tid >> 5;
+    const int yi = lane >> 3, k = lane & 7;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    const int NC = kTX + 2 * rho;
+    const int NT = 2 * rho + 1;
+    const int WS = weight_stride(rho);
+
+    // shared memory: guide ring [3][NC] float4 | cost ring [3][NC][DC] (aliased
+    // by the stage [kNPix][DC+1]) | weights [2][kTY][WS] | den [2][kNPix]
+    float4* const gring = smem_f4;
+    float* const cring = (float*)(gring + 3 * NC);
+    float* const stage = cring;
+    const int cslot = NC * DC;
+    const int ring_sz = 3 * NC * DC, stage_sz = kNPix * (DC + 1);
+    float* const wring = cring + (ring_sz > stage_sz ? ring_sz : stage_sz);
+    const int wslot = kTY * WS;
+    float* const den_s = wring + 2 * wslot;
+
+    // producer role: pixel pp of the tile, half of the dx range
+    const int pp = tid & (kNPix - 1);
+    const int half = tid >> 7;
+    const int pyi = pp / kTX, ppx = pp % kTX;
+    const int py = y0 + pyi, pxg = x0 + ppx;
+    const bool pvalid = py < H && pxg < W;
+    const int dx_lo = half ? rho + 1 : 0;
+    const int dx_hi = half ? NT : rho + 1;
+    float3 pc = make_float3(0.f, 0.f, 0.f);
+    if (pvalid) {
+        const uint8_t* p = guide + ((size_t)py * W + pxg) * C;
+        pc.x = (float)p[0];
+        if (C == 3) {
+            pc.y = (float)p[1];
+            pc.z = (float)p[2];
+        }
+    }
+
+    // WTA role (tid < kNPix): state of pixel tid carried across chunks
+    float best = __int_as_float(0x7f800000), a_prev = 0.f, a_next = 0.f, last = 0.f;
+    int bidx = 0;
+    bool pending = false;
+
+    // consumer role
+    const int y = y0 + yi;
+    const int r_lo = max(0, y0 - rho);
+    const int r_hi = min(H - 1, y0 + kTY - 1 + rho);
+    const int nr = r_hi - r_lo + 1;
+
+    for (int dc0 = 0; dc0 < D; dc0 += DC) {
+        float4 acc[kPX][NQ];
+#pragma unroll
+        for (int i = 0; i < kPX; ++i)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) acc[i][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float den_part = 0.f;
+
+        load_cost_row<DC, VEC>(cring, cost, ld, W, D, r_lo, x0, rho, NC, dc0);
+        cp_async_commit();
+        load_guide_row(gring, guide, W, C, r_lo, x0, rho, NC);
+        __syncthreads();
+
+        for (int s = 0; s < nr; ++s) {
+            const int r = r_lo + s;
+            // (A) prefetch the next cost row, (B) the next guide row
+            if (s + 1 < nr) {
+                load_cost_row<DC, VEC>(cring + ((s + 1) % 3) * cslot, cost, ld, W, D, r + 1, x0, rho, NC, dc0);
+                load_guide_row(gring + ((s + 1) % 3) * NC, guide, W, C, r + 1, x0, rho, NC);
+            }
+            cp_async_commit();
+            // (C) weights of row r for every tile pixel whose window reaches it
+            {
+                const int dy = r - py;
+                if (py < H && dy >= -rho && dy <= rho) {
+                    const float4* gr = gring + (s % 3) * NC;
+                    float* wrow = wring + (s & 1) * wslot + pyi * WS;
+                    const int dy2 = dy * dy;
+                    for (int dx = dx_lo; dx < dx_hi; ++dx) {
+                        const int qx = pxg + dx - rho;
+                        float w = 0.f;
+                        if (pxg < W && qx >= 0 && qx < W) {
+                            const float4 q = gr[ppx + dx];
+                            const float e0 = q.x - pc.x, e1 = q.y - pc.y, e2 = q.z - pc.z;
+                            const float col2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+                            const int ddx = dx - rho;
+                            const float sp2 = (float)(ddx * ddx + dy2);
+                            w = exp2f(fmaf(col2, neg_kr, sp2 * neg_ks));
+                        }
+                        wrow[dx * kTX + ppx] = w;
+                        den_part += w;
+                    }
+                }
+            }
+            // (D) own copies of row r have landed; (E) everyone's have
+            cp_async_wait1();
+            __syncthreads();
+            // (F) accumulate row r
+            const int dy = r - y;
+            if (y < H && dy >= -rho && dy <= rho) {
+                const float* cr = cring + (s % 3) * cslot + (kPX * g) * DC + 4 * k;
+                const float* wr = wring + (s & 1) * wslot + yi * WS + kPX * g;
+                float4 win[4][NQ];
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) win[j][q] = *(const float4*)(cr + j * DC + 32 * q);
+                for (int dx0 = 0; dx0 < NT; dx0 += 4) {
+#pragma unroll
+                    for (int s4 = 0; s4 < 4; ++s4) {
+                        const int dx = dx0 + s4;
+                        if (dx < NT) {
+#pragma unroll
+                            for (int q = 0; q < NQ; ++q)
+                                win[(s4 + 3) & 3][q] = *(const float4*)(cr + (dx + 3) * DC + 32 * q);
+                            const float4 w4 = *(const float4*)(wr + dx * kTX);
+                            const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                            for (int i = 0; i < kPX; ++i) {
+                                const int slot = (i + s4) & 3;
+#pragma unroll
+                                for (int q = 0; q < NQ; ++q) {
+                                    acc[i][q].x = fmaf(wv[i], win[slot][q].x, acc[i][q].x);
+                                    acc[i][q].y = fmaf(wv[i], win[slot][q].y, acc[i][q].y);
+                                    acc[i][q].z = fmaf(wv[i], win[slot][q].z, acc[i][q].z);
+                                    acc[i][q].w = fmaf(wv[i], win[slot][q].w, acc[i][q].w);
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+
+        // normalise and stage: stage[pixel][d] with pixel = yi*kTX + 4g + i
+        den_s[half * kNPix + pp] = den_part;
+        __syncthreads();   // all rows consumed, ring free; den visible
+#pragma unroll
+        for (int i = 0; i < kPX; ++i) {
+            const int pix = yi * kTX + kPX * g + i;
+            const float den = den_s[pix] + den_s[kNPix + pix];
+            const float inv = 1.f / den;
+            float* st = stage + pix * (DC + 1) + 4 * k;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                st[32 * q + 0] = acc[i][q].x * inv;
+                st[32 * q + 1] = acc[i][q].y * inv;
+                st[32 * q + 2] = acc[i][q].z * inv;
+                st[32 * q + 3] = acc[i][q].w * inv;
+            }
+        }
+        __syncthreads();
+        const int nd = min(DC, D - dc0);
+        if (agg_out != nullptr) {
+            for (int e = tid; e < kNPix * nd; e += kThreads) {
+                const int pix = e / nd, j = e - pix * nd;
+                const int ey = y0 + pix / kTX, ex = x0 + pix % kTX;
+                if (ey < H && ex < W) agg_out[((size_t)ey * W + ex) * D + dc0 + j] = stage[pix * (DC + 1) + j];
+            }
+        }
+        if (tid < kNPix) {
+            const float* st = stage + tid * (DC + 1);
+            for (int j = 0; j < nd; ++j) {
+                const float v = st[j];
+                if (pending) {
+                    a_next = v;
+                    pending = false;
+                }
+                if (v < best) {
+                    best = v;
+                    bidx = dc0 + j;
+                    a_prev = last;
+                    pending = true;
+                }
+                last = v;
+            }
+        }
+        __syncthreads();   // stage (aliasing the ring) consumed before the next chunk reloads it
+    }
+
+    if (tid < kNPix) {
+        const int oy = y0 + tid / kTX, ox = x0 + tid % kTX;
+        if (oy < H && ox < W) {
+            float ds = (float)bidx;
+            if (bidx > 0 && bidx < D - 1) {
+                const float den = 2.f * a_prev + 2.f * a_next - 4.f * best;
+                if (den > 0.f) ds = (float)bidx + (a_prev - a_next) / den;
+            }
+            const size_t o = (size_t)oy * W + ox;
+            if (disp_int) disp_int[o] = bidx;
+            if (disp_sub) disp_sub[o] = ds;
+        }
+    }
+}
+
+template <int KD, bool VEC>
+cudaError_t launch_kd(const float* cost, int ld, const uint8_t* guide, int H, int W, int C, int D,
+                      int rho, float neg_ks, float neg_kr, float* agg_out, int32_t* disp_int,
+                      float* disp_sub, cudaStream_t stream)
+{
+    const size_t smem = smem_bytes<8 * KD>(rho);
+    cudaError_t e = cudaFuncSetAttribute(aggregate_f32_kernel<KD, VEC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY);
+    aggregate_f32_kernel<KD, VEC><<<grid, kThreads, smem, stream>>>(
+        cost, ld, guide, H, W, C, D, rho, neg_ks, neg_kr, agg_out, disp_int, disp_sub);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_aggregate_f32(const float* cost, int ld, const uint8_t* guide, int H, int W, int C,
+                                 int D, int radius, float sigma_s, float sigma_r, float* agg_out,
+                                 int32_t* disp_int, float* disp_sub, cudaStream_t stream)
+{
+    // exp(-a/g^2) = exp2(-a * log2(e) / g^2)
+    const double log2e = 1.4426950408889634;
+    const float neg_ks = (float)(-log2e / ((double)sigma_s * sigma_s));
+    const float neg_kr = (float)(-log2e / ((double)sigma_r * sigma_r));
+    const bool vec = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(cost) & 15) == 0);
+    if (D <= 32) {
+        return vec ? launch_kd<4, true>(cost, ld, guide, H, W, C, D, radius, neg_ks, neg_kr, agg_out, disp_int, disp_sub, stream)
+                   : launch_kd<4, false>(cost, ld, guide, H, W, C, D, radius, neg_ks, neg_kr, agg_out, disp_int, disp_sub, stream);
+    }
+    return vec ? launch_kd<8, true>(cost, ld, guide, H, W, C, D, radius, neg_ks, neg_kr, agg_out, disp_int, disp_sub, stream)
+               : launch_kd<8, false>(cost, ld, guide, H, W, C, D, radius, neg_ks, neg_kr, agg_out, disp_int, disp_sub, stream);
+}
+
+}  // namespace fbs

@@ -1,0 +1,429 @@
+// C ABI of libfbs: contexts, argument validation, scratch management and the
+// dispatch of the fast-bilateral-stereo kernels.  See include/fbs.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fbs.h"
+#include "fbs_internal.cuh"
+
+struct fbs_ctx {
+    int device = 0;
+    fbs_options opt{};
+    cudaStream_t stream = nullptr;
+    void* ws = nullptr;          // cost volume scratch
+    size_t ws_bytes = 0;
+    void* io = nullptr;          // device staging for the host-buffer entry point
+    size_t io_bytes = 0;
+    std::string err;
+    // kernel accounting
+    long long launches[FBS_KERNEL_KINDS] = {0, 0, 0, 0};
+    bool profiling = false;
+    struct Rec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;            // recorded launches since fbs_profile(ctx, 1)
+    std::vector<cudaEvent_t> spare;   // event pool
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+fbs_status fail(fbs_ctx* ctx, fbs_status st, const char* fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+fbs_status cuda_fail(fbs_ctx* ctx, cudaError_t e, const char* where)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, FBS_ERR_OOM, "%s: %s", where, cudaGetErrorString(e));
+    return fail(ctx, FBS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
+
+fbs_status check_shape(fbs_ctx* ctx, int H, int W, int C, int D)
+{
+    if (H < 1 || H > 16384 || W < 1 || W > 16384)
+        return fail(ctx, FBS_ERR_INVALID_ARG, "image size %dx%d outside 1..16384", W, H);
+    if (C != 1 && C != 3) return fail(ctx, FBS_ERR_INVALID_ARG, "channels C=%d must be 1 or 3", C);
+    if (D < 1 || D > 1024) return fail(ctx, FBS_ERR_INVALID_ARG, "disparity count D=%d outside 1..1024", D);
+    return FBS_OK;
+}
+
+fbs_status check_agg_params(fbs_ctx* ctx, int radius, float sigma_s, float sigma_r)
+{
+    if (radius < 0 || radius > 31) return fail(ctx, FBS_ERR_INVALID_ARG, "radius=%d outside 0..31", radius);
+    if (!finite_pos(sigma_s)) return fail(ctx, FBS_ERR_INVALID_ARG, "sigma_s must be finite and > 0");
+    if (!finite_pos(sigma_r)) return fail(ctx, FBS_ERR_INVALID_ARG, "sigma_r must be finite and > 0");
+    return FBS_OK;
+}
+
+fbs_status check_tau(fbs_ctx* ctx, float tau)
+{
+    if (ctx->opt.cost == FBS_COST_TAD && !(std::isfinite(tau) && tau >= 0.f))
+        return fail(ctx, FBS_ERR_INVALID_ARG, "tau must be finite and >= 0 in TAD mode");
+    return FBS_OK;
+}
+
+fbs_status check_options(fbs_ctx* ctx, const fbs_options* o)
+{
+    if (o->cost != FBS_COST_NCC && o->cost != FBS_COST_TAD)
+        return fail(ctx, FBS_ERR_INVALID_ARG, "unknown cost mode %d", o->cost);
+    if (o->prec != FBS_PREC_F32 && o->prec != FBS_PREC_BF16 && o->prec != FBS_PREC_F16)
+        return fail(ctx, FBS_ERR_INVALID_ARG, "unknown precision %d", o->prec);
+    return FBS_OK;
+}
+
+cudaStream_t pick_stream(fbs_ctx* ctx, void* s) { return s ? (cudaStream_t)s : ctx->stream; }
+
+cudaEvent_t take_event(fbs_ctx* ctx)
+{
+    if (!ctx->spare.empty()) {
+        cudaEvent_t e = ctx->spare.back();
+        ctx->spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Bracket one kernel launch for the accounting API.
+struct LaunchScope {
+    fbs_ctx* ctx;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    LaunchScope(fbs_ctx* c, int k, cudaStream_t s) : ctx(c), kind(k), st(s)
+    {
+        if (ctx->profiling) {
+            a = take_event(ctx);
+            if (a) cudaEventRecord(a, st);
+        }
+    }
+    ~LaunchScope()
+    {
+        ctx->launches[kind]++;
+        if (a) {
+            cudaEvent_t b = take_event(ctx);
+            if (b) {
+                cudaEventRecord(b, st);
+                ctx->recs.push_back({kind, a, b});
+            } else {
+                ctx->spare.push_back(a);
+            }
+        }
+    }
+};
+
+// Grow-only device scratch, bounded by the context's cap.
+fbs_status ensure(fbs_ctx* ctx, void** buf, size_t* have, size_t need, const char* what)
+{
+    if (need <= *have) return FBS_OK;
+    const size_t cap = ctx->opt.workspace_cap;
+    if (cap && ctx->ws_bytes + ctx->io_bytes - *have + need > cap)
+        return fail(ctx, FBS_ERR_OOM, "%s needs %zu bytes; workspace cap is %zu", what, need, cap);
+    if (*buf) {
+        cudaError_t e = cudaDeviceSynchronize();   // the old buffer may still be in use
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise before growing scratch");
+        cudaFree(*buf);
+        *buf = nullptr;
+        *have = 0;
+    }
+    cudaError_t e = cudaMalloc(buf, need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return fail(ctx, FBS_ERR_OOM, "cudaMalloc(%zu) for %s: %s", need, what, cudaGetErrorString(e));
+    }
+    *have = need;
+    return FBS_OK;
+}
+
+fbs_status run_path(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C, int D,
+                    int radius, float sigma_s, float sigma_r, float tau, int32_t* disp_int,
+                    float* disp_subpix, cudaStream_t st)
+{
+    const int ld = fbs::padded_ld(D);
+    const size_t need = sizeof(float) * (size_t)H * W * ld;
+    fbs_status s = ensure(ctx, &ctx->ws, &ctx->ws_bytes, need, "cost volume");
+    if (s != FBS_OK) return s;
+    float* cost = (float*)ctx->ws;
+    if (ctx->opt.prec != FBS_PREC_F32)
+        return fail(ctx, FBS_ERR_UNSUPPORTED, "precision %d is not built in this library", ctx->opt.prec);
+    cudaError_t e;
+    {
+        LaunchScope ls(ctx, FBS_KERNEL_COST, st);
+        e = fbs::launch_cost_build(left, right, H, W, C, D, ld, ctx->opt.cost, tau, cost, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cost build launch");
+    {
+        LaunchScope ls(ctx, FBS_KERNEL_AGG_F32, st);
+        e = fbs::launch_aggregate_f32(cost, ld, left, H, W, C, D, radius, sigma_s, sigma_r, nullptr, disp_int,
+                                      disp_subpix, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "aggregation launch");
+    return FBS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fbs_default_options(fbs_options* opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof *opt);
+    opt->cost = FBS_COST_NCC;
+    opt->prec = FBS_PREC_F32;
+}
+
+fbs_status fbs_create(fbs_ctx** out, const fbs_options* opt, int device)
+{
+    if (!out) return FBS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return FBS_ERR_CUDA;
+    }
+    if (device < 0 || device >= n) return FBS_ERR_INVALID_ARG;
+    fbs_ctx* ctx = new (std::nothrow) fbs_ctx();
+    if (!ctx) return FBS_ERR_OOM;
+    if (opt) {
+        if (check_options(ctx, opt) != FBS_OK) {
+            delete ctx;
+            return FBS_ERR_INVALID_ARG;
+        }
+        ctx->opt = *opt;
+    } else {
+        fbs_default_options(&ctx->opt);
+    }
+    ctx->device = device;
+    DeviceGuard g(device);
+    if (!g.ok) {
+        delete ctx;
+        return FBS_ERR_CUDA;
+    }
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return FBS_ERR_CUDA;
+    }
+    *out = ctx;
+    return FBS_OK;
+}
+
+fbs_status fbs_destroy(fbs_ctx* ctx)
+{
+    if (!ctx) return FBS_OK;
+    DeviceGuard g(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto& r : ctx->recs) {
+        cudaEventSynchronize(r.b);
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : ctx->spare) cudaEventDestroy(e);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->io) cudaFree(ctx->io);
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return FBS_OK;
+}
+
+fbs_status fbs_set_options(fbs_ctx* ctx, const fbs_options* opt)
+{
+    if (!ctx || !opt) return fail(ctx, FBS_ERR_INVALID_ARG, "null context or options");
+    fbs_status s = check_options(ctx, opt);
+    if (s != FBS_OK) return s;
+    ctx->opt = *opt;
+    return FBS_OK;
+}
+
+fbs_status fbs_sync(fbs_ctx* ctx)
+{
+    if (!ctx) return FBS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pending error");
+    return FBS_OK;
+}
+
+const char* fbs_last_error(const fbs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+fbs_status fbs_profile(fbs_ctx* ctx, int enable)
+{
+    if (!ctx) return FBS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (enable) {
+        for (auto& r : ctx->recs) {
+            cudaEventSynchronize(r.b);
+            ctx->spare.push_back(r.a);
+            ctx->spare.push_back(r.b);
+        }
+        ctx->recs.clear();
+        for (auto& n : ctx->launches) n = 0;
+    }
+    ctx->profiling = enable != 0;
+    return FBS_OK;
+}
+
+fbs_status fbs_profile_read(fbs_ctx* ctx, int kind, double* total_ms, long long* launches)
+{
+    if (!ctx || kind < 0 || kind >= FBS_KERNEL_KINDS) return fail(ctx, FBS_ERR_INVALID_ARG, "bad kernel kind");
+    DeviceGuard g(ctx->device);
+    double t = 0.0;
+    for (auto& r : ctx->recs) {
+        if (r.kind != kind) continue;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "profile event");
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "profile elapsed time");
+        t += ms;
+    }
+    if (total_ms) *total_ms = t;
+    if (launches) *launches = ctx->launches[kind];
+    return FBS_OK;
+}
+
+fbs_status fbs_compute_disparity(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W,
+                                 int C, int D, int radius, float sigma_s, float sigma_r, float tau,
+                                 int32_t* disp_int, float* disp_subpix, void* cuda_stream)
+{
+    if (!ctx) return FBS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!left || !right) return fail(ctx, FBS_ERR_INVALID_ARG, "null image pointer");
+    if (!disp_int && !disp_subpix) return fail(ctx, FBS_ERR_INVALID_ARG, "both outputs are NULL");
+    fbs_status s = check_shape(ctx, H, W, C, D);
+    if (s == FBS_OK) s = check_agg_params(ctx, radius, sigma_s, sigma_r);
+    if (s == FBS_OK) s = check_tau(ctx, tau);
+    if (s != FBS_OK) return s;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, FBS_ERR_CUDA, "cannot select device %d", ctx->device);
+    return run_path(ctx, left, right, H, W, C, D, radius, sigma_s, sigma_r, tau, disp_int, disp_subpix,
+                    pick_stream(ctx, cuda_stream));
+}
+
+fbs_status fbs_compute_disparity_host(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W,
+                                      int C, int D, int radius, float sigma_s, float sigma_r, float tau,
+                                      int32_t* disp_int, float* disp_subpix)
+{
+    if (!ctx) return FBS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!left || !right) return fail(ctx, FBS_ERR_INVALID_ARG, "null image pointer");
+    if (!disp_int && !disp_subpix) return fail(ctx, FBS_ERR_INVALID_ARG, "both outputs are NULL");
+    fbs_status s = check_shape(ctx, H, W, C, D);
+    if (s == FBS_OK) s = check_agg_params(ctx, radius, sigma_s, sigma_r);
+    if (s == FBS_OK) s = check_tau(ctx, tau);
+    if (s != FBS_OK) return s;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, FBS_ERR_CUDA, "cannot select device %d", ctx->device);
+    const size_t npx = (size_t)H * W;
+    const size_t img = npx * C;
+    const size_t img_al = (img + 255) & ~(size_t)255;
+    const size_t out_al = (npx * 4 + 255) & ~(size_t)255;
+    s = ensure(ctx, &ctx->io, &ctx->io_bytes, 2 * img_al + 2 * out_al, "host-path staging");
+    if (s != FBS_OK) return s;
+    uint8_t* dl = (uint8_t*)ctx->io;
+    uint8_t* dr = dl + img_al;
+    int32_t* di = (int32_t*)(dr + img_al);
+    float* dsub = (float*)((uint8_t*)di + out_al);
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaMemcpyAsync(dl, left, img, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dr, right, img, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "host-to-device copy");
+    s = run_path(ctx, dl, dr, H, W, C, D, radius, sigma_s, sigma_r, tau, disp_int ? di : nullptr,
+                 disp_subpix ? dsub : nullptr, st);
+    if (s != FBS_OK) return s;
+    if (disp_int) e = cudaMemcpyAsync(disp_int, di, npx * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && disp_subpix) e = cudaMemcpyAsync(disp_subpix, dsub, npx * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device-to-host copy");
+    return FBS_OK;
+}
+
+fbs_status fbs_cost_volume(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C,
+                           int D, float tau, float* cost_out, void* cuda_stream)
+{
+    if (!ctx) return FBS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!left || !right || !cost_out) return fail(ctx, FBS_ERR_INVALID_ARG, "null pointer");
+    fbs_status s = check_shape(ctx, H, W, C, D);
+    if (s == FBS_OK) s = check_tau(ctx, tau);
+    if (s != FBS_OK) return s;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, FBS_ERR_CUDA, "cannot select device %d", ctx->device);
+    cudaStream_t st = pick_stream(ctx, cuda_stream);
+    cudaError_t e;
+    {
+        LaunchScope ls(ctx, FBS_KERNEL_COST, st);
+        e = fbs::launch_cost_build(left, right, H, W, C, D, D, ctx->opt.cost, tau, cost_out, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cost build launch");
+    return FBS_OK;
+}
+
+fbs_status fbs_aggregate(fbs_ctx* ctx, const float* cost, const uint8_t* guide, int H, int W, int C, int D,
+                         int radius, float sigma_s, float sigma_r, float* agg_out, int32_t* disp_int,
+                         float* disp_subpix, void* cuda_stream)
+{
+    if (!ctx) return FBS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!cost || !guide) return fail(ctx, FBS_ERR_INVALID_ARG, "null pointer");
+    if (!agg_out && !disp_int && !disp_subpix) return fail(ctx, FBS_ERR_INVALID_ARG, "all outputs are NULL");
+    fbs_status s = check_shape(ctx, H, W, C, D);
+    if (s == FBS_OK) s = check_agg_params(ctx, radius, sigma_s, sigma_r);
+    if (s != FBS_OK) return s;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, FBS_ERR_CUDA, "cannot select device %d", ctx->device);
+    if (ctx->opt.prec != FBS_PREC_F32)
+        return fail(ctx, FBS_ERR_UNSUPPORTED, "precision %d is not built in this library", ctx->opt.prec);
+    cudaStream_t st = pick_stream(ctx, cuda_stream);
+    cudaError_t e;
+    {
+        LaunchScope ls(ctx, FBS_KERNEL_AGG_F32, st);
+        e = fbs::launch_aggregate_f32(cost, D, guide, H, W, C, D, radius, sigma_s, sigma_r, agg_out, disp_int,
+                                      disp_subpix, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "aggregation launch");
+    return FBS_OK;
+}
+
+}  // extern "C"

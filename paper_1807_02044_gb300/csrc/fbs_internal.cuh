@@ -1,0 +1,26 @@
+// Internal declarations shared by the translation units of libfbs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fbs {
+
+// Cost volume rows are padded to a multiple of 4 floats so that one pixel's
+// disparity vector starts on a 16-byte boundary (vector loads, TMA, cp.async).
+inline int padded_ld(int D) { return (D + 3) & ~3; }
+
+// ---- step 1: matching cost, Eq. (1)-(3) or TAD -------------------------------
+// cost[(y*W + x)*ld + d] for d < D; entries D <= d < ld are written as 0.
+cudaError_t launch_cost_build(const uint8_t* left, const uint8_t* right, int H, int W, int C,
+                              int D, int ld, int mode, float tau, float* cost,
+                              cudaStream_t stream);
+
+// ---- steps 2-4 in FP32: Eq. (6)-(8), WTA, Eq. (10) ----------------------------
+// agg_out (nullable) is written with row pitch D (caller layout [H][W][D]).
+cudaError_t launch_aggregate_f32(const float* cost, int ld, const uint8_t* guide, int H, int W,
+                                 int C, int D, int radius, float sigma_s, float sigma_r,
+                                 float* agg_out, int32_t* disp_int, float* disp_sub,
+                                 cudaStream_t stream);
+
+}  // namespace fbs
