@@ -132,6 +132,44 @@ fbs_status fbs_aggregate(fbs_ctx *ctx, const float *cost, const uint8_t *guide,
                          void *cuda_stream);
 
 /*
+ * fbs_compute_disparity_noalloc -- the whole path without allocating device
+ * memory.  The paper has no counterpart: this is an interface variant for
+ * callers that cannot call cudaMalloc once they run, such as a plugin inside
+ * a host application that owns all device memory through its own allocator,
+ * or a real-time loop whose memory budget is fixed at start-up and which may
+ * not take an allocation (or the synchronisation cudaMalloc/cudaFree can
+ * imply) in the middle of processing.
+ *
+ * Arguments and results are those of fbs_compute_disparity (FP32 precision
+ * only; the context supplies the cost mode, the default stream and the error
+ * message).  The context's scratch is not used: the cost volume is kept in one
+ * file-scope device array of FBS_NOALLOC_MAX_COST_BYTES bytes that is part of
+ * the library's device code, so every GPU that loads it holds the array until
+ * the process exits (with CUDA's default lazy module loading, from the first
+ * call of this entry point on that GPU).
+ *   - Limit: H * W * round_up(D, 4) * 4 <= FBS_NOALLOC_MAX_COST_BYTES, e.g.
+ *     640x480 with D <= 24 or 320x240 with D <= 108.  Larger requests return
+ *     FBS_ERR_INVALID_ARG with the sizes in fbs_last_error() and launch
+ *     nothing.
+ *   - Set-up: the first call on each device looks up the array's device
+ *     address (cudaGetSymbolAddress; no allocation) and caches it.  Make that
+ *     first call before any stream capture.
+ *   - Sharing: all calls on a device use the same array, which keeps the last
+ *     call's contents.  Nothing in it has to start at zero: each call writes
+ *     every element it later reads.  Calls whose kernels overlap on the GPU
+ *     (different streams or host threads) race on the array; issue them on
+ *     one stream.
+ *   - The entry point calls no cudaMalloc, cudaFree or allocating library
+ *     routine.
+ */
+#define FBS_NOALLOC_MAX_COST_BYTES (32u * 1024u * 1024u)
+
+fbs_status fbs_compute_disparity_noalloc(fbs_ctx *ctx, const uint8_t *left, const uint8_t *right,
+                                         int H, int W, int C, int D, int radius,
+                                         float sigma_s, float sigma_r, float tau,
+                                         int32_t *disp_int, float *disp_subpix, void *cuda_stream);
+
+/*
  * Kernel accounting (not a step of the method).  The context counts every
  * kernel it launches, per kind.  With profiling enabled it also brackets each
  * launch with a CUDA event pair recorded on the launch stream, so the device

@@ -64,6 +64,7 @@ SIGNATURES = {
     "fbs_compute_disparity_host": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _F, _P, _P]),
     "fbs_cost_volume": (_I, [_P, _P, _P, _I, _I, _I, _I, _F, _P, _P]),
     "fbs_aggregate": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _P, _P, _P, _P]),
+    "fbs_compute_disparity_noalloc": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _F, _P, _P, _P]),
     "fbs_profile": (_I, [_P, _I]),
     "fbs_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
 }
@@ -176,6 +177,19 @@ def fbs_compute_disparity_host(ctx, left, right, H, W, C, D, radius, sigma_s, si
                                disp_subpix):
     _check(ctx, lib().fbs_compute_disparity_host(ctx, _addr(left), _addr(right), H, W, C, D, radius, sigma_s,
                                                 sigma_r, tau, _addr(disp_int), _addr(disp_subpix)))
+
+
+FBS_NOALLOC_MAX_COST_BYTES = 32 * 1024 * 1024
+
+
+def fbs_compute_disparity_noalloc(ctx, left, right, H, W, C, D, radius, sigma_s, sigma_r, tau, disp_int,
+                                  disp_subpix, stream=None):
+    """fbs_compute_disparity without device allocation: the cost volume goes to
+    the library's fixed static scratch (H*W*round_up(D,4)*4 bytes at most
+    FBS_NOALLOC_MAX_COST_BYTES)."""
+    _check(ctx, lib().fbs_compute_disparity_noalloc(ctx, _addr(left), _addr(right), H, W, C, D, radius, sigma_s,
+                                                    sigma_r, tau, _addr(disp_int), _addr(disp_subpix),
+                                                    _stream(stream)))
 
 
 def fbs_cost_volume(ctx, left, right, H, W, C, D, tau, cost_out, stream=None):

@@ -201,6 +201,29 @@ fbs_status run_path(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int
 
 }  // namespace
 
+namespace fbs {
+
+fbs_status check_path_args(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C, int D,
+                           int radius, float sigma_s, float sigma_r, float tau, const int32_t* disp_int,
+                           const float* disp_subpix)
+{
+    if (!left || !right) return fail(ctx, FBS_ERR_INVALID_ARG, "null image pointer");
+    if (!disp_int && !disp_subpix) return fail(ctx, FBS_ERR_INVALID_ARG, "both outputs are NULL");
+    fbs_status s = check_shape(ctx, H, W, C, D);
+    if (s == FBS_OK) s = check_agg_params(ctx, radius, sigma_s, sigma_r);
+    if (s == FBS_OK) s = check_tau(ctx, tau);
+    return s;
+}
+
+int ctx_device(const fbs_ctx* ctx) { return ctx->device; }
+int ctx_cost_mode(const fbs_ctx* ctx) { return ctx->opt.cost; }
+int ctx_precision(const fbs_ctx* ctx) { return ctx->opt.prec; }
+cudaStream_t ctx_stream(fbs_ctx* ctx, void* cuda_stream) { return pick_stream(ctx, cuda_stream); }
+fbs_status ctx_error(fbs_ctx* ctx, fbs_status st, const char* msg) { return fail(ctx, st, "%s", msg); }
+void ctx_count_launch(fbs_ctx* ctx, int kind) { ctx->launches[kind]++; }
+
+}  // namespace fbs
+
 extern "C" {
 
 void fbs_default_options(fbs_options* opt)

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/fbs.h"
+
 namespace fbs {
 
 // Cost volume rows are padded to a multiple of 4 floats so that one pixel's
@@ -22,5 +24,17 @@ cudaError_t launch_aggregate_f32(const float* cost, int ld, const uint8_t* guide
                                  int C, int D, int radius, float sigma_s, float sigma_r,
                                  float* agg_out, int32_t* disp_int, float* disp_sub,
                                  cudaStream_t stream);
+
+// ---- context helpers for entry points defined outside fbs_api.cu -------------
+// Host-side checks of fbs_compute_disparity's arguments (sets the message).
+fbs_status check_path_args(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C,
+                           int D, int radius, float sigma_s, float sigma_r, float tau,
+                           const int32_t* disp_int, const float* disp_subpix);
+int ctx_device(const fbs_ctx* ctx);
+int ctx_cost_mode(const fbs_ctx* ctx);
+int ctx_precision(const fbs_ctx* ctx);
+cudaStream_t ctx_stream(fbs_ctx* ctx, void* cuda_stream);
+fbs_status ctx_error(fbs_ctx* ctx, fbs_status st, const char* msg);
+void ctx_count_launch(fbs_ctx* ctx, int kind);
 
 }  // namespace fbs
