@@ -142,15 +142,17 @@ fbs_status fbs_aggregate(fbs_ctx *ctx, const float *cost, const uint8_t *guide,
  *
  * Arguments and results are those of fbs_compute_disparity (FP32 precision
  * only; the context supplies the cost mode, the default stream and the error
- * message).  The context's scratch is not used: the cost volume is kept in one
- * file-scope device array of FBS_NOALLOC_MAX_COST_BYTES bytes that is part of
- * the library's device code, so every GPU that loads it holds the array until
- * the process exits (with CUDA's default lazy module loading, from the first
- * call of this entry point on that GPU).
- *   - Limit: H * W * round_up(D, 4) * 4 <= FBS_NOALLOC_MAX_COST_BYTES, e.g.
- *     640x480 with D <= 24 or 320x240 with D <= 108.  Larger requests return
- *     FBS_ERR_INVALID_ARG with the sizes in fbs_last_error() and launch
- *     nothing.
+ * message).  The context's scratch is not used: the per-pixel block
+ * statistics and the cost volume are kept in one file-scope device array of
+ * FBS_NOALLOC_MAX_COST_BYTES bytes that is part of the library's device code,
+ * so every GPU that loads it holds the array until the process exits (with
+ * CUDA's default lazy module loading, from the first call of this entry point
+ * on that GPU).
+ *   - Limit: about H * W * (4 * round_up(D, 4) + 20) bytes (block statistics
+ *     plus cost volume, each rounded up to 256 bytes) must fit in
+ *     FBS_NOALLOC_MAX_COST_BYTES, e.g. 640x480 with D <= 20 or 320x240 with
+ *     D <= 100.  Larger requests return FBS_ERR_INVALID_ARG with the sizes in
+ *     fbs_last_error() and launch nothing.
  *   - Set-up: the first call on each device looks up the array's device
  *     address (cudaGetSymbolAddress; no allocation) and caches it.  Make that
  *     first call before any stream capture.

@@ -22,6 +22,8 @@ struct fbs_ctx {
     void* io = nullptr;          // device staging for the host-buffer entry point
     size_t io_bytes = 0;
     std::string err;
+    int num_sms = 0;
+    int* derr = nullptr;         // device error word written by kernels with bounded waits
     // kernel accounting
     long long launches[FBS_KERNEL_KINDS] = {0, 0, 0, 0};
     bool profiling = false;
@@ -173,21 +175,56 @@ fbs_status ensure(fbs_ctx* ctx, void** buf, size_t* have, size_t need, const cha
     return FBS_OK;
 }
 
+int round_up_int(int v, int a) { return (v + a - 1) / a * a; }
+
+// Tensor-core form: 16-bit planar cost volume, tcgen05 aggregation.
+fbs_status run_path_tc(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C, int D,
+                       int radius, float sigma_s, float sigma_r, float tau, int32_t* disp_int, float* disp_subpix,
+                       cudaStream_t st)
+{
+    if (!fbs::tc_supported(D, radius))
+        return fail(ctx, FBS_ERR_UNSUPPORTED, "tensor-core aggregation supports D <= 256 and radius <= 24 (got D=%d, radius=%d)",
+                    D, radius);
+    const bool bf16 = ctx->opt.prec == FBS_PREC_BF16;
+    const int wp = round_up_int(W, 8);
+    const size_t stats = fbs::cost_scratch_bytes(H, W);
+    const size_t need = stats + (size_t)2 * H * D * wp;
+    fbs_status s = ensure(ctx, &ctx->ws, &ctx->ws_bytes, need, "cost volume");
+    if (s != FBS_OK) return s;
+    const fbs::CostScratch sc = fbs::carve_cost_scratch(ctx->ws, H, W);
+    void* cost = (uint8_t*)ctx->ws + stats;
+    cudaError_t e;
+    {
+        LaunchScope ls(ctx, FBS_KERNEL_COST, st);
+        e = fbs::launch_cost_build_planar16(sc, left, right, H, W, C, D, wp, ctx->opt.cost, tau, bf16, cost, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cost build launch");
+    {
+        LaunchScope ls(ctx, FBS_KERNEL_AGG_TC, st);
+        e = fbs::launch_aggregate_tc(cost, wp, left, H, W, C, D, radius, sigma_s, sigma_r, bf16, nullptr, disp_int,
+                                     disp_subpix, ctx->derr, ctx->num_sms, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core aggregation launch");
+    return FBS_OK;
+}
+
 fbs_status run_path(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C, int D,
                     int radius, float sigma_s, float sigma_r, float tau, int32_t* disp_int,
                     float* disp_subpix, cudaStream_t st)
 {
+    if (ctx->opt.prec != FBS_PREC_F32)
+        return run_path_tc(ctx, left, right, H, W, C, D, radius, sigma_s, sigma_r, tau, disp_int, disp_subpix, st);
     const int ld = fbs::padded_ld(D);
-    const size_t need = sizeof(float) * (size_t)H * W * ld;
+    const size_t stats = fbs::cost_scratch_bytes(H, W);
+    const size_t need = stats + sizeof(float) * (size_t)H * W * ld;
     fbs_status s = ensure(ctx, &ctx->ws, &ctx->ws_bytes, need, "cost volume");
     if (s != FBS_OK) return s;
-    float* cost = (float*)ctx->ws;
-    if (ctx->opt.prec != FBS_PREC_F32)
-        return fail(ctx, FBS_ERR_UNSUPPORTED, "precision %d is not built in this library", ctx->opt.prec);
+    const fbs::CostScratch sc = fbs::carve_cost_scratch(ctx->ws, H, W);
+    float* cost = (float*)((uint8_t*)ctx->ws + stats);
     cudaError_t e;
     {
         LaunchScope ls(ctx, FBS_KERNEL_COST, st);
-        e = fbs::launch_cost_build(left, right, H, W, C, D, ld, ctx->opt.cost, tau, cost, st);
+        e = fbs::launch_cost_build(sc, left, right, H, W, C, D, ld, ctx->opt.cost, tau, cost, st);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cost build launch");
     {
@@ -266,6 +303,14 @@ fbs_status fbs_create(fbs_ctx** out, const fbs_options* opt, int device)
         delete ctx;
         return FBS_ERR_CUDA;
     }
+    if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMalloc(&ctx->derr, sizeof(int)) != cudaSuccess || cudaMemset(ctx->derr, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->derr) cudaFree(ctx->derr);
+        cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return FBS_ERR_CUDA;
+    }
     *out = ctx;
     return FBS_OK;
 }
@@ -283,6 +328,7 @@ fbs_status fbs_destroy(fbs_ctx* ctx)
     for (auto e : ctx->spare) cudaEventDestroy(e);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->io) cudaFree(ctx->io);
+    if (ctx->derr) cudaFree(ctx->derr);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return FBS_OK;
@@ -305,6 +351,13 @@ fbs_status fbs_sync(fbs_ctx* ctx)
     if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pending error");
+    int word = 0;
+    e = cudaMemcpy(&word, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "read kernel error word");
+    if (word != 0) {
+        cudaMemset(ctx->derr, 0, sizeof(int));
+        return fail(ctx, FBS_ERR_TIMEOUT, "a bounded wait inside a kernel gave up (code %d); its outputs are invalid", word);
+    }
     return FBS_OK;
 }
 
@@ -413,11 +466,14 @@ fbs_status fbs_cost_volume(fbs_ctx* ctx, const uint8_t* left, const uint8_t* rig
     if (s != FBS_OK) return s;
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(ctx, FBS_ERR_CUDA, "cannot select device %d", ctx->device);
+    fbs_status s2 = ensure(ctx, &ctx->ws, &ctx->ws_bytes, fbs::cost_scratch_bytes(H, W), "cost statistics");
+    if (s2 != FBS_OK) return s2;
+    const fbs::CostScratch sc = fbs::carve_cost_scratch(ctx->ws, H, W);
     cudaStream_t st = pick_stream(ctx, cuda_stream);
     cudaError_t e;
     {
         LaunchScope ls(ctx, FBS_KERNEL_COST, st);
-        e = fbs::launch_cost_build(left, right, H, W, C, D, D, ctx->opt.cost, tau, cost_out, st);
+        e = fbs::launch_cost_build(sc, left, right, H, W, C, D, D, ctx->opt.cost, tau, cost_out, st);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cost build launch");
     return FBS_OK;
@@ -436,10 +492,28 @@ fbs_status fbs_aggregate(fbs_ctx* ctx, const float* cost, const uint8_t* guide, 
     if (s != FBS_OK) return s;
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(ctx, FBS_ERR_CUDA, "cannot select device %d", ctx->device);
-    if (ctx->opt.prec != FBS_PREC_F32)
-        return fail(ctx, FBS_ERR_UNSUPPORTED, "precision %d is not built in this library", ctx->opt.prec);
     cudaStream_t st = pick_stream(ctx, cuda_stream);
     cudaError_t e;
+    if (ctx->opt.prec != FBS_PREC_F32) {
+        if (!fbs::tc_supported(D, radius))
+            return fail(ctx, FBS_ERR_UNSUPPORTED, "tensor-core aggregation supports D <= 256 and radius <= 24");
+        const bool bf16 = ctx->opt.prec == FBS_PREC_BF16;
+        const int wp = round_up_int(W, 8);
+        fbs_status s2 = ensure(ctx, &ctx->ws, &ctx->ws_bytes, (size_t)2 * H * D * wp, "16-bit cost copy");
+        if (s2 != FBS_OK) return s2;
+        {
+            LaunchScope ls(ctx, FBS_KERNEL_OTHER, st);
+            e = fbs::launch_hwd_to_planar16(cost, H, W, D, wp, bf16, ctx->ws, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cost conversion launch");
+        {
+            LaunchScope ls(ctx, FBS_KERNEL_AGG_TC, st);
+            e = fbs::launch_aggregate_tc(ctx->ws, wp, guide, H, W, C, D, radius, sigma_s, sigma_r, bf16, agg_out,
+                                         disp_int, disp_subpix, ctx->derr, ctx->num_sms, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core aggregation launch");
+        return FBS_OK;
+    }
     {
         LaunchScope ls(ctx, FBS_KERNEL_AGG_F32, st);
         e = fbs::launch_aggregate_f32(cost, D, guide, H, W, C, D, radius, sigma_s, sigma_r, agg_out, disp_int,

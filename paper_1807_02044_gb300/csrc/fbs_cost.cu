@@ -5,145 +5,383 @@
 // P = sum g_l g_r, Eq. (1) multiplied through by n^2 reads
 //     c = (n P - S_l S_r) / sqrt((n Q_l - S_l^2) (n Q_r - S_r^2)).
 // Every sum and both numerator terms are exact in int32 (g <= 765), so only the
-// final normalisation is rounded.  As the paper pre-computes mu and sigma and
-// keeps only the dot product per (p, d) (Sec. II-A, Sec. III), each CTA first
-// computes the block statistics of its row segment in shared memory; the
-// per-(p, d) work is the 9-term dot product.  Stored cost: C = 1 - c.
-// Boundary rules: blocks clamp to the image; u - d < 0 gives the maximum cost;
-// a block of zero variance gives c = 0.
+// final normalisation is rounded.  Stored cost: C = 1 - c.  Boundary rules:
+// blocks clamp to the image; u - d < 0 gives the maximum cost 2; a block of
+// zero variance gives c = 0.
 //
-// TAD (not in the paper): C = min(mean_c |I_l(u,v) - I_r(u-d,v)|, tau).
+// As in the paper (Sec. II-A, Sec. III) the per-pixel block statistics are
+// computed once per image by a pre-pass (grey_stats_kernel: g, S and
+// 1/sqrt(nQ - S^2)), so the per-(p, d) work is the dot product P.  In the cost
+// kernel a thread owns a run of 4 pixels and 8 consecutive disparities: the
+// left 3x6 grey window stays in registers, the right window slides by one
+// column per disparity (3 new values), the three column products per output
+// column are summed with a sliding 3-column window, and the normaliser of
+// the right block slides the same way -- about 15 instructions per (p, d).
+// Results are staged in shared memory as [d][x] and written out coalesced in
+// either layout:
+//   * [H][W][ld] float32 (D innermost; the FP32 aggregation), padding d in
+//     [D, ld) written as 0;
+//   * [H][D][Wp] 16-bit (x innermost; the tensor-core aggregation, whose B
+//     operand is K-major over window columns).
 //
-// The kernel is bound by the HBM write of the volume (4 bytes per (p, d));
-// consecutive lanes write consecutive d of one pixel, so every warp store is
-// one fully used 128-byte line.
+// TAD (not in the paper): C = min(mean_c |I_l(u,v) - I_r(u-d,v)|, tau), tau
+// when u - d < 0.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "fbs_internal.cuh"
 
 namespace fbs {
 namespace {
 
-constexpr int kCostXS = 64;        // pixels per CTA along x
-constexpr int kCostThreads = 256;  // 8 warps
+constexpr int kXS = 128;          // pixels per CTA along x
+constexpr int kDC = 64;           // disparities per pass
+constexpr int kThreads = 256;     // 32 runs of 4 pixels x 8 groups of 8 disparities
+constexpr int kStage = kXS + 1;   // staged row pitch (odd: conflict-free transposed reads)
+constexpr int kNRG = kXS + kDC + 2;        // right grey columns per pass
+constexpr int kQR = (kNRG + 3) / 4;        // de-interleaved quarter length of a right row
+constexpr int kQS = (kXS + kDC) / 4;       // same for the right block statistics
+
+// Lanes of a warp own pixel runs 4*run .. 4*run+3 and read or write column
+// 4*run + k together; storing column c at (c & 3) * quarter + (c >> 2) puts
+// those 32 accesses in 32 different banks.
+__device__ __forceinline__ int stage_pos(int x) { return (x & 3) * 32 + (x >> 2); }
+__device__ __forceinline__ int rpos(int c) { return (c & 3) * kQR + (c >> 2); }
+__device__ __forceinline__ int spos(int c) { return (c & 3) * kQS + (c >> 2); }
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-__device__ __forceinline__ int grey_at(const uint8_t* __restrict__ img, int W, int C, int x, int y)
+// Per-pixel statistics of one image: g = channel sum, S = 3x3 box sum of g
+// (clamped), rv = 1/sqrt(9 Q - S^2) or 0 for a flat block.
+__global__ void __launch_bounds__(256)
+grey_stats_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int H, int W, int C,
+                  int16_t* __restrict__ g_out, int* __restrict__ s_out, float* __restrict__ rv_out)
 {
-    const uint8_t* p = img + ((size_t)y * W + x) * C;
-    int s = p[0];
-    if (C == 3) s += p[1] + p[2];
-    return s;
+    const int img = blockIdx.z;
+    const uint8_t* src = img == 0 ? L : R;
+    const size_t plane = (size_t)H * W;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W) return;
+    int s = 0, q = 0;
+#pragma unroll
+    for (int j = -1; j <= 1; ++j) {
+        const int yy = clampi(y + j, 0, H - 1);
+#pragma unroll
+        for (int k = -1; k <= 1; ++k) {
+            const uint8_t* p = src + ((size_t)yy * W + clampi(x + k, 0, W - 1)) * C;
+            int g = p[0];
+            if (C == 3) g += p[1] + p[2];
+            s += g;
+            q += g * g;
+        }
+    }
+    const uint8_t* p = src + ((size_t)y * W + x) * C;
+    int g = p[0];
+    if (C == 3) g += p[1] + p[2];
+    const int v = 9 * q - s * s;
+    const size_t o = img * plane + (size_t)y * W + x;
+    g_out[o] = (int16_t)g;
+    s_out[o] = s;
+    rv_out[o] = v > 0 ? rsqrtf((float)v) : 0.f;
 }
 
-__global__ void __launch_bounds__(kCostThreads)
-cost_build_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int H, int W,
-                  int C, int D, int ld, int mode, float tau, float* __restrict__ cost)
+template <typename T>
+__device__ __forceinline__ T to_out(float v);
+template <>
+__device__ __forceinline__ float to_out<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half to_out<__half>(float v) { return __float2half_rn(v); }
+
+template <typename T>
+__device__ __forceinline__ void store4(T* o, const T (&v)[4])
+{
+    if (sizeof(T) == 2) {
+        ushort4 u;
+        u.x = *reinterpret_cast<const unsigned short*>(&v[0]);
+        u.y = *reinterpret_cast<const unsigned short*>(&v[1]);
+        u.z = *reinterpret_cast<const unsigned short*>(&v[2]);
+        u.w = *reinterpret_cast<const unsigned short*>(&v[3]);
+        *reinterpret_cast<ushort4*>(o) = u;
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) o[c] = v[c];
+    }
+}
+
+// MODE 0: NCC from the statistics planes; MODE 1: TAD from the raw images.
+// PLANAR false: out is [H][W][ld] (T = float); true: out is [H][D][ld] with ld = Wp.
+template <int MODE, typename T, bool PLANAR>
+__global__ void __launch_bounds__(kThreads)
+cost_kernel(const int16_t* __restrict__ gplane, const int* __restrict__ splane, const float* __restrict__ rvplane,
+            const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int H, int W, int C, int D, int ld,
+            float tau, T* __restrict__ out)
 {
     extern __shared__ int smem_i[];
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * kCostXS;
+    const int x0 = blockIdx.x * kXS;
     const int y = blockIdx.y;
-    const int nxs = min(kCostXS, W - x0);
-    // left virtual columns x0-1 .. x0+nxs, right virtual columns x0-D .. x0+nxs
-    const int nl = nxs + 2;
-    const int nr = nxs + D + 1;
-    int* gl = smem_i;                       // [3][nl]
-    int* gr = gl + 3 * nl;                  // [3][nr]
-    int* Sl = gr + 3 * nr;                  // [nxs]    left block sums at x0+i
-    float* rl = (float*)(Sl + nxs);         // [nxs]    1/sqrt(V_l), 0 if flat
-    int* Sr = (int*)(rl + nxs);             // [nr-2]   right block sums, centre index 1..nr-2
-    float* rr = (float*)(Sr + (nr - 2));    // [nr-2]
+    const int nxs = min(kXS, W - x0);
+    const size_t plane = (size_t)H * W;
+    // layout: stage [kDC][kStage] float | left grey [3][kXS+2] | right grey [3][kXS+kDC+2] |
+    //         S_l, rv_l [kXS] | S_r, rv_r [kXS+kDC]
+    float* stage = (float*)smem_i;
+    int* gl = (int*)(stage + kDC * kStage);
+    int* gr = gl + 3 * (kXS + 2);      // [3][4 * kQR], column c at rpos(c)
+    int* sl = gr + 3 * 4 * kQR;
+    float* rl = (float*)(sl + kXS);
+    int* sr = (int*)(rl + kXS);
+    float* rr = (float*)(sr + kXS + kDC);
+    uchar4* pl = (uchar4*)gl;          // TAD: raw left row [kXS]
+    uchar4* pr = pl + kXS;             // TAD: raw right row [kXS + kDC]
 
-    if (mode == 0) {
-        for (int i = tid; i < 3 * nl; i += kCostThreads) {
-            int j = i / nl, c = i - j * nl;
-            gl[i] = grey_at(L, W, C, clampi(x0 - 1 + c, 0, W - 1), clampi(y - 1 + j, 0, H - 1));
+    const int run = tid & 31;          // pixels 4*run .. 4*run+3 of the CTA
+    const int dg = tid >> 5;           // disparities dc + 8*dg .. +7
+    const int xl0 = 4 * run;
+
+    if (MODE == 0) {
+        // left grey window rows y-1..y+1, virtual columns x0-1 .. x0+kXS
+        for (int i = tid; i < 3 * (kXS + 2); i += kThreads) {
+            const int j = i / (kXS + 2), c = i - j * (kXS + 2);
+            gl[i] = gplane[(size_t)clampi(y - 1 + j, 0, H - 1) * W + clampi(x0 - 1 + c, 0, W - 1)];
         }
-        for (int i = tid; i < 3 * nr; i += kCostThreads) {
-            int j = i / nr, c = i - j * nr;
-            gr[i] = grey_at(R, W, C, clampi(x0 - D + c, 0, W - 1), clampi(y - 1 + j, 0, H - 1));
+        for (int i = tid; i < kXS; i += kThreads) {
+            const int x = clampi(x0 + i, 0, W - 1);
+            sl[i] = splane[(size_t)y * W + x];
+            rl[i] = rvplane[(size_t)y * W + x];
         }
-        __syncthreads();
-        for (int i = tid; i < nxs; i += kCostThreads) {
-            int s = 0, q = 0;
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    int g = gl[j * nl + i + k];
-                    s += g;
-                    q += g * g;
-                }
-            int v = 9 * q - s * s;
-            Sl[i] = s;
-            rl[i] = v > 0 ? rsqrtf((float)v) : 0.f;
+    } else {
+        for (int i = tid; i < kXS; i += kThreads) {
+            const uint8_t* p = L + ((size_t)y * W + clampi(x0 + i, 0, W - 1)) * C;
+            pl[i] = C == 3 ? make_uchar4(p[0], p[1], p[2], 0) : make_uchar4(p[0], 0, 0, 0);
         }
-        for (int i = tid; i < nr - 2; i += kCostThreads) {
-            int s = 0, q = 0;
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    int g = gr[j * nr + i + k];
-                    s += g;
-                    q += g * g;
-                }
-            int v = 9 * q - s * s;
-            Sr[i] = s;
-            rr[i] = v > 0 ? rsqrtf((float)v) : 0.f;
-        }
-        __syncthreads();
     }
 
-    const int warp = tid >> 5, lane = tid & 31;
-    const float inv_c = 1.f / (float)C;
-    for (int i = warp; i < nxs; i += kCostThreads / 32) {
-        const int x = x0 + i;
-        float* out = cost + ((size_t)y * W + x) * ld;
-        for (int d = lane; d < ld; d += 32) {
-            float cst;
-            if (d >= D) {
-                cst = 0.f;
-            } else if (x - d < 0) {
-                cst = mode == 0 ? 2.f : tau;
-            } else if (mode == 0) {
-                const int rc = i + D - d;   // index of the right block centre (virtual column x-d)
-                int P = 0;
+    for (int dc = 0; dc < D; dc += kDC) {
+        // right columns for this pass: virtual columns rb .. rb + NRG - 1 with
+        // rb = x0 - dc - kDC - 1; the right block of (x, d) spans x-d-1 .. x-d+1
+        const int rb = x0 - dc - kDC - 1;
+        if (MODE == 0) {
+            for (int i = tid; i < 3 * kNRG; i += kThreads) {
+                const int j = i / kNRG, c = i - j * kNRG;
+                gr[j * 4 * kQR + rpos(c)] =
+                    gplane[plane + (size_t)clampi(y - 1 + j, 0, H - 1) * W + clampi(rb + c, 0, W - 1)];
+            }
+            // right block centres rb+1 .. rb+kXS+kDC
+            for (int i = tid; i < kXS + kDC; i += kThreads) {
+                const int x = clampi(rb + 1 + i, 0, W - 1);
+                sr[spos(i)] = splane[plane + (size_t)y * W + x];
+                rr[spos(i)] = rvplane[plane + (size_t)y * W + x];
+            }
+        } else {
+            for (int i = tid; i < kXS + kDC; i += kThreads) {
+                const uint8_t* p = R + ((size_t)y * W + clampi(rb + 1 + i, 0, W - 1)) * C;
+                pr[i] = C == 3 ? make_uchar4(p[0], p[1], p[2], 0) : make_uchar4(p[0], 0, 0, 0);
+            }
+        }
+        __syncthreads();
+
+        const int d_first = dc + 8 * dg;
+        if (MODE == 0) {
+            int glw[3][6];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int c = 0; c < 6; ++c) glw[j][c] = gl[j * (kXS + 2) + xl0 + c];
+            int sli[4];
+            float rli[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                sli[i] = sl[xl0 + i];
+                rli[i] = rl[xl0 + i];
+            }
+            // right window for d_first: virtual columns x0+xl0-d-1 .. +4, index (col - rb)
+            int grw[3][6];
+            int srw[4];
+            float rrw[4];
+            {
+                const int base = x0 + xl0 - d_first - 1 - rb;
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) P += gl[j * nl + i + k] * gr[j * nr + rc - 1 + k];
-                const int num = 9 * P - Sl[i] * Sr[rc - 1];
-                const float c = (float)num * (rl[i] * rr[rc - 1]);
-                cst = 1.f - c;
-            } else {
-                const uint8_t* pl = L + ((size_t)y * W + x) * C;
-                const uint8_t* pr = R + ((size_t)y * W + (x - d)) * C;
-                int s = 0;
-                for (int c = 0; c < C; ++c) s += abs((int)pl[c] - (int)pr[c]);
-                cst = fminf((float)s * inv_c, tau);
+                    for (int c = 0; c < 6; ++c) grw[j][c] = gr[j * 4 * kQR + rpos(base + c)];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    srw[i] = sr[spos(base + i)];
+                    rrw[i] = rr[spos(base + i)];
+                }
             }
-            out[d] = cst;
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const int d = d_first + s;
+                if (s > 0) {
+                    // slide one column to the left: d grew by one
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+#pragma unroll
+                        for (int c = 5; c > 0; --c) grw[j][c] = grw[j][c - 1];
+                    }
+                    const int base = x0 + xl0 - d - 1 - rb;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) grw[j][0] = gr[j * 4 * kQR + rpos(base)];
+#pragma unroll
+                    for (int i = 3; i > 0; --i) {
+                        srw[i] = srw[i - 1];
+                        rrw[i] = rrw[i - 1];
+                    }
+                    srw[0] = sr[spos(base)];
+                    rrw[0] = rr[spos(base)];
+                }
+                int cp[6];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) cp[c] = glw[0][c] * grw[0][c] + glw[1][c] * grw[1][c] + glw[2][c] * grw[2][c];
+                int P = cp[0] + cp[1] + cp[2];
+                float* st = stage + (d - dc) * kStage + run;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (i > 0) P += cp[i + 2] - cp[i - 1];
+                    const int x = x0 + xl0 + i;
+                    float cst;
+                    if (x - d < 0) {
+                        cst = 2.f;
+                    } else {
+                        const int num = 9 * P - sli[i] * srw[i];
+                        cst = 1.f - (float)num * (rli[i] * rrw[i]);
+                    }
+                    st[32 * i] = cst;
+                }
+            }
+        } else {
+            const float inv_c = 1.f / (float)C;
+#pragma unroll 2
+            for (int s = 0; s < 8; ++s) {
+                const int d = d_first + s;
+                float* st = stage + (d - dc) * kStage + run;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int x = x0 + xl0 + i;
+                    float cst = tau;
+                    if (x - d >= 0) {
+                        const uchar4 a = pl[xl0 + i];
+                        const uchar4 b = pr[x - d - (rb + 1)];
+                        const int sad = abs((int)a.x - (int)b.x) + abs((int)a.y - (int)b.y) + abs((int)a.z - (int)b.z);
+                        cst = fminf((float)sad * inv_c, tau);
+                    }
+                    st[32 * i] = cst;
+                }
+            }
         }
+        __syncthreads();
+
+        const int nd = min(kDC, D - dc);
+        if (PLANAR) {
+            // out[(y*D + d)*ld + x]: a thread stores pixels 4g..4g+3 of one row
+            for (int i = tid; i < nd * (kXS / 4); i += kThreads) {
+                const int dd = i >> 5, g = i & 31;
+                const float* sp = stage + dd * kStage + g;
+                T v[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v[c] = to_out<T>(sp[32 * c]);
+                T* o = out + ((size_t)y * D + dc + dd) * ld + x0 + 4 * g;
+                if (4 * g + 3 < nxs) {
+                    store4(o, v);
+                } else {
+                    for (int c = 0; c < 4; ++c)
+                        if (4 * g + c < nxs) o[c] = v[c];
+                }
+            }
+        } else {
+            // out[(y*W + x)*ld + d]; padding d in [D, ld) of the last pass written as 0
+            const int ndw = (dc + kDC >= D) ? (ld - dc) : kDC;
+            const int warp = tid >> 5, lane = tid & 31;
+            for (int x = warp; x < nxs; x += kThreads / 32) {
+                T* o = out + ((size_t)y * W + x0 + x) * ld + dc;
+                const int px = stage_pos(x);
+                for (int dd = lane; dd < ndw; dd += 32) o[dd] = to_out<T>(dd < nd ? stage[dd * kStage + px] : 0.f);
+            }
+        }
+        __syncthreads();
     }
+}
+
+size_t cost_smem_bytes()
+{
+    return sizeof(float) * (size_t)kDC * kStage +
+           sizeof(int) * (size_t)(3 * (kXS + 2) + 3 * 4 * kQR + 2 * kXS + 2 * (kXS + kDC));
+}
+
+template <int MODE, typename T, bool PLANAR>
+cudaError_t launch_cost_kernel(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H, int W,
+                               int C, int D, int ld, float tau, T* out, cudaStream_t stream)
+{
+    const size_t smem = cost_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(cost_kernel<MODE, T, PLANAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((W + kXS - 1) / kXS, H);
+    cost_kernel<MODE, T, PLANAR><<<grid, kThreads, smem, stream>>>(sc.g, sc.s, sc.rv, left, right, H, W, C, D, ld,
+                                                                   tau, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H, int W, int C,
+                         cudaStream_t stream)
+{
+    dim3 grid((W + 255) / 256, H, 2);
+    grey_stats_kernel<<<grid, 256, 0, stream>>>(left, right, H, W, C, sc.g, sc.s, sc.rv);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_cost_build(const uint8_t* left, const uint8_t* right, int H, int W, int C,
-                              int D, int ld, int mode, float tau, float* cost, cudaStream_t stream)
+size_t cost_scratch_bytes(int H, int W)
 {
-    const int nxs = kCostXS;
-    const int nl = nxs + 2, nr = nxs + D + 1;
-    const size_t smem = sizeof(int) * (size_t)(3 * nl + 3 * nr + 2 * nxs + 2 * (nr - 2));
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(cost_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    const size_t n = (size_t)2 * H * W;
+    return ((n * sizeof(int16_t) + 255) & ~(size_t)255) + ((n * sizeof(int) + 255) & ~(size_t)255) +
+           ((n * sizeof(float) + 255) & ~(size_t)255);
+}
+
+CostScratch carve_cost_scratch(void* base, int H, int W)
+{
+    const size_t n = (size_t)2 * H * W;
+    CostScratch sc;
+    uint8_t* p = (uint8_t*)base;
+    sc.g = (int16_t*)p;
+    p += (n * sizeof(int16_t) + 255) & ~(size_t)255;
+    sc.s = (int*)p;
+    p += (n * sizeof(int) + 255) & ~(size_t)255;
+    sc.rv = (float*)p;
+    return sc;
+}
+
+cudaError_t launch_cost_build(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H, int W,
+                              int C, int D, int ld, int mode, float tau, float* cost, cudaStream_t stream)
+{
+    if (mode == 0) {
+        cudaError_t e = launch_stats(sc, left, right, H, W, C, stream);
         if (e != cudaSuccess) return e;
+        return launch_cost_kernel<0, float, false>(sc, left, right, H, W, C, D, ld, tau, cost, stream);
     }
-    dim3 grid((W + kCostXS - 1) / kCostXS, H);
-    cost_build_kernel<<<grid, kCostThreads, smem, stream>>>(left, right, H, W, C, D, ld, mode, tau, cost);
-    return cudaGetLastError();
+    return launch_cost_kernel<1, float, false>(sc, left, right, H, W, C, D, ld, tau, cost, stream);
+}
+
+cudaError_t launch_cost_build_planar16(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H,
+                                       int W, int C, int D, int wp, int mode, float tau, bool bf16, void* cost,
+                                       cudaStream_t stream)
+{
+    if (mode == 0) {
+        cudaError_t e = launch_stats(sc, left, right, H, W, C, stream);
+        if (e != cudaSuccess) return e;
+        return bf16 ? launch_cost_kernel<0, __nv_bfloat16, true>(sc, left, right, H, W, C, D, wp, tau,
+                                                                 (__nv_bfloat16*)cost, stream)
+                    : launch_cost_kernel<0, __half, true>(sc, left, right, H, W, C, D, wp, tau, (__half*)cost,
+                                                          stream);
+    }
+    return bf16 ? launch_cost_kernel<1, __nv_bfloat16, true>(sc, left, right, H, W, C, D, wp, tau,
+                                                             (__nv_bfloat16*)cost, stream)
+                : launch_cost_kernel<1, __half, true>(sc, left, right, H, W, C, D, wp, tau, (__half*)cost, stream);
 }
 
 }  // namespace fbs

@@ -13,10 +13,26 @@ namespace fbs {
 inline int padded_ld(int D) { return (D + 3) & ~3; }
 
 // ---- step 1: matching cost, Eq. (1)-(3) or TAD -------------------------------
+// Per-pixel statistics of both images (grey value, 3x3 block sum, 1/sqrt of
+// the block variance times n^2), computed by a pre-pass and read by the cost
+// kernels.  Both images: 2*H*W entries each.
+struct CostScratch {
+    int16_t* g;
+    int* s;
+    float* rv;
+};
+size_t cost_scratch_bytes(int H, int W);
+CostScratch carve_cost_scratch(void* base, int H, int W);
+
 // cost[(y*W + x)*ld + d] for d < D; entries D <= d < ld are written as 0.
-cudaError_t launch_cost_build(const uint8_t* left, const uint8_t* right, int H, int W, int C,
-                              int D, int ld, int mode, float tau, float* cost,
-                              cudaStream_t stream);
+cudaError_t launch_cost_build(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H, int W,
+                              int C, int D, int ld, int mode, float tau, float* cost, cudaStream_t stream);
+
+// 16-bit planar volume cost[(y*D + d)*wp + x] (x < W written), wp % 8 == 0;
+// bf16 selects __nv_bfloat16, otherwise __half.
+cudaError_t launch_cost_build_planar16(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H,
+                                       int W, int C, int D, int wp, int mode, float tau, bool bf16, void* cost,
+                                       cudaStream_t stream);
 
 // ---- steps 2-4 in FP32: Eq. (6)-(8), WTA, Eq. (10) ----------------------------
 // agg_out (nullable) is written with row pitch D (caller layout [H][W][D]).
@@ -24,6 +40,17 @@ cudaError_t launch_aggregate_f32(const float* cost, int ld, const uint8_t* guide
                                  int C, int D, int radius, float sigma_s, float sigma_r,
                                  float* agg_out, int32_t* disp_int, float* disp_sub,
                                  cudaStream_t stream);
+
+// ---- steps 2-4 on the tensor cores (BF16 / FP16 operands, FP32 accumulate) ---
+// cost: 16-bit planar [H][D][wp], wp % 8 == 0, 16-byte aligned.  err: device
+// int set to nonzero if a bounded wait inside the kernel gave up.
+int tc_supported(int D, int radius);
+cudaError_t launch_aggregate_tc(const void* cost, int wp, const uint8_t* guide, int H, int W, int C, int D,
+                                int radius, float sigma_s, float sigma_r, bool bf16, float* agg_out,
+                                int32_t* disp_int, float* disp_sub, int* err, int num_sms, cudaStream_t stream);
+// FP32 [H][W][D] -> 16-bit planar [H][D][wp] (rounded to nearest).
+cudaError_t launch_hwd_to_planar16(const float* in, int H, int W, int D, int wp, bool bf16, void* out,
+                                   cudaStream_t stream);
 
 // ---- context helpers for entry points defined outside fbs_api.cu -------------
 // Host-side checks of fbs_compute_disparity's arguments (sets the message).

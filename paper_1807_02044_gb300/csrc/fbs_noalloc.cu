@@ -6,8 +6,9 @@
 // which may not take the allocation (or the synchronisation that cudaMalloc
 // and cudaFree can imply) in the middle of processing.  This entry point gives
 // them the same result as fbs_compute_disparity without touching the
-// context's grow-on-demand scratch: the cost volume lives in one file-scope
-// device array of fixed size, part of the library's device code.
+// context's grow-on-demand scratch: the per-pixel block statistics and the
+// cost volume live in one file-scope device array of fixed size, part of the
+// library's device code.
 //
 // The array's name is a host-side stand-in in host code, not a device
 // address.  The first call on each device (with that device current) asks the
@@ -24,7 +25,7 @@ namespace {
 
 constexpr size_t kScratchFloats = FBS_NOALLOC_MAX_COST_BYTES / sizeof(float);
 
-// Shared by every call on a device; holds the last call's cost volume.
+// Shared by every call on a device; holds the last call's statistics and cost volume.
 static __device__ __align__(256) float g_noalloc_cost[kScratchFloats];
 
 constexpr int kMaxDevices = 64;
@@ -75,10 +76,11 @@ extern "C" fbs_status fbs_compute_disparity_noalloc(fbs_ctx* ctx, const uint8_t*
     if (fbs::ctx_precision(ctx) != FBS_PREC_F32)
         return fbs::ctx_error(ctx, FBS_ERR_UNSUPPORTED, "fbs_compute_disparity_noalloc serves FP32 precision only");
     const int ld = fbs::padded_ld(D);
-    const size_t need = sizeof(float) * (size_t)H * W * ld;
+    const size_t stats = fbs::cost_scratch_bytes(H, W);
+    const size_t need = stats + sizeof(float) * (size_t)H * W * ld;
     if (need > FBS_NOALLOC_MAX_COST_BYTES) {
-        std::string msg = "fbs_compute_disparity_noalloc: cost volume H*W*round_up(D,4)*4 = " +
-                          std::to_string(need) + " bytes exceeds the static scratch of " +
+        std::string msg = "fbs_compute_disparity_noalloc: block statistics plus cost volume need " +
+                          std::to_string(need) + " bytes, which exceeds the static scratch of " +
                           std::to_string((size_t)FBS_NOALLOC_MAX_COST_BYTES) + " bytes";
         return fbs::ctx_error(ctx, FBS_ERR_INVALID_ARG, msg.c_str());
     }
@@ -86,16 +88,19 @@ extern "C" fbs_status fbs_compute_disparity_noalloc(fbs_ctx* ctx, const uint8_t*
     if (dev < 0 || dev >= kMaxDevices) return fbs::ctx_error(ctx, FBS_ERR_UNSUPPORTED, "device ordinal too large");
     CurrentDevice guard(dev);
     if (!guard.ok) return fbs::ctx_error(ctx, FBS_ERR_CUDA, "cannot select the context's device");
-    float* cost = nullptr;
-    cudaError_t e = scratch_address(dev, &cost);
+    float* scratch = nullptr;
+    cudaError_t e = scratch_address(dev, &scratch);
     if (e != cudaSuccess) {
         std::string msg = std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e);
         return fbs::ctx_error(ctx, FBS_ERR_CUDA, msg.c_str());
     }
     cudaStream_t st = fbs::ctx_stream(ctx, cuda_stream);
-    // Every element the aggregation reads is written by the cost build first
-    // (padding lanes included), so nothing in the array needs clearing.
-    e = fbs::launch_cost_build(left, right, H, W, C, D, ld, fbs::ctx_cost_mode(ctx), tau, cost, st);
+    // [block statistics | cost volume]; every element a kernel reads is written
+    // earlier in the same call (padding lanes included), so nothing in the
+    // array needs clearing.
+    const fbs::CostScratch sc = fbs::carve_cost_scratch(scratch, H, W);
+    float* cost = (float*)((uint8_t*)scratch + stats);
+    e = fbs::launch_cost_build(sc, left, right, H, W, C, D, ld, fbs::ctx_cost_mode(ctx), tau, cost, st);
     fbs::ctx_count_launch(ctx, FBS_KERNEL_COST);
     if (e != cudaSuccess) {
         std::string msg = std::string("cost build launch: ") + cudaGetErrorString(e);

@@ -1,0 +1,108 @@
+"""Tensor-core (BF16 / FP16 operand) aggregation through the C ABI.
+
+Tolerances come from the arithmetic: with unit roundoff u of the 16-bit type
+(2^-9 for BF16, 2^-11 for FP16) applied to every cost and every weight, and
+the normaliser summed from the same rounded weights in FP32,
+    |Agg_tc - Agg| <= u max|C| + 2u max|C - Agg| / (1 - u) + FP32 terms
+                   <= 3 u R + 1e-5          (R = cost range = 2 for NCC).
+"""
+
+import numpy as np
+import pytest
+
+from tests._compare import near_tie_mask
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U = {"bf16": 2.0 ** -9, "f16": 2.0 ** -11}
+
+
+@pytest.fixture(scope="module")
+def fbs():
+    from paper_1807_02044_gb300 import build as b
+    b.build()
+    import paper_1807_02044_gb300 as m
+    return m
+
+
+def _prec(fbs, name):
+    return fbs.FBS_PREC_BF16 if name == "bf16" else fbs.FBS_PREC_F16
+
+
+def _round16(a, name):
+    t = torch.from_numpy(np.ascontiguousarray(a, np.float32))
+    return (t.to(torch.bfloat16) if name == "bf16" else t.to(torch.float16)).to(torch.float32).numpy()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+@pytest.mark.parametrize("H,W,D", [(8, 16, 16), (13, 37, 20), (24, 50, 64)])
+def test_radius_zero_returns_the_rounded_cost_exactly(fbs, prec, H, W, D):
+    """With radius 0 every pixel's only weight is 1, so the tensor-core product
+    must reproduce the 16-bit cost bit for bit: this pins the operand layouts,
+    the TMA box, the instruction descriptor and the accumulator read-out."""
+    rng = np.random.default_rng(H * W + D)
+    cost = (rng.random((H, W, D)) * 2).astype(np.float32)
+    G = rng.integers(0, 256, size=(H, W, 3)).astype(np.uint8)
+    with fbs.Context(0, prec=_prec(fbs, prec)) as ctx:
+        agg, di, ds = ctx.aggregate(_dev(cost), _dev(G), 0, 1.0, 10.0)
+        torch.cuda.synchronize()
+        fbs.fbs_sync(ctx.ctx)
+    np.testing.assert_array_equal(agg.cpu().numpy(), _round16(cost, prec))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+@pytest.mark.parametrize("H,W,C,D,r", [(16, 24, 3, 16, 2), (21, 45, 3, 40, 7), (9, 70, 1, 64, 4), (30, 33, 3, 100, 9)])
+def test_tc_aggregation_within_rounding_bound(fbs, oracle_mod, prec, H, W, C, D, r):
+    rng = np.random.default_rng(7 * H + W)
+    L = rng.integers(0, 256, size=(H, W, C)).astype(np.uint8)
+    R = np.roll(L, -3, axis=1)
+    with fbs.Context(0, prec=_prec(fbs, prec)) as ctx:
+        dl, dr = _dev(L), _dev(R)
+        cost = ctx.cost_volume(dl, dr, D)
+        agg, di, ds = ctx.aggregate(cost, dl, r, float(r), 12.0)
+        di2, ds2 = ctx.compute_disparity(dl, dr, D, r, float(r), 12.0)
+        torch.cuda.synchronize()
+        fbs.fbs_sync(ctx.ctx)
+    ref_di, ref_ds, ref_agg = oracle_mod.fbs(L, R, D, r, float(r), 12.0, want_agg=True)
+    err = np.abs(agg.cpu().numpy() - ref_agg).max()
+    tol = 3 * U[prec] * 2.0 + 1e-5
+    assert err <= tol, f"max |dAgg| {err:.3e} > {tol:.3e}"
+    # integer winners agree except where the oracle's two best are within 2*tol
+    di = di.cpu().numpy()
+    ties = near_tie_mask(ref_agg, 2 * tol)
+    assert np.all((di == ref_di) | ties)
+    # the production entry point (16-bit cost built directly) agrees with the
+    # debug route (FP32 cost rounded by the conversion kernel): same rounding
+    assert np.array_equal(di, di2.cpu().numpy())
+    np.testing.assert_allclose(ds.cpu().numpy(), ds2.cpu().numpy(), atol=1e-6)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_tc_full_size_bench_workload_bad_pixels(fbs, oracle_mod, prec):
+    """640x480 RGB, D=64, radius 7: extra bad pixels (>1 px from the oracle)
+    of the 16-bit form over the FP32 form stay at or below 0.5%, and sampled
+    aggregated costs stay within the rounding bound."""
+    from synth import make_pair
+    p = make_pair("rgb640x480_d64_r7", 0)
+    dl, dr = _dev(p.left), _dev(p.right)
+    out = {}
+    for name, pr in [("f32", fbs.FBS_PREC_F32), (prec, _prec(fbs, prec))]:
+        with fbs.Context(0, prec=pr) as ctx:
+            di, ds = ctx.compute_disparity(dl, dr, p.D, p.radius, p.sigma_s, p.sigma_r, p.tau)
+            torch.cuda.synchronize()
+            fbs.fbs_sync(ctx.ctx)
+            out[name] = ds.cpu().numpy()
+    rng = np.random.default_rng(1)
+    ys = rng.integers(0, p.H, 400)
+    xs = rng.integers(0, p.W, 400)
+    ref_di, ref_ds, ref_agg = oracle_mod.fbs_points(p.left, p.right, p.D, p.radius, p.sigma_s, p.sigma_r, xs, ys)
+    bad32 = np.mean(np.abs(out["f32"][ys, xs] - ref_ds) > 1.0)
+    bad16 = np.mean(np.abs(out[prec][ys, xs] - ref_ds) > 1.0)
+    assert bad16 - bad32 <= 0.005, (bad32, bad16)
+    # whole frame against the FP32 path
+    assert np.mean(np.abs(out[prec] - out["f32"]) > 1.0) <= 0.005
