@@ -4,6 +4,11 @@
 A step is one stereo pair through the whole path (cost volume, bilateral
 aggregation of every disparity slice, WTA, Eq. (10) refinement) via the C ABI
 entry point fbs_compute_disparity, with the pair already resident in HBM.
+Three forms are timed on the same pair: plain FP32, and the tensor-core form
+with BF16 and with FP16 operands (FP32 accumulation).  The headline value is
+the BF16 form (--prec selects another); every form's Gtaps/s, fps and extra
+bad-pixel rate (>1 px against the FP32 form on the whole frame, and against
+the FP64 oracle on 300 sampled pixels) are in "forms".
 The workload is the 640x480 RGB pair with D = 64, radius 7 (15x15 window),
 sigma_s = 7, sigma_r = 12, rendered by the seeded synthetic scene generator
 (fractal texture, slanted planes, occlusions).  The metric is aggregated
@@ -53,7 +58,10 @@ def _args():
     ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--prec", default="f32", choices=["f32"])
+    ap.add_argument("--prec", default="bf16", choices=["f32", "bf16", "f16"],
+                    help="the form reported as the headline value; all three forms are timed unless --only-form")
+    ap.add_argument("--only-form", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--cost", default="ncc", choices=["ncc", "tad"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -221,6 +229,47 @@ def _traffic_for(kernel_file, kernel_name):
     return ent.get("dram_bytes_per_launch_full_size")
 
 
+FORM_PREC = {"f32": 0, "bf16": 1, "f16": 2}
+
+
+def _time_form(fbs, torch, p, form, mode, dev, stream, dl, dr, flush, steps, warmup, dist):
+    """Warm up, then time exactly `steps` steps of one form; per-step CUDA events
+    on the launch stream, the L2 flush outside them."""
+    ctx = fbs.Context(dev.index, cost=mode, prec=FORM_PREC[form])
+    di = torch.empty((p.H, p.W), dtype=torch.int32, device=dev)
+    ds = torch.empty((p.H, p.W), dtype=torch.float32, device=dev)
+    call = lambda: fbs.fbs_compute_disparity(ctx.ctx, dl, dr, p.H, p.W, p.C, p.D, p.radius, p.sigma_s, p.sigma_r,
+                                             p.tau, di, ds, stream)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            flush.fill_(1)
+            call()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        fbs.fbs_profile(ctx.ctx, 1)
+        t0 = time.time()
+        for a, b in evs:
+            flush.fill_(1)
+            a.record(stream)
+            call()
+            b.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t1 = time.time()
+        fbs.fbs_profile(ctx.ctx, 0)
+    fbs.fbs_sync(ctx.ctx)
+    step_ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    if dist:
+        t = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    kt = {fbs.KERNEL_NAMES[k]: fbs.fbs_profile_read(ctx.ctx, k) for k in range(fbs.FBS_KERNEL_KINDS)}
+    return dict(ctx=ctx, di=di, ds=ds, step_ms=step_ms, kt=kt, t0=t0, t1=t1)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -244,82 +293,102 @@ def run_ours(args):
 
     p = make_pair(args.workload, args.seed + rank)
     mode = fbs.FBS_COST_NCC if args.cost == "ncc" else fbs.FBS_COST_TAD
-    ctx = fbs.Context(dev.index, cost=mode)
     stream = torch.cuda.Stream(dev)
     dl = torch.from_numpy(p.left).to(dev)
     dr = torch.from_numpy(p.right).to(dev)
-    di = torch.empty((p.H, p.W), dtype=torch.int32, device=dev)
-    ds = torch.empty((p.H, p.W), dtype=torch.float32, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    call = lambda: fbs.fbs_compute_disparity(ctx.ctx, dl, dr, p.H, p.W, p.C, p.D, p.radius, p.sigma_s, p.sigma_r,
-                                             p.tau, di, ds, stream)
-    torch.cuda.synchronize()
+    forms = [args.prec] if args.only_form else ["f32", "bf16", "f16"]
+    if args.prec not in forms:
+        forms.append(args.prec)
     sampler = None if args.no_clocks else ClockSampler(dev.index, os.path.join(ROOT, "_bench_clocks.csv"))
-    with torch.cuda.stream(stream):
-        for _ in range(warmup):
-            flush.fill_(1)
-            call()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        fbs.fbs_profile(ctx.ctx, 1)
-        t0 = time.time()
-        for a, b in evs:
-            flush.fill_(1)
-            a.record(stream)
-            call()
-            b.record(stream)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        t1 = time.time()
-        fbs.fbs_profile(ctx.ctx, 0)
-    step_ms = sum(a.elapsed_time(b) for a, b in evs) / steps
-    if dist:
-        t = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
-    kt = {fbs.KERNEL_NAMES[k]: fbs.fbs_profile_read(ctx.ctx, k) for k in range(fbs.FBS_KERNEL_KINDS)}
-    launches = sum(n for _, n in kt.values())
-    clocks = None
+    res = {f: _time_form(fbs, torch, p, f, mode, dev, stream, dl, dr, flush, steps, warmup, dist) for f in forms}
     if sampler is not None:
         sampler.stop()
-        clocks = sampler.summary(t0, t1)
+
+    taps = _taps(p)
+    peaks, peak_src = _peaks()
+    chosen = res[args.prec]
+    # accuracy at fixed error: extra bad pixels (>1 px) against the FP32 form
+    # on the whole frame, and against the FP64 oracle on sampled pixels
+    ref = res.get("f32")
+    rng = np.random.default_rng(1234)
+    ns = 0 if args.no_oracle_check or rank != 0 else 300
+    xs, ys = rng.integers(0, p.W, ns), rng.integers(0, p.H, ns)
+    ref_ds = None
+    if ns:
+        import oracle
+        oracle.build()
+        _, ref_ds, _ = oracle.fbs_points(p.left, p.right, p.D, p.radius, p.sigma_s, p.sigma_r, xs, ys, tau=p.tau,
+                                         mode=mode)
+    form_out = {}
+    for f, r in res.items():
+        ds_np = r["ds"].cpu().numpy()
+        ent = {"gtaps_per_s": world * taps / (r["step_ms"] * 1e-3) / 1e9, "ms_per_step": r["step_ms"],
+               "fps": world * 1e3 / r["step_ms"],
+               "kernel_ms_per_step": {k: v[0] / steps for k, v in r["kt"].items() if v[1]}}
+        if ref is not None and f != "f32":
+            ent["bad_px_vs_f32_pct"] = 100.0 * float(np.mean(np.abs(ds_np - ref["ds"].cpu().numpy()) > 1.0))
+        if ref_ds is not None:
+            ent["bad_px_vs_oracle_pct_sampled"] = 100.0 * float(np.mean(np.abs(ds_np[ys, xs] - ref_ds) > 1.0))
+        form_out[f] = ent
+    if ref_ds is not None and "f32" in form_out:
+        for f, ent in form_out.items():
+            ent["extra_bad_px_vs_oracle_pct"] = ent["bad_px_vs_oracle_pct_sampled"] - \
+                form_out["f32"]["bad_px_vs_oracle_pct_sampled"]
+
+    step_ms = chosen["step_ms"]
+    value = world * taps / (step_ms * 1e-3) / 1e9
+    kt = chosen["kt"]
+    launches = sum(n for _, n in kt.values())
+    clocks = sampler.summary(chosen["t0"], chosen["t1"]) if sampler is not None else None
+    if sampler is not None:
         try:
             os.remove(sampler.path)
         except OSError:
             pass
-
-    taps = _taps(p)
-    value = world * taps / (step_ms * 1e-3) / 1e9
-    peaks, peak_src = _peaks()
-    agg_ms, agg_n = kt["aggregate_f32"]
-    cost_ms, cost_n = kt["cost_build"]
-    agg_launch_ms = agg_ms / max(1, agg_n)
-    cost_launch_ms = cost_ms / max(1, cost_n)
-    fp32_peak = GB300_SMS * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    csrc = os.path.join(ROOT, "paper_1807_02044_gb300", "csrc")
     flops = 2.0 * taps
-    roofline = {"kernel": "aggregate_f32_kernel", "bound": "alu", "achieved": flops / (agg_launch_ms * 1e-3) / 1e12,
-                "peak": fp32_peak, "unit": "TFLOP/s", "frac": None, "traffic": None,
-                "peak_source": f"derived: {GB300_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
-                               f"{peaks['sm_max_mhz']:.0f} MHz (max SM clock, {peak_src})",
-                "algorithmic": "2 flop per tap (one FMA per window tap per disparity), H*W*D*(2r+1)^2 taps",
-                "avg_launch_ms": agg_launch_ms, "launches": agg_n}
+    if args.prec == "f32":
+        agg_ms, agg_n = kt["aggregate_f32"]
+        agg_launch_ms = agg_ms / max(1, agg_n)
+        fp32_peak = GB300_SMS * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        roofline = {"kernel": "aggregate_f32_kernel", "bound": "alu",
+                    "achieved": flops / (agg_launch_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "peak_source": f"derived: {GB300_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                                   f"{peaks['sm_max_mhz']:.0f} MHz (max SM clock, {peak_src})",
+                    "traffic": _traffic_for(os.path.join(csrc, "fbs_aggregate_f32.cu"), "aggregate_f32_kernel")}
+    else:
+        agg_ms, agg_n = kt["aggregate_tc"]
+        agg_launch_ms = agg_ms / max(1, agg_n)
+        # tensor peak: measured cuBLAS bf16 (burst); FP16 dense rate is the same on GB300
+        rho8 = (p.radius + 7) // 8 * 8
+        kw = (16 + rho8 + p.radius + 15) // 16 * 16
+        n = (p.D + 15) // 16 * 16
+        tiles = ((p.W + 15) // 16) * ((p.H + 7) // 8)
+        issued = 2.0 * tiles * 128 * n * kw * (8 + 2 * p.radius)
+        roofline = {"kernel": "aggregate_tc_kernel", "bound": "tensor",
+                    "achieved": flops / (agg_launch_ms * 1e-3) / 1e12, "peak": peaks["bf16_tflops"],
+                    "unit": "TFLOP/s", "peak_source": f"bf16_tflops burst ({peak_src}); FP16 dense equals BF16",
+                    "issued_dense_tflops": issued / (agg_launch_ms * 1e-3) / 1e12,
+                    "issued_over_algorithmic": issued / flops,
+                    "traffic": _traffic_for(os.path.join(csrc, "fbs_aggregate_tc.cu"), "aggregate_tc_kernel")}
+    roofline.update({"algorithmic": "2 flop per tap (one multiply-add per window tap per disparity), "
+                                    "H*W*D*(2r+1)^2 taps", "avg_launch_ms": agg_launch_ms, "launches": agg_n})
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
-    roofline["traffic"] = _traffic_for(os.path.join(ROOT, "paper_1807_02044_gb300", "csrc", "fbs_aggregate_f32.cu"),
-                                       "aggregate_f32_kernel")
+    cost_ms, cost_n = kt["cost_build"]
+    cost_launch_ms = cost_ms / max(1, cost_n)
     ld = (p.D + 3) // 4 * 4
-    cost_bytes = 2 * p.H * p.W * p.C + 4 * p.H * p.W * ld
-    roofline_cost = {"kernel": "cost_build_kernel", "bound": "hbm",
+    vol = 4 * p.H * p.W * ld if args.prec == "f32" else 2 * p.H * p.D * ((p.W + 7) // 8 * 8)
+    cost_bytes = 2 * p.H * p.W * p.C + vol
+    roofline_cost = {"kernel": "cost_kernel (+ grey_stats_kernel)", "bound": "hbm",
                      "achieved": cost_bytes / (cost_launch_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": None, "avg_launch_ms": cost_launch_ms, "launches": cost_n,
-                     "algorithmic": "read both images once, write the FP32 cost volume once",
-                     "traffic": _traffic_for(os.path.join(ROOT, "paper_1807_02044_gb300", "csrc", "fbs_cost.cu"),
-                                             "cost_build_kernel")}
+                     "unit": "GB/s", "avg_launch_ms": cost_launch_ms, "launches": cost_n,
+                     "algorithmic": "read both images once, write the cost volume once",
+                     "traffic": _traffic_for(os.path.join(csrc, "fbs_cost.cu"), "cost_kernel")}
     roofline_cost["frac"] = roofline_cost["achieved"] / roofline_cost["peak"]
 
     e2e = None
+    ctx = chosen["ctx"]
     if not args.no_e2e:
         n_e2e = min(steps, 200)
         hl = torch.from_numpy(p.left).pin_memory()
@@ -343,8 +412,7 @@ def run_ours(args):
             t = torch.tensor([e2e_s], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
-        # the host path must agree with the device path
-        assert np.array_equal(hi.numpy(), di.cpu().numpy())
+        assert np.array_equal(hi.numpy(), chosen["di"].cpu().numpy())
         e2e = {"value": world * taps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * p.H * p.W * p.C,
                "d2h_bytes_per_step": 8 * p.H * p.W, "steps": n_e2e,
                "call": "fbs_compute_disparity_host (pinned host buffers, copies and sync inside the timed call)"}
@@ -353,16 +421,20 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(p, args.cpu_seconds, mode)
 
+    cfg = _config(p, args, "ours")
+    cfg["forms_timed"] = forms
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
            "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32", "data": "synthetic", "config": _config(p, args, "ours"),
+           "dtype": args.prec, "data": "synthetic", "config": cfg,
            "fps": world * 1e3 / step_ms, "mde_per_s": world * p.W * p.H * p.D / (step_ms * 1e-3) * 1e-6,
+           "form": args.prec, "forms": form_out,
            "roofline": roofline, "roofline_cost_build": roofline_cost, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": launches, "kernel_ms_per_step": {k: v[0] / steps for k, v in kt.items() if v[1]},
-           "clocks": clocks, "wall_s_timed_region": t1 - t0}
+           "clocks": clocks, "wall_s_timed_region": chosen["t1"] - chosen["t0"]}
     if rank == 0:
         print(json.dumps(out))
-    ctx.close()
+    for r in res.values():
+        r["ctx"].close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -7,8 +7,9 @@
 // C[k][d] the cost volume.  The K dimension is walked one window row at a
 // time: for window row hr the CTA
 //   * loads C[row hr, KW columns][N disparities] with TMA from the 16-bit
-//     disparity-planar cost volume [H][D][Wp] (B operand, K-major: for each d
-//     the KW columns are contiguous), out-of-image columns/rows zero-filled;
+//     x-blocked cost volume [H][W/8][D][8] (B operand, K-major): one box per
+//     block of 8 columns, each a contiguous D x 16-byte block that lands as N/8
+//     core matrices; out-of-image columns/rows and d >= D are zero-filled;
 //   * computes the weights of every tile pixel whose window contains row hr
 //     (A operand, K-major, 128 rows x KW columns) into shared memory: each
 //     weight is one exp2 in FP32, rounded to BF16 or FP16; the rounded values
@@ -26,7 +27,8 @@
 //     (k / 8) * (R * 16) + r * 16 + (k % 8) * 2,
 // i.e. the stride between core matrices along K (LBO) is R*16 bytes and along
 // the rows (SBO) 128 bytes.  TMA writes a box of 8 columns x N disparities in
-// exactly that order, so B needs no rearrangement.
+// exactly that order, so B needs no rearrangement.  All operands live in
+// shared memory; warp roles and mbarrier pipelines are described at the kernel.
 //
 // Every wait on an mbarrier is bounded (iteration and clock limits); on a
 // timeout the kernel records an error code, stops issuing work, drains what
@@ -43,16 +45,31 @@ namespace {
 constexpr int kTW = 16;         // tile width
 constexpr int kTH = 8;          // tile height
 constexpr int kM = kTW * kTH;   // 128 = MMA M = TMEM lanes
-constexpr int kThreads = 256;
-constexpr int kStages = 3;
+constexpr int kProducerWarps = 16;                 // warps 0-15
+constexpr int kProducers = 32 * kProducerWarps;
+constexpr int kPasses = 32 / kProducerWarps;       // 32 pixel groups of 4 per tile
+constexpr int kEpiWarp0 = kProducerWarps;          // 4 epilogue warps: TMEM lane quarters 0-3
+constexpr int kEpilogue = 128;
+constexpr int kTmaWarp = kEpiWarp0 + 4;
+constexpr int kMmaWarp = kTmaWarp + 1;
+constexpr int kThreads = 32 * (kMmaWarp + 1);
+constexpr int kMaxR = 4;          // window rows per stage, at most
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 constexpr unsigned kWaitIters = 1u << 30;
+constexpr uint32_t kSuspendNs = 20000;   // a waiting thread sleeps up to this long per try
 
 struct TcParams {
-    int H, W, C, D, N, rho, rho8, KW, NH, ntx, ntiles;
+    int H, W, C, D;
+    int N;          // round_up(D, 16): disparity rows the TMA box loads
+    int Nb;         // rows of a B stage: N, plus 16 normaliser rows when they share the MMA
+    int ones_sep;   // normaliser by a separate N=16 MMA (when N + 16 > 256)
+    int rho, rho8, KW, NH, ntx, ntiles;
+    int R;          // window rows per pipeline stage
+    int S;          // pipeline stages (weights and cost rows share the stage index)
+    int nacc;       // accumulator buffers in TMEM (2 = epilogue overlaps the next tile)
+    uint32_t acc_stride, den_col, tmem_cols;
     float neg_ks, neg_kr;
-    uint32_t idesc;
-    uint32_t tmem_cols;
+    uint32_t idesc, idesc16;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -70,10 +87,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -88,12 +105,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar)
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
             dst),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar)
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
         : "memory");
 }
 
@@ -172,217 +198,289 @@ struct Op16<false> {
 };
 
 struct TcSmem {
-    size_t a_off, b_off, g_off, den_off, bar_off, misc_off, total;
+    size_t a_off, b_off, ones_off, g_off, bar_off, misc_off, total;
 };
 
-__host__ __device__ inline TcSmem tc_smem_layout(int KW, int N, int NH)
+// Per stage: R window rows of weights (A, (KW/8) x 2048 bytes each) and R
+// rows of costs (B, (KW/8) x Nb x 16 bytes each).
+__host__ __device__ inline TcSmem tc_smem_layout(int KW, int Nb, int NH, int R, int S, bool ones_sep)
 {
     TcSmem s;
     size_t o = 0;
     s.a_off = o;
-    o += (size_t)kStages * kM * KW * 2;
+    o += (size_t)S * R * (KW / 8) * 2048;
     s.b_off = o;
-    o += (size_t)kStages * KW * N * 2;
+    o += (size_t)S * R * (KW / 8) * Nb * 16;
+    s.ones_off = o;
+    o += ones_sep ? (size_t)(KW / 8) * 16 * 16 : 0;
+    o = (o + 127) & ~(size_t)127;
     s.g_off = o;
-    o += (size_t)NH * KW * 16;
-    s.den_off = o;
-    o += 2 * kM * sizeof(float);
+    o += (size_t)2 * NH * KW * 8;
+    o = (o + 15) & ~(size_t)15;
     s.bar_off = o;
-    o += (2 * kStages + 1) * 8;
+    o += (size_t)(3 * S + 9) * 8;
     s.misc_off = o;
     o += 16;
     s.total = o + 1024;   // slack for aligning the base to 1024 bytes
     return s;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Bounded wait that also gives up as soon as another role has aborted.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (unsigned i = 0; i < kWaitIters; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) break;
+    }
+    return false;
+}
+__device__ __forceinline__ void raise_abort(volatile uint32_t* abort_flag, int* err, int code)
+{
+    if (*abort_flag == 0) *abort_flag = (uint32_t)code;
+    atomicCAS(err, 0, code);
+}
+
 template <bool BF16>
-__global__ void __launch_bounds__(kThreads, 2)
-aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t* __restrict__ guide, TcParams p,
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    uint32_t r;
+    if (BF16)
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    else
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// Warp roles: 0-15 weight producers, 16-19 epilogue (TMEM lane quarters 0-3),
+// 20 TMA producer (guide tiles and cost rows), 21 MMA issuer.  NG = number of
+// groups of 8 column pairs a pixel's window row needs (ceil((rho + 1) / 8)).
+//
+// Pipeline: a stage holds R consecutive window rows of one tile (the last
+// stage of a tile may hold fewer).  For stage g in slot s = g % S:
+//   producers  wait empty[s] (stage g - S consumed), write R rows of weights,
+//              arrive full_a[s] (one arrival per warp);
+//   TMA        waits empty[s], loads R cost rows, full_b[s] completes on bytes;
+//   MMA        waits full_a[s] and full_b[s], issues R * KW/16 MMAs, commits
+//              to empty[s]; after a tile's last stage commits acc_full[ab];
+//   epilogue   waits acc_full[ab], reads the accumulator, arrives acc_empty[ab].
+// One wait/commit pair per R rows keeps the single-thread control path
+// (which shares its scheduler with busy warps) off the critical path.
+template <bool BF16, int NG>
+__global__ void __launch_bounds__(kThreads, 1)
+aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap gmap, TcParams p,
                     float* __restrict__ agg_out, int32_t* __restrict__ disp_int, float* __restrict__ disp_sub,
                     int* __restrict__ err)
 {
-    using O = Op16<BF16>;
-    using T = typename O::T;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const TcSmem L = tc_smem_layout(p.KW, p.N, p.NH);
+    const bool ones_sep = p.ones_sep != 0;
+    const TcSmem L = tc_smem_layout(p.KW, p.Nb, p.NH, p.R, p.S, ones_sep);
     uint8_t* a_base = sm + L.a_off;
     uint8_t* b_base = sm + L.b_off;
-    float4* gtile = (float4*)(sm + L.g_off);
-    float* den_s = (float*)(sm + L.den_off);
-    const uint32_t bar0 = smem_u32(sm + L.bar_off);   // full_b[s] at bar0 + 8s, mma_done[s] at +8(S+s), acc at +16S
-    uint32_t* misc = (uint32_t*)(sm + L.misc_off);    // [0] TMEM base, [1] abort flag
+    uint2* gtile = (uint2*)(sm + L.g_off);   // [2][NH][KW] of (RGBX, |colour|^2)
+    const uint32_t bars = smem_u32(sm + L.bar_off);
+    const uint32_t full_a0 = bars, full_b0 = bars + 8 * p.S, empty0 = bars + 16 * p.S,
+                   acc_full0 = bars + 24 * p.S, acc_empty0 = acc_full0 + 16, drain_bar = acc_empty0 + 16,
+                   g_full0 = drain_bar + 8, g_empty0 = g_full0 + 16;
+    uint32_t* misc = (uint32_t*)(sm + L.misc_off);   // [0] TMEM base, [1] abort flag
+    volatile uint32_t* abort_flag = misc + 1;
 
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int KW = p.KW;
-    const uint32_t a_slot = (uint32_t)kM * KW * 2;
-    const uint32_t b_slot = (uint32_t)KW * p.N * 2;
-    const uint32_t lbo_a = kM * 16, lbo_b = (uint32_t)p.N * 16;
-    const uint32_t tma_bytes = (uint32_t)KW * p.N * 2;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int KW = p.KW, R = p.R, S = p.S;
+    const uint32_t a_row = (uint32_t)(KW / 8) * 2048;       // bytes of one window row of weights
+    const uint32_t lbo_b = (uint32_t)p.Nb * 16;
+    const uint32_t b_row = (uint32_t)(KW / 8) * lbo_b;      // bytes of one window row of costs
+    const uint32_t a_stage = a_row * R, b_stage = b_row * R;
 
+    // ---- set-up --------------------------------------------------------------
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(bar0 + 8 * s, 1);
-            mbar_init(bar0 + 8 * (kStages + s), 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full_a0 + 8 * s, kProducerWarps);   // one elected arrival per producer warp
+            mbar_init(full_b0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
         }
-        mbar_init(bar0 + 16 * kStages, 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(acc_full0 + 8 * s, 1);
+            mbar_init(acc_empty0 + 8 * s, kEpilogue / 32);   // one per epilogue warp
+            mbar_init(g_full0 + 8 * s, 1);
+            mbar_init(g_empty0 + 8 * s, kProducerWarps);
+        }
+        mbar_init(drain_bar, 1);
         misc[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmap) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&gmap) : "memory");
     }
     if (warp == 0) tmem_alloc(smem_u32(&misc[0]), p.tmem_cols);
-    // all weight positions not written later stay zero
-    for (int i = tid; i < (int)(kStages * a_slot / 16); i += kThreads) ((uint4*)a_base)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < (int)(S * a_stage / 16); i += kThreads) ((uint4*)a_base)[i] = make_uint4(0, 0, 0, 0);
+    {
+        // the normaliser rows: B row N is all ones and rows N+1..N+15 zero, so the
+        // accumulator column N is sum_k W[m][k] over the same rounded weights
+        const uint16_t one = BF16 ? (uint16_t)0x3F80 : (uint16_t)0x3C00;
+        if (!ones_sep) {
+            for (int i = tid; i < S * R * (KW / 8) * 16 * 8; i += kThreads) {
+                const int e = i & 7, row = (i >> 3) & 15, chunk = i >> 7;   // chunk = (stage*R + r)*(KW/8) + j
+                uint16_t* q = (uint16_t*)(b_base + (size_t)chunk * lbo_b + (size_t)(p.N + row) * 16) + e;
+                *q = row == 0 ? one : (uint16_t)0;
+            }
+        } else {
+            for (int i = tid; i < (KW / 8) * 16 * 8; i += kThreads) {
+                const int row = (i >> 3) & 15;
+                ((uint16_t*)(sm + L.ones_off))[i] = row == 0 ? one : (uint16_t)0;
+            }
+        }
+    }
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = misc[0];
 
-    // producer role: pixel m, taps dx in [-rho, 0] (half 0) or [1, rho] (half 1)
-    const int m = tid & (kM - 1), half = tid >> 7;
-    const int ty = m >> 4, tx = m & 15;
-    const int kc = tx + p.rho8;   // window column of the pixel itself
-    const int dxa = half ? 1 : -p.rho, dxb = half ? p.rho : 0;
-
-    uint32_t g = 0;          // window rows issued so far (global across tiles): slot g % S, use g / S
-    uint32_t tile_iter = 0;
-    bool aborted = false;
-    uint32_t tma_pending = 0;   // thread 0: slots with a TMA not yet waited for
-    uint32_t tma_par = 0;       // thread 0: phase parity of each such TMA
-
-    for (int tile = blockIdx.x; tile < p.ntiles && !aborted; tile += gridDim.x) {
-        const int tx0 = (tile % p.ntx) * kTW, ty0 = (tile / p.ntx) * kTH;
-        const int xlo = tx0 - p.rho8;
-        // guide tile: window rows ty0-rho .. ty0+7+rho, columns xlo .. xlo+KW-1
-        for (int i = tid; i < p.NH * KW; i += kThreads) {
-            const int hr = i / KW, k = i - hr * KW;
-            const int yq = ty0 - p.rho + hr, xq = xlo + k;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (yq >= 0 && yq < p.H && xq >= 0 && xq < p.W) {
-                const uint8_t* q = guide + ((size_t)yq * p.W + xq) * p.C;
-                v.x = (float)q[0];
-                if (p.C == 3) {
-                    v.y = (float)q[1];
-                    v.z = (float)q[2];
-                }
-            }
-            gtile[i] = v;
-        }
-        const int py = ty0 + ty, px = tx0 + tx;
-        const bool pvalid = py < p.H && px < p.W;
-        float3 pc = make_float3(0.f, 0.f, 0.f);
-        if (pvalid) {
-            const uint8_t* q = guide + ((size_t)py * p.W + px) * p.C;
-            pc.x = (float)q[0];
-            if (p.C == 3) {
-                pc.y = (float)q[1];
-                pc.z = (float)q[2];
+    if (warp < kProducerWarps) {
+        // ================= weight producers =================================
+        // Pass i of warp w covers pixels m = 8b + par + 2*ps (ps = lane >> 3) with
+        // j = kPasses*w + i, b = j >> 1, par = j & 1 (the 4 pixels of a pass share
+        // a tile row).  Pixel m needs window columns kc-rho .. kc+rho (kc = tx +
+        // rho8); they are covered by rho+1 pairs of adjacent columns (k, k+1)
+        // starting at the even column <= kc-rho, 8 pairs per group (lane & 7).
+        // Columns a pixel never reaches are never written and stay zero.  The
+        // four pixels of a pass start 8 banks apart, so a pass's 4-byte stores
+        // need two wavefronts at most.
+        // Colour distance: |q - p|^2 = |q|^2 + |p|^2 - 2 q.p, exact in integers
+        // (|q|^2 comes with the guide tile, q.p is one dp4a).
+        const int ps = lane >> 3, pi = lane & 7;
+        const int np = p.rho + 1;
+        int pm[kPasses], kcen[kPasses], kk[kPasses][NG];
+        uint32_t aoff[kPasses][NG];
+        bool on[kPasses][NG];
+#pragma unroll
+        for (int i = 0; i < kPasses; ++i) {
+            const int j = kPasses * warp + i;
+            pm[i] = 8 * (j >> 1) + (j & 1) + 2 * ps;
+            kcen[i] = (pm[i] & 15) + p.rho8;
+#pragma unroll
+            for (int pg = 0; pg < NG; ++pg) {
+                const int k = ((kcen[i] - p.rho) & ~1) + 2 * pi + 16 * pg;
+                kk[i][pg] = k;
+                on[i][pg] = pg * 8 + pi < np;
+                aoff[i][pg] = (uint32_t)((k >> 3) * 2048 + pm[i] * 16 + (k & 7) * 2);
             }
         }
-        float den = 0.f;
-        const int hr_lo = max(0, p.rho - ty0);
-        const int hr_hi = min(p.NH, p.H - ty0 + p.rho);
-        const int nrows = hr_hi - hr_lo;
-
-        // thread 0: TMA for window row hr_lo + r_off of this tile (global row g_tile0 + r_off)
-        const uint32_t g_tile0 = g;
-        auto issue_tma = [&](int r_off) {
-            const uint32_t gg = g_tile0 + (uint32_t)r_off;
-            const uint32_t s = gg % kStages, use = gg / kStages;
-            if (use > 0 && !mbar_wait(bar0 + 8 * (kStages + s), (use - 1) & 1)) return false;
-            const int hr = hr_lo + r_off;
-            mbar_expect_tx(bar0 + 8 * s, tma_bytes);
-            const uint32_t dst = smem_u32(b_base + s * b_slot);
-            for (int j = 0; j < KW / 8; ++j)
-                tma_load_3d(dst + j * (uint32_t)p.N * 16, &tmap, xlo + 8 * j, 0, ty0 - p.rho + hr, bar0 + 8 * s);
-            tma_pending |= 1u << s;
-            tma_par = (tma_par & ~(1u << s)) | ((use & 1u) << s);
-            return true;
-        };
-        if (tid == 0) {
-            for (int r = 0; r < 2 && r < nrows; ++r)
-                if (!issue_tma(r)) {
-                    misc[1] = 2;
-                    break;
-                }
-        }
-        __syncthreads();   // guide tile staged
-        uint32_t accumulate = 0;
-
-        for (int r = 0; r < nrows; ++r) {
-            const int hr = hr_lo + r;
-            const uint32_t s = g % kStages, use = g / kStages;
-            // the MMA that last read stage s must be done before it is overwritten
-            if (use > 0 && !mbar_wait(bar0 + 8 * (kStages + s), (use - 1) & 1)) misc[1] = 1;
-            if (tid == 0 && r + 2 < nrows && !misc[1])
-                if (!issue_tma(r + 2)) misc[1] = 2;
-            // weights of window row hr
-            {
-                uint8_t* arow = a_base + s * a_slot;
-                const int dy = hr - p.rho - ty;
-                const bool act = pvalid && dy >= -p.rho && dy <= p.rho;
-                const float sy = (float)(dy * dy) * p.neg_ks;
-                const float4* grow = gtile + hr * KW;
-                for (int dx = dxa; dx <= dxb; ++dx) {
-                    const int k = kc + dx;
-                    float w = 0.f;
-                    if (act && (unsigned)(px + dx) < (unsigned)p.W) {
-                        const float4 q = grow[k];
-                        const float e0 = q.x - pc.x, e1 = q.y - pc.y, e2 = q.z - pc.z;
-                        const float col2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
-                        w = ex2_approx(fmaf(col2, p.neg_kr, fmaf((float)(dx * dx), p.neg_ks, sy)));
-                    }
-                    const T wq = O::from(w);
-                    den += O::to(wq);
-                    *(T*)(arow + (k >> 3) * lbo_a + m * 16 + (k & 7) * 2) = wq;
-                }
-            }
-            fence_proxy_async();
-            __syncthreads();
-            if (misc[1]) {
-                aborted = true;
+        const float ninf = __int_as_float(0xff800000);
+        uint32_t g = 0, t = 0;
+        bool stop = false;
+        for (int tile = blockIdx.x; tile < p.ntiles && !stop; tile += gridDim.x, ++t) {
+            const int tx0 = (tile % p.ntx) * kTW, ty0 = (tile / p.ntx) * kTH;
+            const int xlo = tx0 - p.rho8;
+            const uint32_t tb = t & 1;
+            if (!mbar_wait_or_abort(g_full0 + 8 * tb, (t >> 1) & 1, abort_flag)) {
+                raise_abort(abort_flag, err, 6);
                 break;
             }
-            if (tid == 0) {
-                if (!mbar_wait(bar0 + 8 * s, use & 1)) {
-                    misc[1] = 3;
-                } else {
-                    tma_pending &= ~(1u << s);
-                    tc_fence_after();
-                    const uint32_t a0 = smem_u32(a_base + s * a_slot);
-                    const uint32_t b0 = smem_u32(b_base + s * b_slot);
-                    for (int j = 0; j < KW / 16; ++j) {
-                        const uint64_t ad = sdesc(a0 + j * 2 * lbo_a, lbo_a, 128);
-                        const uint64_t bd = sdesc(b0 + j * 2 * lbo_b, lbo_b, 128);
-                        umma_f16(tmem, ad, bd, p.idesc, accumulate);
-                        accumulate = 1;
-                    }
-                    umma_commit(bar0 + 8 * (kStages + s));
+            const uint2* gt = gtile + tb * (p.NH * KW);
+            // per pass and pair: spatial x-term, or -inf when the column is outside
+            // the window or the image or the pixel is outside the image
+            uint32_t pcol[kPasses], pp[kPasses];
+            int pty[kPasses];
+            float sx0[kPasses][NG], sx1[kPasses][NG];
+#pragma unroll
+            for (int i = 0; i < kPasses; ++i) {
+                pty[i] = pm[i] >> 4;
+                const bool pval = ty0 + pty[i] < p.H && tx0 + (pm[i] & 15) < p.W;
+                const uint2 pc = gt[(pty[i] + p.rho) * KW + kcen[i]];
+                pcol[i] = pc.x;
+                pp[i] = pc.y;
+#pragma unroll
+                for (int pg = 0; pg < NG; ++pg) {
+                    const int d0 = kk[i][pg] - kcen[i], d1 = d0 + 1;
+                    const int x0 = xlo + kk[i][pg];
+                    sx0[i][pg] = (pval && d0 >= -p.rho && d0 <= p.rho && (unsigned)x0 < (unsigned)p.W)
+                                     ? (float)(d0 * d0) * p.neg_ks : ninf;
+                    sx1[i][pg] = (pval && d1 >= -p.rho && d1 <= p.rho && (unsigned)(x0 + 1) < (unsigned)p.W)
+                                     ? (float)(d1 * d1) * p.neg_ks : ninf;
                 }
             }
-            ++g;
+            const int hr_lo = max(0, p.rho - ty0);
+            const int hr_hi = min(p.NH, p.H - ty0 + p.rho);
+            for (int h0 = hr_lo; h0 < hr_hi; h0 += R) {
+                const int nr = min(R, hr_hi - h0);
+                const uint32_t s = g % S, use = g / S;
+                // one lane waits for the MMAs that last read stage s; the warp follows
+                bool ok = true;
+                if (lane == 0 && use > 0) ok = mbar_wait_or_abort(empty0 + 8 * s, (use - 1) & 1, abort_flag);
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    raise_abort(abort_flag, err, 1);
+                    stop = true;
+                    break;
+                }
+                for (int r = 0; r < nr; ++r) {
+                    const int hr = h0 + r;
+                    uint8_t* arow = a_base + s * a_stage + r * a_row;
+                    const uint2* grow = gt + hr * KW;
+#pragma unroll
+                    for (int i = 0; i < kPasses; ++i) {
+                        const int dy = hr - p.rho - pty[i];
+                        const bool act = dy >= -p.rho && dy <= p.rho;   // uniform over the pass
+                        const float sy = (float)(dy * dy) * p.neg_ks;
+#pragma unroll
+                        for (int pg = 0; pg < NG; ++pg) {
+                            if (!on[i][pg]) continue;
+                            uint32_t packed = 0;
+                            if (act) {
+                                const uint4 q = *(const uint4*)(grow + kk[i][pg]);
+                                const int c0 = (int)(q.y + pp[i]) - 2 * (int)__dp4a(q.x, pcol[i], 0u);
+                                const int c1 = (int)(q.w + pp[i]) - 2 * (int)__dp4a(q.z, pcol[i], 0u);
+                                const float w0 = ex2_approx(fmaf((float)c0, p.neg_kr, sx0[i][pg] + sy));
+                                const float w1 = ex2_approx(fmaf((float)c1, p.neg_kr, sx1[i][pg] + sy));
+                                packed = pack2<BF16>(w0, w1);
+                            }
+                            *(uint32_t*)(arow + aoff[i][pg]) = packed;
+                        }
+                    }
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(full_a0 + 8 * s);
+                ++g;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(g_empty0 + 8 * tb);   // this tile's guide is no longer read
         }
-        if (aborted) break;
-        den_s[half * kM + m] = den;
-        if (tid == 0) umma_commit(bar0 + 16 * kStages);
-        if (!mbar_wait(bar0 + 16 * kStages, tile_iter & 1)) misc[1] = 4;
-        tc_fence_after();
-        __syncthreads();
-        if (misc[1]) {
-            aborted = true;
-            break;
-        }
-        if (warp < 4) {
-            const float dsum = den_s[m] + den_s[kM + m];
-            const float inv = 1.f / dsum;
+    } else if (warp < kTmaWarp) {
+        // ================= epilogue: TMEM -> normalise -> WTA -> Eq. (10) ======
+        const int q4 = warp - kEpiWarp0;    // TMEM lane quarter
+        const int m = 32 * q4 + lane;       // pixel of the tile == TMEM lane
+        uint32_t t = 0;
+        for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++t) {
+            const uint32_t ab = t % p.nacc, u = t / p.nacc;
+            // tcgen05.ld is warp-collective: the whole warp continues or stops
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_or_abort(acc_full0 + 8 * ab, u & 1, abort_flag));
+            if (!ok) {
+                raise_abort(abort_flag, err, 4);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q4) << 16) + ab * p.acc_stride;
+            const int tx0 = (tile % p.ntx) * kTW, ty0 = (tile / p.ntx) * kTH;
+            const int py = ty0 + (m >> 4), px = tx0 + (m & 15);
+            const bool pvalid = py < p.H && px < p.W;
+            float dv[16];
+            tmem_ld16(tbase + p.den_col, dv);
+            const float inv = 1.f / dv[0];
             float best = __int_as_float(0x7f800000), a_prev = 0.f, a_next = 0.f, last = 0.f;
             int bidx = 0;
             bool pending = false;
             float* arow = (agg_out && pvalid) ? agg_out + ((size_t)py * p.W + px) * p.D : nullptr;
             for (int c0 = 0; c0 < p.N; c0 += 16) {
                 float v[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+                tmem_ld16(tbase + (uint32_t)c0, v);
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int d = c0 + i;
@@ -403,6 +501,9 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t* __r
                     }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty0 + 8 * ab);
             if (pvalid) {
                 float ds = (float)bidx;
                 if (bidx > 0 && bidx < p.D - 1) {
@@ -414,22 +515,107 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t* __r
                 if (disp_sub) disp_sub[o] = ds;
             }
         }
-        tc_fence_before();
-        __syncthreads();   // accumulator read before the next tile overwrites it; guide tile free
-        ++tile_iter;
-    }
-
-    if (aborted || misc[1]) {
-        if (tid == 0) {
-            // 1: stage reuse, 2: TMA stage, 3: TMA arrival, 4: accumulator; + 16 * tile
-            atomicExch(err, (int)misc[1] + 16 * (int)tile_iter);
-            // drain: every MMA issued so far, and every TMA still in flight
-            umma_commit(bar0 + 16 * kStages);
-            mbar_wait(bar0 + 16 * kStages, tile_iter & 1);
-            for (int s = 0; s < kStages; ++s)
-                if (tma_pending & (1u << s)) mbar_wait(bar0 + 8 * s, (tma_par >> s) & 1u);
+    } else if (warp == kTmaWarp) {
+        // ================= TMA producer of guide tiles and cost rows ==========
+        if (lane == 0) {
+            uint32_t g = 0, t = 0, gpend = 0;
+            const uint32_t row_bytes = (uint32_t)KW * p.N * 2;
+            const uint32_t guide_bytes = (uint32_t)p.NH * KW * 8;
+            bool stop = false;
+            for (int tile = blockIdx.x; tile < p.ntiles && !stop; tile += gridDim.x, ++t) {
+                const int tx0 = (tile % p.ntx) * kTW, ty0 = (tile / p.ntx) * kTH;
+                const int xlo = tx0 - p.rho8;
+                {
+                    const uint32_t tb = t & 1, u = t >> 1;
+                    if (u > 0 && !mbar_wait_or_abort(g_empty0 + 8 * tb, (u - 1) & 1, abort_flag)) {
+                        raise_abort(abort_flag, err, 7);
+                        break;
+                    }
+                    mbar_expect_tx(g_full0 + 8 * tb, guide_bytes);
+                    tma_load_2d(smem_u32(gtile + tb * (p.NH * KW)), &gmap, xlo, ty0 - p.rho, g_full0 + 8 * tb);
+                    gpend = t + 1;
+                }
+                const int hr_lo = max(0, p.rho - ty0);
+                const int hr_hi = min(p.NH, p.H - ty0 + p.rho);
+                for (int h0 = hr_lo; h0 < hr_hi; h0 += R) {
+                    const int nr = min(R, hr_hi - h0);
+                    const uint32_t s = g % S, use = g / S;
+                    if (use > 0 && !mbar_wait_or_abort(empty0 + 8 * s, (use - 1) & 1, abort_flag)) {
+                        raise_abort(abort_flag, err, 2);
+                        stop = true;
+                        break;
+                    }
+                    mbar_expect_tx(full_b0 + 8 * s, row_bytes * nr);
+                    const uint32_t dst = smem_u32(b_base + s * b_stage);
+                    for (int r = 0; r < nr; ++r)
+                        for (int j = 0; j < KW / 8; ++j)
+                            tma_load_4d(dst + r * b_row + j * lbo_b, &tmap, 0, 0, (xlo >> 3) + j, ty0 - p.rho + h0 + r,
+                                        full_b0 + 8 * s);
+                    ++g;
+                }
+            }
+            if (*abort_flag) {
+                // let the copies still in flight land before the CTA exits
+                const uint32_t n = g < (uint32_t)S ? g : (uint32_t)S;
+                for (uint32_t x = g - n; x < g; ++x) mbar_wait(full_b0 + 8 * (x % S), (x / S) & 1);
+                const uint32_t ng2 = gpend < 2 ? gpend : 2;
+                for (uint32_t x = gpend - ng2; x < gpend; ++x) mbar_wait(g_full0 + 8 * (x & 1), (x >> 1) & 1);
+            }
+        }
+    } else {
+        // ================= MMA issuer =========================================
+        if (lane == 0) {
+            uint32_t g = 0, t = 0;
+            // descriptors of stage 0, row 0, K-step 0; other positions add their
+            // byte offset >> 4 to the 14-bit start-address field
+            const uint64_t a_desc0 = sdesc(smem_u32(a_base), 2048, 128);
+            const uint64_t b_desc0 = sdesc(smem_u32(b_base), lbo_b, 128);
+            const uint64_t o_desc0 = sdesc(smem_u32(sm + L.ones_off), 256, 128);
+            bool stop = false;
+            for (int tile = blockIdx.x; tile < p.ntiles && !stop; tile += gridDim.x, ++t) {
+                const uint32_t ab = t % p.nacc, u = t / p.nacc;
+                if (u > 0 && !mbar_wait_or_abort(acc_empty0 + 8 * ab, (u - 1) & 1, abort_flag)) {
+                    raise_abort(abort_flag, err, 5);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dacc = tmem + ab * p.acc_stride;
+                const int ty0 = (tile / p.ntx) * kTH;
+                const int hr_lo = max(0, p.rho - ty0);
+                const int hr_hi = min(p.NH, p.H - ty0 + p.rho);
+                uint32_t accumulate = 0;
+                for (int h0 = hr_lo; h0 < hr_hi; h0 += R) {
+                    const int nr = min(R, hr_hi - h0);
+                    const uint32_t s = g % S, par = (g / S) & 1;
+                    if (!mbar_wait_or_abort(full_a0 + 8 * s, par, abort_flag) ||
+                        !mbar_wait_or_abort(full_b0 + 8 * s, par, abort_flag)) {
+                        raise_abort(abort_flag, err, 3);
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t as = a_desc0 + ((s * a_stage) >> 4), bs = b_desc0 + ((s * b_stage) >> 4);
+                    for (int r = 0; r < nr; ++r) {
+                        const uint64_t ar = as + ((r * a_row) >> 4), br = bs + ((r * b_row) >> 4);
+                        for (int j = 0; j < KW / 16; ++j) {
+                            const uint64_t ad = ar + ((j * 2 * 2048) >> 4);
+                            umma_f16(dacc, ad, br + ((j * 2 * lbo_b) >> 4), p.idesc, accumulate);
+                            if (ones_sep) umma_f16(dacc + p.den_col, ad, o_desc0 + ((j * 2 * 256) >> 4), p.idesc16, accumulate);
+                            accumulate = 1;
+                        }
+                    }
+                    umma_commit(empty0 + 8 * s);
+                    ++g;
+                }
+                if (stop) break;
+                umma_commit(acc_full0 + 8 * ab);
+            }
+            // every MMA issued by this thread has completed before the CTA exits
+            umma_commit(drain_bar);
+            mbar_wait(drain_bar, 0);
         }
     }
+
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -457,62 +643,69 @@ EncodeTiledFn encode_fn()
 int round_up(int v, int a) { return (v + a - 1) / a * a; }
 
 template <bool BF16>
-__global__ void hwd_to_planar16_kernel(const float* __restrict__ in, int H, int W, int D, int wp,
+__global__ void hwd_to_xblock16_kernel(const float* __restrict__ in, int H, int W, int D,
                                        typename Op16<BF16>::T* __restrict__ out)
 {
-    // one CTA per (row y, 32-disparity group): read [x][d] rows, write [d][x] rows
-    __shared__ float tile[32][33];
-    const int y = blockIdx.y, d0 = blockIdx.z * 32;
-    for (int x0 = blockIdx.x * 32; x0 < W; x0 += gridDim.x * 32) {
-        for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-            const int x = x0 + i, d = d0 + threadIdx.x;
-            tile[i][threadIdx.x] = (x < W && d < D) ? in[((size_t)y * W + x) * D + d] : 0.f;
+    // one thread per (row, block of 8 columns, disparity): 8 values, 16 bytes out
+    const int nxb = (W + 7) / 8;
+    const size_t n = (size_t)H * nxb * D;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int d = (int)(i % D);
+        const size_t yb = i / D;
+        const int xb = (int)(yb % nxb), y = (int)(yb / nxb);
+        typename Op16<BF16>::T v[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int x = 8 * xb + c;
+            v[c] = Op16<BF16>::from(x < W ? in[((size_t)y * W + x) * D + d] : 0.f);
         }
-        __syncthreads();
-        for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-            const int d = d0 + i, x = x0 + threadIdx.x;
-            if (d < D && x < W) out[((size_t)y * D + d) * wp + x] = Op16<BF16>::from(tile[threadIdx.x][i]);
-        }
-        __syncthreads();
+        uint32_t w[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            w[c] = (uint32_t)*reinterpret_cast<const unsigned short*>(&v[2 * c]) |
+                   ((uint32_t)*reinterpret_cast<const unsigned short*>(&v[2 * c + 1]) << 16);
+        *reinterpret_cast<uint4*>(out + i * 8) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_hwd_to_planar16(const float* in, int H, int W, int D, int wp, bool bf16, void* out,
-                                   cudaStream_t stream)
+cudaError_t launch_hwd_to_xblock16(const float* in, int H, int W, int D, bool bf16, void* out, cudaStream_t stream)
 {
-    dim3 grid((W + 31) / 32 < 8 ? (W + 31) / 32 : 8, H, (D + 31) / 32);
-    dim3 block(32, 8);
+    const size_t n = (size_t)H * ((W + 7) / 8) * D;
+    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     if (bf16)
-        hwd_to_planar16_kernel<true><<<grid, block, 0, stream>>>(in, H, W, D, wp, (__nv_bfloat16*)out);
+        hwd_to_xblock16_kernel<true><<<blocks, 256, 0, stream>>>(in, H, W, D, (__nv_bfloat16*)out);
     else
-        hwd_to_planar16_kernel<false><<<grid, block, 0, stream>>>(in, H, W, D, wp, (__half*)out);
+        hwd_to_xblock16_kernel<false><<<blocks, 256, 0, stream>>>(in, H, W, D, (__half*)out);
     return cudaGetLastError();
 }
 
-int tc_supported(int D, int radius)
+namespace {
+
+template <bool BF16, int NG>
+cudaError_t run_tc(const CUtensorMap& map, const CUtensorMap& gmap, const TcParams& p, const TcSmem& L, int grid,
+                   float* agg_out, int32_t* disp_int, float* disp_sub, int* err, cudaStream_t stream)
 {
-    if (D > 256 || radius > 24) return 0;
-    const int rho8 = round_up(radius, 8);
-    const int KW = round_up(16 + rho8 + radius, 16);
-    const int N = round_up(D, 16);
-    const TcSmem L = tc_smem_layout(KW, N, kTH + 2 * radius);
-    return L.total <= 227 * 1024 ? 1 : 0;
+    cudaError_t e = cudaFuncSetAttribute(aggregate_tc_kernel<BF16, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L.total);
+    if (e != cudaSuccess) return e;
+    aggregate_tc_kernel<BF16, NG><<<grid, kThreads, L.total, stream>>>(map, gmap, p, agg_out, disp_int, disp_sub, err);
+    return cudaGetLastError();
 }
 
-cudaError_t launch_aggregate_tc(const void* cost, int wp, const uint8_t* guide, int H, int W, int C, int D,
-                                int radius, float sigma_s, float sigma_r, bool bf16, float* agg_out,
-                                int32_t* disp_int, float* disp_sub, int* err, int num_sms, cudaStream_t stream)
+// Derived launch parameters; returns false if the case does not fit.
+bool tc_plan(int H, int W, int C, int D, int radius, float sigma_s, float sigma_r, bool bf16, TcParams& p,
+             TcSmem& L)
 {
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return cudaErrorNotSupported;
-    TcParams p;
+    if (D < 1 || D > 256 || radius < 0 || radius > 24) return false;
     p.H = H;
     p.W = W;
     p.C = C;
     p.D = D;
     p.N = round_up(D, 16);
+    p.ones_sep = p.N + 16 > 256 ? 1 : 0;
+    p.Nb = p.ones_sep ? p.N : p.N + 16;
     p.rho = radius;
     p.rho8 = round_up(radius, 8);
     p.KW = round_up(16 + p.rho8 + radius, 16);
@@ -522,43 +715,84 @@ cudaError_t launch_aggregate_tc(const void* cost, int wp, const uint8_t* guide, 
     const double log2e = 1.4426950408889634;
     p.neg_ks = (float)(-log2e / ((double)sigma_s * sigma_s));
     p.neg_kr = (float)(-log2e / ((double)sigma_r * sigma_r));
+    const uint32_t total_n = (uint32_t)p.N + 16;   // disparities + normaliser column block
+    p.den_col = (uint32_t)p.N;
+    p.nacc = 2 * total_n <= 512 ? 2 : 1;
+    p.acc_stride = total_n;
+    uint32_t cols = 32;
+    while (cols < p.nacc * total_n) cols <<= 1;
+    p.tmem_cols = cols;
     // kind::f16 instruction descriptor: D = F32, A = B = BF16 (1) or F16 (0),
     // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
     const uint32_t fmt = bf16 ? 1u : 0u;
-    p.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(p.N >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
-    uint32_t cols = 32;
-    while ((int)cols < p.N) cols <<= 1;
-    p.tmem_cols = cols;
+    const uint32_t base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kM >> 4) << 24);
+    p.idesc = base | ((uint32_t)((p.ones_sep ? p.N : p.Nb) >> 3) << 17);
+    p.idesc16 = base | (2u << 17);
+    // R window rows per stage and S stages: the largest R (<= 4) with at least
+    // 3 stages in 227 KB, then as many stages (<= 6) as fit
+    for (p.R = kMaxR; p.R >= 1; --p.R) {
+        for (p.S = 6; p.S >= 3; --p.S) {
+            L = tc_smem_layout(p.KW, p.Nb, p.NH, p.R, p.S, p.ones_sep != 0);
+            if (L.total <= 227 * 1024) return true;
+        }
+    }
+    return false;
+}
 
+}  // namespace
+
+int tc_supported(int D, int radius)
+{
+    TcParams p;
+    TcSmem L;
+    return tc_plan(64, 64, 3, D, radius, 1.f, 1.f, true, p, L) ? 1 : 0;
+}
+
+cudaError_t launch_aggregate_tc(const void* cost, const uint2* rgbx, int H, int W, int C, int D,
+                                int radius, float sigma_s, float sigma_r, bool bf16, float* agg_out,
+                                int32_t* disp_int, float* disp_sub, int* err, int num_sms, cudaStream_t stream)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    TcParams p;
+    TcSmem L;
+    if (!tc_plan(H, W, C, D, radius, sigma_s, sigma_r, bf16, p, L)) return cudaErrorInvalidValue;
+
+    // x-blocked volume as a 4-D tensor: (column in block, d, block, row)
     CUtensorMap map;
-    cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)D, (cuuint64_t)H};
-    cuuint64_t strides[2] = {(cuuint64_t)wp * 2, (cuuint64_t)D * wp * 2};
-    cuuint32_t box[3] = {8, (cuuint32_t)p.N, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(&map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+    const int nxb = (W + 7) / 8;
+    cuuint64_t dims[4] = {8, (cuuint64_t)D, (cuuint64_t)nxb, (cuuint64_t)H};
+    cuuint64_t strides[3] = {16, (cuuint64_t)D * 16, (cuuint64_t)nxb * D * 16};
+    cuuint32_t box[4] = {8, (cuuint32_t)p.N, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(&map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4,
                      const_cast<void*>(cost), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    CUtensorMap gmap;
+    cuuint64_t gdims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    cuuint64_t gstrides[1] = {(cuuint64_t)rgbx_pitch(W) * 8};
+    cuuint32_t gbox[2] = {(cuuint32_t)p.KW, (cuuint32_t)p.NH};
+    cuuint32_t gestr[2] = {1, 1};
+    r = enc(&gmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint2*>(rgbx), gdims, gstrides, gbox, gestr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
 
-    const TcSmem L = tc_smem_layout(p.KW, p.N, p.NH);
-    const int per_sm = L.total <= 113 * 1024 ? 2 : 1;
-    const int grid = p.ntiles < per_sm * num_sms ? p.ntiles : per_sm * num_sms;
-    cudaError_t e;
-    if (bf16) {
-        e = cudaFuncSetAttribute(aggregate_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)L.total);
-        if (e != cudaSuccess) return e;
-        aggregate_tc_kernel<true><<<grid, kThreads, L.total, stream>>>(map, guide, p, agg_out, disp_int, disp_sub,
-                                                                      err);
-    } else {
-        e = cudaFuncSetAttribute(aggregate_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)L.total);
-        if (e != cudaSuccess) return e;
-        aggregate_tc_kernel<false><<<grid, kThreads, L.total, stream>>>(map, guide, p, agg_out, disp_int,
-                                                                       disp_sub, err);
+    const int grid = p.ntiles < num_sms ? p.ntiles : num_sms;
+    const int ng = (radius + 1 + 7) / 8;
+    switch ((bf16 ? 10 : 0) + ng) {
+    case 1: return run_tc<false, 1>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
+    case 2: return run_tc<false, 2>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
+    case 3: return run_tc<false, 3>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
+    case 4: return run_tc<false, 4>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
+    case 11: return run_tc<true, 1>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
+    case 12: return run_tc<true, 2>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
+    case 13: return run_tc<true, 3>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
+    case 14: return run_tc<true, 4>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
+    default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace fbs

@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/fbs.h"
+#include "fbs.h"
 #include "fbs_internal.cuh"
 
 struct fbs_ctx {
@@ -175,8 +175,6 @@ fbs_status ensure(fbs_ctx* ctx, void** buf, size_t* have, size_t need, const cha
     return FBS_OK;
 }
 
-int round_up_int(int v, int a) { return (v + a - 1) / a * a; }
-
 // Tensor-core form: 16-bit planar cost volume, tcgen05 aggregation.
 fbs_status run_path_tc(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C, int D,
                        int radius, float sigma_s, float sigma_r, float tau, int32_t* disp_int, float* disp_subpix,
@@ -186,22 +184,28 @@ fbs_status run_path_tc(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, 
         return fail(ctx, FBS_ERR_UNSUPPORTED, "tensor-core aggregation supports D <= 256 and radius <= 24 (got D=%d, radius=%d)",
                     D, radius);
     const bool bf16 = ctx->opt.prec == FBS_PREC_BF16;
-    const int wp = round_up_int(W, 8);
     const size_t stats = fbs::cost_scratch_bytes(H, W);
-    const size_t need = stats + (size_t)2 * H * D * wp;
+    const size_t rgbx = fbs::rgbx_bytes(H, W);
+    const size_t need = stats + rgbx + fbs::xblock16_bytes(H, W, D);
     fbs_status s = ensure(ctx, &ctx->ws, &ctx->ws_bytes, need, "cost volume");
     if (s != FBS_OK) return s;
-    const fbs::CostScratch sc = fbs::carve_cost_scratch(ctx->ws, H, W);
-    void* cost = (uint8_t*)ctx->ws + stats;
-    cudaError_t e;
+    fbs::CostScratch sc = fbs::carve_cost_scratch(ctx->ws, H, W);
+    sc.rgbx = (uint2*)((uint8_t*)ctx->ws + stats);   // written by the statistics pre-pass (NCC)
+    void* cost = (uint8_t*)ctx->ws + stats + rgbx;
+    cudaError_t e = cudaSuccess;
+    if (ctx->opt.cost != FBS_COST_NCC) {
+        LaunchScope ls(ctx, FBS_KERNEL_OTHER, st);
+        e = fbs::launch_pack_rgbx(left, H, W, C, sc.rgbx, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "guide packing launch");
     {
         LaunchScope ls(ctx, FBS_KERNEL_COST, st);
-        e = fbs::launch_cost_build_planar16(sc, left, right, H, W, C, D, wp, ctx->opt.cost, tau, bf16, cost, st);
+        e = fbs::launch_cost_build_xblock16(sc, left, right, H, W, C, D, ctx->opt.cost, tau, bf16, cost, st);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cost build launch");
     {
         LaunchScope ls(ctx, FBS_KERNEL_AGG_TC, st);
-        e = fbs::launch_aggregate_tc(cost, wp, left, H, W, C, D, radius, sigma_s, sigma_r, bf16, nullptr, disp_int,
+        e = fbs::launch_aggregate_tc(cost, sc.rgbx, H, W, C, D, radius, sigma_s, sigma_r, bf16, nullptr, disp_int,
                                      disp_subpix, ctx->derr, ctx->num_sms, st);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core aggregation launch");
@@ -498,17 +502,20 @@ fbs_status fbs_aggregate(fbs_ctx* ctx, const float* cost, const uint8_t* guide, 
         if (!fbs::tc_supported(D, radius))
             return fail(ctx, FBS_ERR_UNSUPPORTED, "tensor-core aggregation supports D <= 256 and radius <= 24");
         const bool bf16 = ctx->opt.prec == FBS_PREC_BF16;
-        const int wp = round_up_int(W, 8);
-        fbs_status s2 = ensure(ctx, &ctx->ws, &ctx->ws_bytes, (size_t)2 * H * D * wp, "16-bit cost copy");
+        const size_t rgbx = fbs::rgbx_bytes(H, W);
+        fbs_status s2 = ensure(ctx, &ctx->ws, &ctx->ws_bytes, rgbx + fbs::xblock16_bytes(H, W, D), "16-bit cost copy");
         if (s2 != FBS_OK) return s2;
+        uint2* packed = (uint2*)ctx->ws;
+        void* cost16 = (uint8_t*)ctx->ws + rgbx;
         {
             LaunchScope ls(ctx, FBS_KERNEL_OTHER, st);
-            e = fbs::launch_hwd_to_planar16(cost, H, W, D, wp, bf16, ctx->ws, st);
+            e = fbs::launch_hwd_to_xblock16(cost, H, W, D, bf16, cost16, st);
+            if (e == cudaSuccess) e = fbs::launch_pack_rgbx(guide, H, W, C, packed, st);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cost conversion launch");
         {
             LaunchScope ls(ctx, FBS_KERNEL_AGG_TC, st);
-            e = fbs::launch_aggregate_tc(ctx->ws, wp, guide, H, W, C, D, radius, sigma_s, sigma_r, bf16, agg_out,
+            e = fbs::launch_aggregate_tc(cost16, packed, H, W, C, D, radius, sigma_s, sigma_r, bf16, agg_out,
                                          disp_int, disp_subpix, ctx->derr, ctx->num_sms, st);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core aggregation launch");

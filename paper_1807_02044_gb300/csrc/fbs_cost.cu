@@ -21,8 +21,11 @@
 // either layout:
 //   * [H][W][ld] float32 (D innermost; the FP32 aggregation), padding d in
 //     [D, ld) written as 0;
-//   * [H][D][Wp] 16-bit (x innermost; the tensor-core aggregation, whose B
-//     operand is K-major over window columns).
+//   * 16-bit x-blocked [H][ceil(W/8)][D][8] (the tensor-core aggregation):
+//     for a row y and a block of 8 columns, the D x 8 block is contiguous, so
+//     the tensor-core kernel's TMA reads contiguous 16*D-byte blocks that land
+//     as K-major core matrices (8 columns x 8 disparities, 128 bytes); columns
+//     x >= W of the last block are written as 0.
 //
 // TAD (not in the paper): C = min(mean_c |I_l(u,v) - I_r(u-d,v)|, tau), tau
 // when u - d < 0.
@@ -55,7 +58,8 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 // (clamped), rv = 1/sqrt(9 Q - S^2) or 0 for a flat block.
 __global__ void __launch_bounds__(256)
 grey_stats_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int H, int W, int C,
-                  int16_t* __restrict__ g_out, int* __restrict__ s_out, float* __restrict__ rv_out)
+                  int16_t* __restrict__ g_out, int* __restrict__ s_out, float* __restrict__ rv_out,
+                  uint2* __restrict__ rgbx)
 {
     const int img = blockIdx.z;
     const uint8_t* src = img == 0 ? L : R;
@@ -79,6 +83,10 @@ grey_stats_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, 
     const uint8_t* p = src + ((size_t)y * W + x) * C;
     int g = p[0];
     if (C == 3) g += p[1] + p[2];
+    if (rgbx != nullptr && img == 0) {
+        const uint32_t c = C == 3 ? (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) : (uint32_t)p[0];
+        rgbx[(size_t)y * rgbx_pitch(W) + x] = make_uint2(c, (uint32_t)__dp4a(c, c, 0u));
+    }
     const int v = 9 * q - s * s;
     const size_t o = img * plane + (size_t)y * W + x;
     g_out[o] = (int16_t)g;
@@ -96,23 +104,23 @@ template <>
 __device__ __forceinline__ __half to_out<__half>(float v) { return __float2half_rn(v); }
 
 template <typename T>
-__device__ __forceinline__ void store4(T* o, const T (&v)[4])
+__device__ __forceinline__ void store8(T* o, const T (&v)[8])
 {
     if (sizeof(T) == 2) {
-        ushort4 u;
-        u.x = *reinterpret_cast<const unsigned short*>(&v[0]);
-        u.y = *reinterpret_cast<const unsigned short*>(&v[1]);
-        u.z = *reinterpret_cast<const unsigned short*>(&v[2]);
-        u.w = *reinterpret_cast<const unsigned short*>(&v[3]);
-        *reinterpret_cast<ushort4*>(o) = u;
+        uint32_t w[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            w[c] = (uint32_t)*reinterpret_cast<const unsigned short*>(&v[2 * c]) |
+                   ((uint32_t)*reinterpret_cast<const unsigned short*>(&v[2 * c + 1]) << 16);
+        *reinterpret_cast<uint4*>(o) = make_uint4(w[0], w[1], w[2], w[3]);
     } else {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) o[c] = v[c];
+        for (int c = 0; c < 8; ++c) o[c] = v[c];
     }
 }
 
 // MODE 0: NCC from the statistics planes; MODE 1: TAD from the raw images.
-// PLANAR false: out is [H][W][ld] (T = float); true: out is [H][D][ld] with ld = Wp.
+// PLANAR false: out is [H][W][ld] (T = float); true: out is x-blocked [H][ld][D][8] with ld = ceil(W/8).
 template <int MODE, typename T, bool PLANAR>
 __global__ void __launch_bounds__(kThreads)
 cost_kernel(const int16_t* __restrict__ gplane, const int* __restrict__ splane, const float* __restrict__ rvplane,
@@ -277,20 +285,20 @@ cost_kernel(const int16_t* __restrict__ gplane, const int* __restrict__ splane, 
 
         const int nd = min(kDC, D - dc);
         if (PLANAR) {
-            // out[(y*D + d)*ld + x]: a thread stores pixels 4g..4g+3 of one row
-            for (int i = tid; i < nd * (kXS / 4); i += kThreads) {
-                const int dd = i >> 5, g = i & 31;
-                const float* sp = stage + dd * kStage + g;
-                T v[4];
+            // out[((y*ld + xb)*D + d)*8 + xi]: one lane stores the 8 columns of a
+            // block for one disparity (16 bytes), a warp 32 consecutive disparities
+            const int nb = (nxs + 7) >> 3;
+            for (int i = tid; i < nb * nd; i += kThreads) {
+                const int b = i / nd, dd = i - b * nd;
+                const float* sp = stage + dd * kStage;
+                T v[8];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) v[c] = to_out<T>(sp[32 * c]);
-                T* o = out + ((size_t)y * D + dc + dd) * ld + x0 + 4 * g;
-                if (4 * g + 3 < nxs) {
-                    store4(o, v);
-                } else {
-                    for (int c = 0; c < 4; ++c)
-                        if (4 * g + c < nxs) o[c] = v[c];
+                for (int c = 0; c < 8; ++c) {
+                    const int x = 8 * b + c;
+                    v[c] = to_out<T>(x < nxs ? sp[stage_pos(x)] : 0.f);
                 }
+                T* o = out + (((size_t)y * ld + (x0 >> 3) + b) * D + dc + dd) * 8;
+                store8(o, v);
             }
         } else {
             // out[(y*W + x)*ld + d]; padding d in [D, ld) of the last pass written as 0
@@ -330,7 +338,7 @@ cudaError_t launch_stats(const CostScratch& sc, const uint8_t* left, const uint8
                          cudaStream_t stream)
 {
     dim3 grid((W + 255) / 256, H, 2);
-    grey_stats_kernel<<<grid, 256, 0, stream>>>(left, right, H, W, C, sc.g, sc.s, sc.rv);
+    grey_stats_kernel<<<grid, 256, 0, stream>>>(left, right, H, W, C, sc.g, sc.s, sc.rv, sc.rgbx);
     return cudaGetLastError();
 }
 
@@ -343,10 +351,29 @@ size_t cost_scratch_bytes(int H, int W)
            ((n * sizeof(float) + 255) & ~(size_t)255);
 }
 
+size_t rgbx_bytes(int H, int W) { return ((size_t)H * rgbx_pitch(W) * 8 + 255) & ~(size_t)255; }
+
+__global__ void pack_rgbx_kernel(const uint8_t* __restrict__ img, int H, int W, int C, uint2* __restrict__ out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W) return;
+    const uint8_t* p = img + ((size_t)y * W + x) * C;
+    const uint32_t c = C == 3 ? (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) : (uint32_t)p[0];
+    out[(size_t)y * rgbx_pitch(W) + x] = make_uint2(c, (uint32_t)__dp4a(c, c, 0u));
+}
+
+cudaError_t launch_pack_rgbx(const uint8_t* img, int H, int W, int C, uint2* rgbx, cudaStream_t stream)
+{
+    dim3 grid((W + 255) / 256, H);
+    pack_rgbx_kernel<<<grid, 256, 0, stream>>>(img, H, W, C, rgbx);
+    return cudaGetLastError();
+}
+
 CostScratch carve_cost_scratch(void* base, int H, int W)
 {
     const size_t n = (size_t)2 * H * W;
     CostScratch sc;
+    sc.rgbx = nullptr;
     uint8_t* p = (uint8_t*)base;
     sc.g = (int16_t*)p;
     p += (n * sizeof(int16_t) + 255) & ~(size_t)255;
@@ -367,21 +394,22 @@ cudaError_t launch_cost_build(const CostScratch& sc, const uint8_t* left, const 
     return launch_cost_kernel<1, float, false>(sc, left, right, H, W, C, D, ld, tau, cost, stream);
 }
 
-cudaError_t launch_cost_build_planar16(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H,
-                                       int W, int C, int D, int wp, int mode, float tau, bool bf16, void* cost,
+cudaError_t launch_cost_build_xblock16(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H,
+                                       int W, int C, int D, int mode, float tau, bool bf16, void* cost,
                                        cudaStream_t stream)
 {
+    const int nxb = (W + 7) / 8;
     if (mode == 0) {
         cudaError_t e = launch_stats(sc, left, right, H, W, C, stream);
         if (e != cudaSuccess) return e;
-        return bf16 ? launch_cost_kernel<0, __nv_bfloat16, true>(sc, left, right, H, W, C, D, wp, tau,
+        return bf16 ? launch_cost_kernel<0, __nv_bfloat16, true>(sc, left, right, H, W, C, D, nxb, tau,
                                                                  (__nv_bfloat16*)cost, stream)
-                    : launch_cost_kernel<0, __half, true>(sc, left, right, H, W, C, D, wp, tau, (__half*)cost,
+                    : launch_cost_kernel<0, __half, true>(sc, left, right, H, W, C, D, nxb, tau, (__half*)cost,
                                                           stream);
     }
-    return bf16 ? launch_cost_kernel<1, __nv_bfloat16, true>(sc, left, right, H, W, C, D, wp, tau,
+    return bf16 ? launch_cost_kernel<1, __nv_bfloat16, true>(sc, left, right, H, W, C, D, nxb, tau,
                                                              (__nv_bfloat16*)cost, stream)
-                : launch_cost_kernel<1, __half, true>(sc, left, right, H, W, C, D, wp, tau, (__half*)cost, stream);
+                : launch_cost_kernel<1, __half, true>(sc, left, right, H, W, C, D, nxb, tau, (__half*)cost, stream);
 }
 
 }  // namespace fbs

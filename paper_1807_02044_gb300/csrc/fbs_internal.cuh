@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/fbs.h"
+#include "fbs.h"
 
 namespace fbs {
 
@@ -20,18 +20,23 @@ struct CostScratch {
     int16_t* g;
     int* s;
     float* rv;
+    uint2* rgbx;      // optional: left image as (R | G << 8 | B << 16, R^2 + G^2 + B^2), pitch rgbx_pitch(W)
 };
 size_t cost_scratch_bytes(int H, int W);
 CostScratch carve_cost_scratch(void* base, int H, int W);
+// Size and carving of the optional packed guide plane that follows the statistics.
+size_t rgbx_bytes(int H, int W);
+__host__ __device__ inline int rgbx_pitch(int W) { return (W + 1) & ~1; }
 
 // cost[(y*W + x)*ld + d] for d < D; entries D <= d < ld are written as 0.
 cudaError_t launch_cost_build(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H, int W,
                               int C, int D, int ld, int mode, float tau, float* cost, cudaStream_t stream);
 
-// 16-bit planar volume cost[(y*D + d)*wp + x] (x < W written), wp % 8 == 0;
-// bf16 selects __nv_bfloat16, otherwise __half.
-cudaError_t launch_cost_build_planar16(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H,
-                                       int W, int C, int D, int wp, int mode, float tau, bool bf16, void* cost,
+// 16-bit x-blocked volume cost[((y*ceil(W/8) + x/8)*D + d)*8 + x%8], columns
+// x >= W of the last block written as 0; bf16 selects __nv_bfloat16, else __half.
+inline size_t xblock16_bytes(int H, int W, int D) { return (size_t)H * ((W + 7) / 8) * D * 8 * 2; }
+cudaError_t launch_cost_build_xblock16(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H,
+                                       int W, int C, int D, int mode, float tau, bool bf16, void* cost,
                                        cudaStream_t stream);
 
 // ---- steps 2-4 in FP32: Eq. (6)-(8), WTA, Eq. (10) ----------------------------
@@ -42,15 +47,18 @@ cudaError_t launch_aggregate_f32(const float* cost, int ld, const uint8_t* guide
                                  cudaStream_t stream);
 
 // ---- steps 2-4 on the tensor cores (BF16 / FP16 operands, FP32 accumulate) ---
-// cost: 16-bit planar [H][D][wp], wp % 8 == 0, 16-byte aligned.  err: device
-// int set to nonzero if a bounded wait inside the kernel gave up.
+// cost: 16-bit x-blocked volume (see launch_cost_build_xblock16), 16-byte
+// aligned.  err: device int set to nonzero if a bounded wait inside the kernel
+// gave up.
 int tc_supported(int D, int radius);
-cudaError_t launch_aggregate_tc(const void* cost, int wp, const uint8_t* guide, int H, int W, int C, int D,
+cudaError_t launch_aggregate_tc(const void* cost, const uint2* rgbx, int H, int W, int C, int D,
                                 int radius, float sigma_s, float sigma_r, bool bf16, float* agg_out,
                                 int32_t* disp_int, float* disp_sub, int* err, int num_sms, cudaStream_t stream);
-// FP32 [H][W][D] -> 16-bit planar [H][D][wp] (rounded to nearest).
-cudaError_t launch_hwd_to_planar16(const float* in, int H, int W, int D, int wp, bool bf16, void* out,
-                                   cudaStream_t stream);
+// Packed guide plane of an image: (RGBX, squared norm) per pixel, pitch rgbx_pitch(W); the
+// tensor-core path loads its guide tiles from it.
+cudaError_t launch_pack_rgbx(const uint8_t* img, int H, int W, int C, uint2* rgbx, cudaStream_t stream);
+// FP32 [H][W][D] -> 16-bit x-blocked volume (rounded to nearest).
+cudaError_t launch_hwd_to_xblock16(const float* in, int H, int W, int D, bool bf16, void* out, cudaStream_t stream);
 
 // ---- context helpers for entry points defined outside fbs_api.cu -------------
 // Host-side checks of fbs_compute_disparity's arguments (sets the message).
