@@ -321,16 +321,11 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
     if (warp == 0) tmem_alloc(smem_u32(&misc[0]), p.tmem_cols);
     for (int i = tid; i < (int)(S * a_stage / 16); i += kThreads) ((uint4*)a_base)[i] = make_uint4(0, 0, 0, 0);
     {
-        // the normaliser rows: B row N is all ones and rows N+1..N+15 zero, so the
-        // accumulator column N is sum_k W[m][k] over the same rounded weights
+        // with D + 16 > 256 the normaliser is a separate N=16 MMA against this
+        // block (row 0 all ones, rows 1..15 zero); otherwise the ones row comes
+        // with the cost volume (see launch_cost_build_xblock16)
         const uint16_t one = BF16 ? (uint16_t)0x3F80 : (uint16_t)0x3C00;
-        if (!ones_sep) {
-            for (int i = tid; i < S * R * (KW / 8) * 16 * 8; i += kThreads) {
-                const int e = i & 7, row = (i >> 3) & 15, chunk = i >> 7;   // chunk = (stage*R + r)*(KW/8) + j
-                uint16_t* q = (uint16_t*)(b_base + (size_t)chunk * lbo_b + (size_t)(p.N + row) * 16) + e;
-                *q = row == 0 ? one : (uint16_t)0;
-            }
-        } else {
+        if (ones_sep) {
             for (int i = tid; i < (KW / 8) * 16 * 8; i += kThreads) {
                 const int row = (i >> 3) & 15;
                 ((uint16_t*)(sm + L.ones_off))[i] = row == 0 ? one : (uint16_t)0;
@@ -519,7 +514,6 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
         // ================= TMA producer of guide tiles and cost rows ==========
         if (lane == 0) {
             uint32_t g = 0, t = 0, gpend = 0;
-            const uint32_t row_bytes = (uint32_t)KW * p.N * 2;
             const uint32_t guide_bytes = (uint32_t)p.NH * KW * 8;
             bool stop = false;
             for (int tile = blockIdx.x; tile < p.ntiles && !stop; tile += gridDim.x, ++t) {
@@ -545,12 +539,9 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                         stop = true;
                         break;
                     }
-                    mbar_expect_tx(full_b0 + 8 * s, row_bytes * nr);
-                    const uint32_t dst = smem_u32(b_base + s * b_stage);
-                    for (int r = 0; r < nr; ++r)
-                        for (int j = 0; j < KW / 8; ++j)
-                            tma_load_4d(dst + r * b_row + j * lbo_b, &tmap, 0, 0, (xlo >> 3) + j, ty0 - p.rho + h0 + r,
-                                        full_b0 + 8 * s);
+                    // one box: 8 columns x Nb rows x KW/8 blocks x R window rows
+                    mbar_expect_tx(full_b0 + 8 * s, b_stage);
+                    tma_load_4d(smem_u32(b_base + s * b_stage), &tmap, 0, 0, xlo >> 3, ty0 - p.rho + h0, full_b0 + 8 * s);
                     ++g;
                 }
             }
@@ -594,14 +585,25 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t as = a_desc0 + ((s * a_stage) >> 4), bs = b_desc0 + ((s * b_stage) >> 4);
-                    for (int r = 0; r < nr; ++r) {
-                        const uint64_t ar = as + ((r * a_row) >> 4), br = bs + ((r * b_row) >> 4);
-                        for (int j = 0; j < KW / 16; ++j) {
-                            const uint64_t ad = ar + ((j * 2 * 2048) >> 4);
-                            umma_f16(dacc, ad, br + ((j * 2 * lbo_b) >> 4), p.idesc, accumulate);
-                            if (ones_sep) umma_f16(dacc + p.den_col, ad, o_desc0 + ((j * 2 * 256) >> 4), p.idesc16, accumulate);
+                    // K steps of 16 walk a stage's rows contiguously: a row is KW/16
+                    // steps of 2 core-matrix columns in both operands
+                    uint64_t ad = a_desc0 + ((s * a_stage) >> 4), bd = b_desc0 + ((s * b_stage) >> 4);
+                    const int nk = nr * (KW / 16);
+                    if (!ones_sep) {
+                        for (int k = 0; k < nk; ++k) {
+                            umma_f16(dacc, ad, bd, p.idesc, accumulate);
                             accumulate = 1;
+                            ad += (2 * 2048) >> 4;
+                            bd += (2 * lbo_b) >> 4;
+                        }
+                    } else {
+                        for (int k = 0; k < nk; ++k) {
+                            const int j = k % (KW / 16);
+                            umma_f16(dacc, ad, bd, p.idesc, accumulate);
+                            umma_f16(dacc + p.den_col, ad, o_desc0 + ((j * 2 * 256) >> 4), p.idesc16, accumulate);
+                            accumulate = 1;
+                            ad += (2 * 2048) >> 4;
+                            bd += (2 * lbo_b) >> 4;
                         }
                     }
                     umma_commit(empty0 + 8 * s);
@@ -648,6 +650,7 @@ __global__ void hwd_to_xblock16_kernel(const float* __restrict__ in, int H, int 
 {
     // one thread per (row, block of 8 columns, disparity): 8 values, 16 bytes out
     const int nxb = (W + 7) / 8;
+    const int dp = tc_block_rows(D);
     const size_t n = (size_t)H * nxb * D;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const int d = (int)(i % D);
@@ -664,7 +667,23 @@ __global__ void hwd_to_xblock16_kernel(const float* __restrict__ in, int H, int 
         for (int c = 0; c < 4; ++c)
             w[c] = (uint32_t)*reinterpret_cast<const unsigned short*>(&v[2 * c]) |
                    ((uint32_t)*reinterpret_cast<const unsigned short*>(&v[2 * c + 1]) << 16);
-        *reinterpret_cast<uint4*>(out + i * 8) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(out + (yb * dp + d) * 8) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+template <bool BF16>
+__global__ void xblock16_pad_kernel(int H, int W, int D, typename Op16<BF16>::T* __restrict__ out)
+{
+    // rows D .. Dp-1 of every block: zero, except row round_up(D,16) = all ones
+    const int nxb = (W + 7) / 8;
+    const int n16 = (D + 15) / 16 * 16, dp = tc_block_rows(D), extra = dp - D;
+    const uint16_t one = BF16 ? (uint16_t)0x3F80 : (uint16_t)0x3C00;
+    const size_t n = (size_t)H * nxb * extra;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int d = D + (int)(i % extra);
+        const size_t yb = i / extra;
+        const uint32_t v = (d == n16 && dp > n16) ? ((uint32_t)one | ((uint32_t)one << 16)) : 0u;
+        *reinterpret_cast<uint4*>(out + (yb * dp + d) * 8) = make_uint4(v, v, v, v);
     }
 }
 
@@ -748,6 +767,19 @@ int tc_supported(int D, int radius)
     return tc_plan(64, 64, 3, D, radius, 1.f, 1.f, true, p, L) ? 1 : 0;
 }
 
+cudaError_t launch_xblock16_pad_rows(int H, int W, int D, bool bf16, void* out, cudaStream_t stream)
+{
+    const int extra = tc_block_rows(D) - D;
+    if (extra <= 0) return cudaSuccess;
+    const size_t n = (size_t)H * ((W + 7) / 8) * extra;
+    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    if (bf16)
+        xblock16_pad_kernel<true><<<blocks, 256, 0, stream>>>(H, W, D, (__nv_bfloat16*)out);
+    else
+        xblock16_pad_kernel<false><<<blocks, 256, 0, stream>>>(H, W, D, (__half*)out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_aggregate_tc(const void* cost, const uint2* rgbx, int H, int W, int C, int D,
                                 int radius, float sigma_s, float sigma_r, bool bf16, float* agg_out,
                                 int32_t* disp_int, float* disp_sub, int* err, int num_sms, cudaStream_t stream)
@@ -758,12 +790,13 @@ cudaError_t launch_aggregate_tc(const void* cost, const uint2* rgbx, int H, int 
     TcSmem L;
     if (!tc_plan(H, W, C, D, radius, sigma_s, sigma_r, bf16, p, L)) return cudaErrorInvalidValue;
 
-    // x-blocked volume as a 4-D tensor: (column in block, d, block, row)
+    // x-blocked volume as a 4-D tensor: (column in block, block row d, block, image row);
+    // a box covers all Nb block rows of the KW/8 blocks of R window rows
     CUtensorMap map;
     const int nxb = (W + 7) / 8;
-    cuuint64_t dims[4] = {8, (cuuint64_t)D, (cuuint64_t)nxb, (cuuint64_t)H};
-    cuuint64_t strides[3] = {16, (cuuint64_t)D * 16, (cuuint64_t)nxb * D * 16};
-    cuuint32_t box[4] = {8, (cuuint32_t)p.N, 1, 1};
+    cuuint64_t dims[4] = {8, (cuuint64_t)p.Nb, (cuuint64_t)nxb, (cuuint64_t)H};
+    cuuint64_t strides[3] = {16, (cuuint64_t)p.Nb * 16, (cuuint64_t)nxb * p.Nb * 16};
+    cuuint32_t box[4] = {8, (cuuint32_t)p.Nb, (cuuint32_t)(p.KW / 8), (cuuint32_t)p.R};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(&map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4,
                      const_cast<void*>(cost), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

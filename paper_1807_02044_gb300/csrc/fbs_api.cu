@@ -510,6 +510,7 @@ fbs_status fbs_aggregate(fbs_ctx* ctx, const float* cost, const uint8_t* guide, 
         {
             LaunchScope ls(ctx, FBS_KERNEL_OTHER, st);
             e = fbs::launch_hwd_to_xblock16(cost, H, W, D, bf16, cost16, st);
+            if (e == cudaSuccess) e = fbs::launch_xblock16_pad_rows(H, W, D, bf16, cost16, st);
             if (e == cudaSuccess) e = fbs::launch_pack_rgbx(guide, H, W, C, packed, st);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cost conversion launch");

@@ -297,7 +297,7 @@ cost_kernel(const int16_t* __restrict__ gplane, const int* __restrict__ splane, 
                     const int x = 8 * b + c;
                     v[c] = to_out<T>(x < nxs ? sp[stage_pos(x)] : 0.f);
                 }
-                T* o = out + (((size_t)y * ld + (x0 >> 3) + b) * D + dc + dd) * 8;
+                T* o = out + (((size_t)y * ld + (x0 >> 3) + b) * tc_block_rows(D) + dc + dd) * 8;
                 store8(o, v);
             }
         } else {
@@ -399,6 +399,8 @@ cudaError_t launch_cost_build_xblock16(const CostScratch& sc, const uint8_t* lef
                                        cudaStream_t stream)
 {
     const int nxb = (W + 7) / 8;
+    cudaError_t pe = launch_xblock16_pad_rows(H, W, D, bf16, cost, stream);
+    if (pe != cudaSuccess) return pe;
     if (mode == 0) {
         cudaError_t e = launch_stats(sc, left, right, H, W, C, stream);
         if (e != cudaSuccess) return e;

@@ -32,9 +32,18 @@ __host__ __device__ inline int rgbx_pitch(int W) { return (W + 1) & ~1; }
 cudaError_t launch_cost_build(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H, int W,
                               int C, int D, int ld, int mode, float tau, float* cost, cudaStream_t stream);
 
-// 16-bit x-blocked volume cost[((y*ceil(W/8) + x/8)*D + d)*8 + x%8], columns
-// x >= W of the last block written as 0; bf16 selects __nv_bfloat16, else __half.
-inline size_t xblock16_bytes(int H, int W, int D) { return (size_t)H * ((W + 7) / 8) * D * 8 * 2; }
+// 16-bit x-blocked volume cost[((y*ceil(W/8) + x/8)*Dp + d)*8 + x%8] with
+// Dp = tc_block_rows(D) rows per block: d < D the cost, D <= d < round_up(D,16)
+// zero, and (when Dp > round_up(D,16)) row round_up(D,16) all ones followed by
+// zero rows -- the ones row lets the tensor-core product also form the sum of
+// the weights.  Columns x >= W of the last block are 0.  bf16 selects
+// __nv_bfloat16, otherwise __half.
+__host__ __device__ inline int tc_block_rows(int D)
+{
+    const int n = (D + 15) / 16 * 16;
+    return n + 16 <= 256 ? n + 16 : n;
+}
+inline size_t xblock16_bytes(int H, int W, int D) { return (size_t)H * ((W + 7) / 8) * tc_block_rows(D) * 8 * 2; }
 cudaError_t launch_cost_build_xblock16(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H,
                                        int W, int C, int D, int mode, float tau, bool bf16, void* cost,
                                        cudaStream_t stream);
@@ -59,6 +68,8 @@ cudaError_t launch_aggregate_tc(const void* cost, const uint2* rgbx, int H, int 
 cudaError_t launch_pack_rgbx(const uint8_t* img, int H, int W, int C, uint2* rgbx, cudaStream_t stream);
 // FP32 [H][W][D] -> 16-bit x-blocked volume (rounded to nearest).
 cudaError_t launch_hwd_to_xblock16(const float* in, int H, int W, int D, bool bf16, void* out, cudaStream_t stream);
+// Rows D .. Dp-1 of every block of the x-blocked volume (zeros and the ones row).
+cudaError_t launch_xblock16_pad_rows(int H, int W, int D, bool bf16, void* out, cudaStream_t stream);
 
 // ---- context helpers for entry points defined outside fbs_api.cu -------------
 // Host-side checks of fbs_compute_disparity's arguments (sets the message).
