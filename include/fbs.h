@@ -132,6 +132,41 @@ fbs_status fbs_aggregate(fbs_ctx *ctx, const float *cost, const uint8_t *guide,
                          void *cuda_stream);
 
 /*
+ * Batched form (not a step of the method; a serving form of Sec. II-III):
+ * one stereo pair of a batch.  Pointers are device memory owned by the
+ * caller; parameters as for fbs_compute_disparity.
+ */
+typedef struct {
+    const uint8_t *left, *right;
+    int H, W, C, D, radius;
+    float sigma_s, sigma_r, tau;
+    int32_t *disp_int;          /* may be NULL */
+    float *disp_subpix;         /* may be NULL (not both) */
+} fbs_pair;
+
+/*
+ * fbs_compute_disparity for n pairs of uneven size, disparity count and
+ * radius (1 <= n <= 4096; pairs is a host array).  Each stage (block
+ * statistics, cost volumes, aggregation with WTA and Eq. (10)) is one
+ * persistent launch over all pairs, the three replayed as one CUDA graph per
+ * batch shape; results are bit-identical to fbs_compute_disparity.  FP32
+ * precision only (FBS_ERR_UNSUPPORTED otherwise).  The first call of a new
+ * shape (the list of H, W, C, D, radius and the cost mode) runs the
+ * library's autotuner: it times each schedule plan on the given data and
+ * keeps the fastest (recorded in the options' autotune_cache_path file when
+ * set, and read back from it by later contexts).  Scratch: every pair's cost
+ * volume at once (sum of H*W*round_up(D,4)*4 bytes plus statistics), owned
+ * by ctx.  Asynchronous on cuda_stream; the call returns once the pair table
+ * has been staged.
+ */
+fbs_status fbs_compute_disparity_batched(fbs_ctx *ctx, int n, const fbs_pair *pairs, void *cuda_stream);
+
+/* The plan the autotuner chose for this batch shape (0..3), or -1 if none
+ * yet.  plan = 2 * order + (aggregation CTAs per SM - 1), order 0 = largest
+ * pair first, 1 = as given. */
+fbs_status fbs_batch_plan(fbs_ctx *ctx, int n, const fbs_pair *pairs, int *plan);
+
+/*
  * fbs_compute_disparity_noalloc -- the whole path without allocating device
  * memory.  The paper has no counterpart: this is an interface variant for
  * callers that cannot call cudaMalloc once they run, such as a plugin inside
@@ -186,7 +221,8 @@ typedef enum {
     FBS_KERNEL_AGG_F32 = 1,     /* FP32 aggregation + WTA + Eq. (10) */
     FBS_KERNEL_AGG_TC = 2,      /* tensor-core aggregation + WTA + Eq. (10) */
     FBS_KERNEL_OTHER = 3,       /* every other kernel of the library */
-    FBS_KERNEL_KINDS = 4
+    FBS_KERNEL_BATCH = 4,       /* one batch graph (timed as a whole; its kernels count as COST and AGG_F32) */
+    FBS_KERNEL_KINDS = 5
 } fbs_kernel_kind;
 
 fbs_status fbs_profile(fbs_ctx *ctx, int enable);

@@ -38,14 +38,20 @@ FBS_KERNEL_COST = 0
 FBS_KERNEL_AGG_F32 = 1
 FBS_KERNEL_AGG_TC = 2
 FBS_KERNEL_OTHER = 3
-FBS_KERNEL_KINDS = 4
-KERNEL_NAMES = {0: "cost_build", 1: "aggregate_f32", 2: "aggregate_tc", 3: "other"}
+FBS_KERNEL_BATCH = 4
+FBS_KERNEL_KINDS = 5
+KERNEL_NAMES = {0: "cost_build", 1: "aggregate_f32", 2: "aggregate_tc", 3: "other", 4: "batch_graph"}
 
 # Every function the header declares, with (restype, argtypes).
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _F = ctypes.c_float
 _Z = ctypes.c_size_t
+
+
+class fbs_pair(ctypes.Structure):
+    _fields_ = [("left", _P), ("right", _P), ("H", _I), ("W", _I), ("C", _I), ("D", _I), ("radius", _I),
+                ("sigma_s", _F), ("sigma_r", _F), ("tau", _F), ("disp_int", _P), ("disp_subpix", _P)]
 
 
 class fbs_options(ctypes.Structure):
@@ -65,6 +71,8 @@ SIGNATURES = {
     "fbs_cost_volume": (_I, [_P, _P, _P, _I, _I, _I, _I, _F, _P, _P]),
     "fbs_aggregate": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _P, _P, _P, _P]),
     "fbs_compute_disparity_noalloc": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _F, _P, _P, _P]),
+    "fbs_compute_disparity_batched": (_I, [_P, _I, _P, _P]),
+    "fbs_batch_plan": (_I, [_P, _I, _P, ctypes.POINTER(_I)]),
     "fbs_profile": (_I, [_P, _I]),
     "fbs_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
 }
@@ -203,6 +211,31 @@ def fbs_aggregate(ctx, cost, guide, H, W, C, D, radius, sigma_s, sigma_r, agg_ou
                                    _addr(agg_out), _addr(disp_int), _addr(disp_subpix), _stream(stream)))
 
 
+def make_pairs(pairs):
+    """ctypes array of fbs_pair from dicts with keys left, right, H, W, C, D, radius,
+    sigma_s, sigma_r, tau, disp_int, disp_subpix (tensors or addresses)."""
+    arr = (fbs_pair * len(pairs))()
+    for a, q in zip(arr, pairs):
+        a.left, a.right = _addr(q["left"]), _addr(q["right"])
+        a.H, a.W, a.C, a.D, a.radius = q["H"], q["W"], q["C"], q["D"], q["radius"]
+        a.sigma_s, a.sigma_r, a.tau = q["sigma_s"], q["sigma_r"], q.get("tau", 0.0)
+        a.disp_int, a.disp_subpix = _addr(q.get("disp_int")), _addr(q.get("disp_subpix"))
+    return arr
+
+
+def fbs_compute_disparity_batched(ctx, pairs, stream=None):
+    """pairs: a ctypes fbs_pair array (see make_pairs) or a list of dicts."""
+    arr = pairs if isinstance(pairs, ctypes.Array) else make_pairs(pairs)
+    _check(ctx, lib().fbs_compute_disparity_batched(ctx, len(arr), ctypes.cast(arr, _P), _stream(stream)))
+
+
+def fbs_batch_plan(ctx, pairs):
+    arr = pairs if isinstance(pairs, ctypes.Array) else make_pairs(pairs)
+    plan = _I()
+    _check(ctx, lib().fbs_batch_plan(ctx, len(arr), ctypes.cast(arr, _P), ctypes.byref(plan)))
+    return plan.value
+
+
 def fbs_profile(ctx, enable):
     _check(ctx, lib().fbs_profile(ctx, int(bool(enable))))
 
@@ -218,9 +251,12 @@ def fbs_profile_read(ctx, kind):
 class Context:
     """Owning handle around fbs_create / fbs_destroy with tensor-level helpers."""
 
-    def __init__(self, device=0, cost=FBS_COST_NCC, prec=FBS_PREC_F32, workspace_cap=0):
+    def __init__(self, device=0, cost=FBS_COST_NCC, prec=FBS_PREC_F32, workspace_cap=0, autotune_cache_path=None):
         self.device = device
-        self.ctx = fbs_create(make_options(cost=cost, prec=prec, workspace_cap=workspace_cap), device)
+        self._opts = make_options(cost=cost, prec=prec, workspace_cap=workspace_cap)
+        self._cache_path = autotune_cache_path.encode() if autotune_cache_path else None
+        self._opts.autotune_cache_path = self._cache_path
+        self.ctx = fbs_create(self._opts, device)
 
     def close(self):
         if self.ctx:

@@ -120,21 +120,21 @@ __device__ __forceinline__ void load_guide_row(float4* dst, const uint8_t* __res
     }
 }
 
+// One 32 x 4 tile with top-left pixel (x0, y0), all disparities; ends with a
+// __syncthreads, so a CTA may call it for several tiles in a row.
 template <int KD, bool VEC>
-__global__ void __launch_bounds__(kThreads, 2)
-aggregate_f32_kernel(const float* __restrict__ cost, int ld, const uint8_t* __restrict__ guide, int H,
-                     int W, int C, int D, int rho, float neg_ks, float neg_kr,
-                     float* __restrict__ agg_out, int32_t* __restrict__ disp_int,
-                     float* __restrict__ disp_sub)
+__device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, int ld,
+                                               const uint8_t* __restrict__ guide, int H, int W, int C, int D,
+                                               int rho, float neg_ks, float neg_kr, float* __restrict__ agg_out,
+                                               int32_t* __restrict__ disp_int, float* __restrict__ disp_sub, int x0,
+                                               int y0, float4* smem_f4)
 {
     constexpr int DC = 8 * KD;   // disparities per chunk
     constexpr int NQ = KD / 4;   // float4 groups per thread
-    extern __shared__ float4 smem_f4[];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, g = tid >> 5;
     const int yi = lane >> 3, k = lane & 7;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int NC = kTX + 2 * rho;
     const int NT = 2 * rho + 1;
     const int WS = weight_stride(rho);
@@ -325,6 +325,41 @@ aggregate_f32_kernel(const float* __restrict__ cost, int ld, const uint8_t* __re
 }
 
 template <int KD, bool VEC>
+__global__ void __launch_bounds__(kThreads, 2)
+aggregate_f32_kernel(const float* __restrict__ cost, int ld, const uint8_t* __restrict__ guide, int H,
+                     int W, int C, int D, int rho, float neg_ks, float neg_kr,
+                     float* __restrict__ agg_out, int32_t* __restrict__ disp_int,
+                     float* __restrict__ disp_sub)
+{
+    extern __shared__ float4 smem_f4[];
+    aggregate_tile<KD, VEC>(cost, ld, guide, H, W, C, D, rho, neg_ks, neg_kr, agg_out, disp_int, disp_sub,
+                            blockIdx.x * kTX, blockIdx.y * kTY, smem_f4);
+}
+
+// Persistent form over a batch: CTAs claim (pair, tile) items from a counter;
+// pairs[p].agg_off is the first item of pair p, items of a pair are its tiles
+// in row-major order.  No CTA waits on another.
+__global__ void __launch_bounds__(kThreads, 2)
+aggregate_f32_batched_kernel(const BatchPair* __restrict__ pairs, int npairs, int nitems, int* __restrict__ counter)
+{
+    extern __shared__ float4 smem_f4[];
+    __shared__ int item_s;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = item_s;
+        __syncthreads();
+        if (item >= nitems) break;
+        const int pi = find_pair(pairs, npairs, item, &BatchPair::agg_off);
+        const BatchPair& bp = pairs[pi];
+        const int t = item - bp.agg_off;
+        const int ntx = (bp.W + kTX - 1) / kTX;
+        aggregate_tile<8, true>(bp.cost, bp.ld, bp.left, bp.H, bp.W, bp.C, bp.D, bp.radius, bp.neg_ks, bp.neg_kr,
+                                nullptr, bp.disp_int, bp.disp_sub, (t % ntx) * kTX, (t / ntx) * kTY, smem_f4);
+    }
+}
+
+template <int KD, bool VEC>
 cudaError_t launch_kd(const float* cost, int ld, const uint8_t* guide, int H, int W, int C, int D,
                       int rho, float neg_ks, float neg_kr, float* agg_out, int32_t* disp_int,
                       float* disp_sub, cudaStream_t stream)
@@ -340,6 +375,22 @@ cudaError_t launch_kd(const float* cost, int ld, const uint8_t* guide, int H, in
 }
 
 }  // namespace
+
+int agg_f32_tiles(int H, int W) { return ((W + kTX - 1) / kTX) * ((H + kTY - 1) / kTY); }
+
+cudaError_t prepare_aggregate_f32_batched(int max_radius, size_t* smem_out)
+{
+    const size_t smem = smem_bytes<64>(max_radius);
+    *smem_out = smem;
+    return cudaFuncSetAttribute(aggregate_f32_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_aggregate_f32_batched(const BatchPair* pairs, int npairs, int nitems, int* counter, int grid,
+                                         size_t smem, cudaStream_t stream)
+{
+    aggregate_f32_batched_kernel<<<grid, kThreads, smem, stream>>>(pairs, npairs, nitems, counter);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_aggregate_f32(const float* cost, int ld, const uint8_t* guide, int H, int W, int C,
                                  int D, int radius, float sigma_s, float sigma_r, float* agg_out,

@@ -46,7 +46,6 @@ constexpr int kTW = 16;         // tile width
 constexpr int kTH = 8;          // tile height
 constexpr int kM = kTW * kTH;   // 128 = MMA M = TMEM lanes
 constexpr int kProducerWarps = 16;                 // warps 0-15
-constexpr int kProducers = 32 * kProducerWarps;
 constexpr int kPasses = 32 / kProducerWarps;       // 32 pixel groups of 4 per tile
 constexpr int kEpiWarp0 = kProducerWarps;          // 4 epilogue warps: TMEM lane quarters 0-3
 constexpr int kEpilogue = 128;

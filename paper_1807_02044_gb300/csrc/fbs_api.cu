@@ -10,170 +10,12 @@
 #include <string>
 #include <vector>
 
-#include "fbs.h"
-#include "fbs_internal.cuh"
 
-struct fbs_ctx {
-    int device = 0;
-    fbs_options opt{};
-    cudaStream_t stream = nullptr;
-    void* ws = nullptr;          // cost volume scratch
-    size_t ws_bytes = 0;
-    void* io = nullptr;          // device staging for the host-buffer entry point
-    size_t io_bytes = 0;
-    std::string err;
-    int num_sms = 0;
-    int* derr = nullptr;         // device error word written by kernels with bounded waits
-    // kernel accounting
-    long long launches[FBS_KERNEL_KINDS] = {0, 0, 0, 0};
-    bool profiling = false;
-    struct Rec {
-        int kind;
-        cudaEvent_t a, b;
-    };
-    std::vector<Rec> recs;            // recorded launches since fbs_profile(ctx, 1)
-    std::vector<cudaEvent_t> spare;   // event pool
-};
+#include "fbs_context.cuh"
+
+using namespace fbs_detail;
 
 namespace {
-
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-fbs_status fail(fbs_ctx* ctx, fbs_status st, const char* fmt, ...)
-{
-    if (ctx) {
-        char buf[512];
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(buf, sizeof buf, fmt, ap);
-        va_end(ap);
-        ctx->err = buf;
-    }
-    return st;
-}
-
-fbs_status cuda_fail(fbs_ctx* ctx, cudaError_t e, const char* where)
-{
-    if (e == cudaErrorMemoryAllocation) return fail(ctx, FBS_ERR_OOM, "%s: %s", where, cudaGetErrorString(e));
-    return fail(ctx, FBS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
-}
-
-bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
-
-fbs_status check_shape(fbs_ctx* ctx, int H, int W, int C, int D)
-{
-    if (H < 1 || H > 16384 || W < 1 || W > 16384)
-        return fail(ctx, FBS_ERR_INVALID_ARG, "image size %dx%d outside 1..16384", W, H);
-    if (C != 1 && C != 3) return fail(ctx, FBS_ERR_INVALID_ARG, "channels C=%d must be 1 or 3", C);
-    if (D < 1 || D > 1024) return fail(ctx, FBS_ERR_INVALID_ARG, "disparity count D=%d outside 1..1024", D);
-    return FBS_OK;
-}
-
-fbs_status check_agg_params(fbs_ctx* ctx, int radius, float sigma_s, float sigma_r)
-{
-    if (radius < 0 || radius > 31) return fail(ctx, FBS_ERR_INVALID_ARG, "radius=%d outside 0..31", radius);
-    if (!finite_pos(sigma_s)) return fail(ctx, FBS_ERR_INVALID_ARG, "sigma_s must be finite and > 0");
-    if (!finite_pos(sigma_r)) return fail(ctx, FBS_ERR_INVALID_ARG, "sigma_r must be finite and > 0");
-    return FBS_OK;
-}
-
-fbs_status check_tau(fbs_ctx* ctx, float tau)
-{
-    if (ctx->opt.cost == FBS_COST_TAD && !(std::isfinite(tau) && tau >= 0.f))
-        return fail(ctx, FBS_ERR_INVALID_ARG, "tau must be finite and >= 0 in TAD mode");
-    return FBS_OK;
-}
-
-fbs_status check_options(fbs_ctx* ctx, const fbs_options* o)
-{
-    if (o->cost != FBS_COST_NCC && o->cost != FBS_COST_TAD)
-        return fail(ctx, FBS_ERR_INVALID_ARG, "unknown cost mode %d", o->cost);
-    if (o->prec != FBS_PREC_F32 && o->prec != FBS_PREC_BF16 && o->prec != FBS_PREC_F16)
-        return fail(ctx, FBS_ERR_INVALID_ARG, "unknown precision %d", o->prec);
-    return FBS_OK;
-}
-
-cudaStream_t pick_stream(fbs_ctx* ctx, void* s) { return s ? (cudaStream_t)s : ctx->stream; }
-
-cudaEvent_t take_event(fbs_ctx* ctx)
-{
-    if (!ctx->spare.empty()) {
-        cudaEvent_t e = ctx->spare.back();
-        ctx->spare.pop_back();
-        return e;
-    }
-    cudaEvent_t e = nullptr;
-    if (cudaEventCreate(&e) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    return e;
-}
-
-// Bracket one kernel launch for the accounting API.
-struct LaunchScope {
-    fbs_ctx* ctx;
-    int kind;
-    cudaStream_t st;
-    cudaEvent_t a = nullptr;
-    LaunchScope(fbs_ctx* c, int k, cudaStream_t s) : ctx(c), kind(k), st(s)
-    {
-        if (ctx->profiling) {
-            a = take_event(ctx);
-            if (a) cudaEventRecord(a, st);
-        }
-    }
-    ~LaunchScope()
-    {
-        ctx->launches[kind]++;
-        if (a) {
-            cudaEvent_t b = take_event(ctx);
-            if (b) {
-                cudaEventRecord(b, st);
-                ctx->recs.push_back({kind, a, b});
-            } else {
-                ctx->spare.push_back(a);
-            }
-        }
-    }
-};
-
-// Grow-only device scratch, bounded by the context's cap.
-fbs_status ensure(fbs_ctx* ctx, void** buf, size_t* have, size_t need, const char* what)
-{
-    if (need <= *have) return FBS_OK;
-    const size_t cap = ctx->opt.workspace_cap;
-    if (cap && ctx->ws_bytes + ctx->io_bytes - *have + need > cap)
-        return fail(ctx, FBS_ERR_OOM, "%s needs %zu bytes; workspace cap is %zu", what, need, cap);
-    if (*buf) {
-        cudaError_t e = cudaDeviceSynchronize();   // the old buffer may still be in use
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise before growing scratch");
-        cudaFree(*buf);
-        *buf = nullptr;
-        *have = 0;
-    }
-    cudaError_t e = cudaMalloc(buf, need);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        *buf = nullptr;
-        return fail(ctx, FBS_ERR_OOM, "cudaMalloc(%zu) for %s: %s", need, what, cudaGetErrorString(e));
-    }
-    *have = need;
-    return FBS_OK;
-}
 
 // Tensor-core form: 16-bit planar cost volume, tcgen05 aggregation.
 fbs_status run_path_tc(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C, int D,
@@ -333,6 +175,13 @@ fbs_status fbs_destroy(fbs_ctx* ctx)
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->io) cudaFree(ctx->io);
     if (ctx->derr) cudaFree(ctx->derr);
+    for (auto& kv : ctx->bgraphs) cudaGraphExecDestroy(kv.second.exec);
+    if (ctx->bpairs) cudaFree(ctx->bpairs);
+    if (ctx->bcounters) cudaFree(ctx->bcounters);
+    for (int k = 0; k < 2; ++k) {
+        if (ctx->bstage[k]) cudaFreeHost(ctx->bstage[k]);
+        if (ctx->bstage_done[k]) cudaEventDestroy(ctx->bstage_done[k]);
+    }
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return FBS_OK;

@@ -1,0 +1,198 @@
+// Private definition of the library context and the host helpers shared by
+// the translation units that implement the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fbs.h"
+#include "fbs_internal.cuh"
+
+// One cached batch: the work description uploaded from a pinned staging slot
+// and the CUDA graph that runs it.
+struct fbs_batch_graph {
+    cudaGraphExec_t exec = nullptr;
+    int slot = 0;
+};
+
+struct fbs_ctx {
+    int device = 0;
+    fbs_options opt{};
+    cudaStream_t stream = nullptr;
+    void* ws = nullptr;          // cost volume scratch
+    size_t ws_bytes = 0;
+    void* io = nullptr;          // device staging for the host-buffer entry point
+    size_t io_bytes = 0;
+    std::string err;
+    int num_sms = 0;
+    int* derr = nullptr;         // device error word written by kernels with bounded waits
+    // kernel accounting
+    long long launches[FBS_KERNEL_KINDS] = {};
+    bool profiling = false;
+    struct Rec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;            // recorded launches since fbs_profile(ctx, 1)
+    std::vector<cudaEvent_t> spare;   // event pool
+    // batched form
+    fbs::BatchPair* bpairs = nullptr;      // device pair table
+    int bpairs_cap = 0;
+    int* bcounters = nullptr;              // work counters of the three batched kernels
+    fbs::BatchPair* bstage[2] = {nullptr, nullptr};   // pinned staging slots for the table
+    cudaEvent_t bstage_done[2] = {nullptr, nullptr};  // slot free again when recorded work completes
+    int bslot = 0;
+    std::map<std::string, int> btuned;                 // batch shape -> chosen plan
+    std::map<std::string, fbs_batch_graph> bgraphs;    // plan-specific graph per slot
+    bool btuned_loaded = false;
+};
+
+namespace fbs_detail {
+
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+inline fbs_status fail(fbs_ctx* ctx, fbs_status st, const char* fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+inline fbs_status cuda_fail(fbs_ctx* ctx, cudaError_t e, const char* where)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, FBS_ERR_OOM, "%s: %s", where, cudaGetErrorString(e));
+    return fail(ctx, FBS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+inline bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
+
+inline fbs_status check_shape(fbs_ctx* ctx, int H, int W, int C, int D)
+{
+    if (H < 1 || H > 16384 || W < 1 || W > 16384)
+        return fail(ctx, FBS_ERR_INVALID_ARG, "image size %dx%d outside 1..16384", W, H);
+    if (C != 1 && C != 3) return fail(ctx, FBS_ERR_INVALID_ARG, "channels C=%d must be 1 or 3", C);
+    if (D < 1 || D > 1024) return fail(ctx, FBS_ERR_INVALID_ARG, "disparity count D=%d outside 1..1024", D);
+    return FBS_OK;
+}
+
+inline fbs_status check_agg_params(fbs_ctx* ctx, int radius, float sigma_s, float sigma_r)
+{
+    if (radius < 0 || radius > 31) return fail(ctx, FBS_ERR_INVALID_ARG, "radius=%d outside 0..31", radius);
+    if (!finite_pos(sigma_s)) return fail(ctx, FBS_ERR_INVALID_ARG, "sigma_s must be finite and > 0");
+    if (!finite_pos(sigma_r)) return fail(ctx, FBS_ERR_INVALID_ARG, "sigma_r must be finite and > 0");
+    return FBS_OK;
+}
+
+inline fbs_status check_tau(fbs_ctx* ctx, float tau)
+{
+    if (ctx->opt.cost == FBS_COST_TAD && !(std::isfinite(tau) && tau >= 0.f))
+        return fail(ctx, FBS_ERR_INVALID_ARG, "tau must be finite and >= 0 in TAD mode");
+    return FBS_OK;
+}
+
+inline fbs_status check_options(fbs_ctx* ctx, const fbs_options* o)
+{
+    if (o->cost != FBS_COST_NCC && o->cost != FBS_COST_TAD)
+        return fail(ctx, FBS_ERR_INVALID_ARG, "unknown cost mode %d", o->cost);
+    if (o->prec != FBS_PREC_F32 && o->prec != FBS_PREC_BF16 && o->prec != FBS_PREC_F16)
+        return fail(ctx, FBS_ERR_INVALID_ARG, "unknown precision %d", o->prec);
+    return FBS_OK;
+}
+
+inline cudaStream_t pick_stream(fbs_ctx* ctx, void* s) { return s ? (cudaStream_t)s : ctx->stream; }
+
+inline cudaEvent_t take_event(fbs_ctx* ctx)
+{
+    if (!ctx->spare.empty()) {
+        cudaEvent_t e = ctx->spare.back();
+        ctx->spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Bracket one kernel launch for the accounting API.
+struct LaunchScope {
+    fbs_ctx* ctx;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    LaunchScope(fbs_ctx* c, int k, cudaStream_t s) : ctx(c), kind(k), st(s)
+    {
+        if (ctx->profiling) {
+            a = take_event(ctx);
+            if (a) cudaEventRecord(a, st);
+        }
+    }
+    ~LaunchScope()
+    {
+        ctx->launches[kind]++;
+        if (a) {
+            cudaEvent_t b = take_event(ctx);
+            if (b) {
+                cudaEventRecord(b, st);
+                ctx->recs.push_back({kind, a, b});
+            } else {
+                ctx->spare.push_back(a);
+            }
+        }
+    }
+};
+
+// Grow-only device scratch, bounded by the context's cap.
+inline fbs_status ensure(fbs_ctx* ctx, void** buf, size_t* have, size_t need, const char* what)
+{
+    if (need <= *have) return FBS_OK;
+    const size_t cap = ctx->opt.workspace_cap;
+    if (cap && ctx->ws_bytes + ctx->io_bytes - *have + need > cap)
+        return fail(ctx, FBS_ERR_OOM, "%s needs %zu bytes; workspace cap is %zu", what, need, cap);
+    if (*buf) {
+        cudaError_t e = cudaDeviceSynchronize();   // the old buffer may still be in use
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise before growing scratch");
+        cudaFree(*buf);
+        *buf = nullptr;
+        *have = 0;
+    }
+    cudaError_t e = cudaMalloc(buf, need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return fail(ctx, FBS_ERR_OOM, "cudaMalloc(%zu) for %s: %s", need, what, cudaGetErrorString(e));
+    }
+    *have = need;
+    return FBS_OK;
+}
+
+}  // namespace fbs_detail

@@ -56,17 +56,11 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 
 // Per-pixel statistics of one image: g = channel sum, S = 3x3 box sum of g
 // (clamped), rv = 1/sqrt(9 Q - S^2) or 0 for a flat block.
-__global__ void __launch_bounds__(256)
-grey_stats_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int H, int W, int C,
-                  int16_t* __restrict__ g_out, int* __restrict__ s_out, float* __restrict__ rv_out,
-                  uint2* __restrict__ rgbx)
+__device__ __forceinline__ void stats_pixel(const uint8_t* __restrict__ src, int img, int H, int W, int C, int x,
+                                            int y, int16_t* __restrict__ g_out, int* __restrict__ s_out,
+                                            float* __restrict__ rv_out, uint2* __restrict__ rgbx)
 {
-    const int img = blockIdx.z;
-    const uint8_t* src = img == 0 ? L : R;
     const size_t plane = (size_t)H * W;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= W) return;
     int s = 0, q = 0;
 #pragma unroll
     for (int j = -1; j <= 1; ++j) {
@@ -92,6 +86,38 @@ grey_stats_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, 
     g_out[o] = (int16_t)g;
     s_out[o] = s;
     rv_out[o] = v > 0 ? rsqrtf((float)v) : 0.f;
+}
+
+__global__ void __launch_bounds__(256)
+grey_stats_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int H, int W, int C,
+                  int16_t* __restrict__ g_out, int* __restrict__ s_out, float* __restrict__ rv_out,
+                  uint2* __restrict__ rgbx)
+{
+    const int img = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= W) return;
+    stats_pixel(img == 0 ? L : R, img, H, W, C, x, blockIdx.y, g_out, s_out, rv_out, rgbx);
+}
+
+// Batched statistics: an item is one row of one pair (both images).
+__global__ void __launch_bounds__(256)
+grey_stats_batched_kernel(const BatchPair* __restrict__ pairs, int npairs, int nitems, int* __restrict__ counter)
+{
+    __shared__ int item_s;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = item_s;
+        __syncthreads();
+        if (item >= nitems) break;
+        const BatchPair& bp = pairs[find_pair(pairs, npairs, item, &BatchPair::stat_off)];
+        const int y = item - bp.stat_off;
+        if (bp.mode != 0) continue;   // TAD needs no statistics
+        for (int x = threadIdx.x; x < bp.W; x += blockDim.x)
+            for (int img = 0; img < 2; ++img)
+                stats_pixel(img == 0 ? bp.left : bp.right, img, bp.H, bp.W, bp.C, x, y, bp.sc.g, bp.sc.s, bp.sc.rv,
+                            bp.sc.rgbx);
+    }
 }
 
 template <typename T>
@@ -121,16 +147,14 @@ __device__ __forceinline__ void store8(T* o, const T (&v)[8])
 
 // MODE 0: NCC from the statistics planes; MODE 1: TAD from the raw images.
 // PLANAR false: out is [H][W][ld] (T = float); true: out is x-blocked [H][ld][D][8] with ld = ceil(W/8).
+// One row y and 128 pixels from x0, all disparities; ends with a __syncthreads.
 template <int MODE, typename T, bool PLANAR>
-__global__ void __launch_bounds__(kThreads)
-cost_kernel(const int16_t* __restrict__ gplane, const int* __restrict__ splane, const float* __restrict__ rvplane,
-            const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int H, int W, int C, int D, int ld,
-            float tau, T* __restrict__ out)
+__device__ __forceinline__ void cost_tile(const int16_t* __restrict__ gplane, const int* __restrict__ splane,
+                                          const float* __restrict__ rvplane, const uint8_t* __restrict__ L,
+                                          const uint8_t* __restrict__ R, int H, int W, int C, int D, int ld, float tau,
+                                          T* __restrict__ out, int x0, int y, int* smem_i)
 {
-    extern __shared__ int smem_i[];
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * kXS;
-    const int y = blockIdx.y;
     const int nxs = min(kXS, W - x0);
     const size_t plane = (size_t)H * W;
     // layout: stage [kDC][kStage] float | left grey [3][kXS+2] | right grey [3][kXS+kDC+2] |
@@ -314,6 +338,42 @@ cost_kernel(const int16_t* __restrict__ gplane, const int* __restrict__ splane, 
     }
 }
 
+template <int MODE, typename T, bool PLANAR>
+__global__ void __launch_bounds__(kThreads)
+cost_kernel(const int16_t* __restrict__ gplane, const int* __restrict__ splane, const float* __restrict__ rvplane,
+            const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int H, int W, int C, int D, int ld,
+            float tau, T* __restrict__ out)
+{
+    extern __shared__ int smem_i[];
+    cost_tile<MODE, T, PLANAR>(gplane, splane, rvplane, L, R, H, W, C, D, ld, tau, out, blockIdx.x * kXS, blockIdx.y,
+                               smem_i);
+}
+
+// Batched FP32 cost volumes [H][W][ld]: an item is (row, 128-pixel segment) of a pair.
+__global__ void __launch_bounds__(kThreads)
+cost_batched_kernel(const BatchPair* __restrict__ pairs, int npairs, int nitems, int* __restrict__ counter)
+{
+    extern __shared__ int smem_i[];
+    __shared__ int item_s;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = item_s;
+        __syncthreads();
+        if (item >= nitems) break;
+        const BatchPair& bp = pairs[find_pair(pairs, npairs, item, &BatchPair::cost_off)];
+        const int t = item - bp.cost_off;
+        const int nseg = (bp.W + kXS - 1) / kXS;
+        const int x0 = (t % nseg) * kXS, y = t / nseg;
+        if (bp.mode == 0)
+            cost_tile<0, float, false>(bp.sc.g, bp.sc.s, bp.sc.rv, bp.left, bp.right, bp.H, bp.W, bp.C, bp.D, bp.ld,
+                                       bp.tau, bp.cost, x0, y, smem_i);
+        else
+            cost_tile<1, float, false>(bp.sc.g, bp.sc.s, bp.sc.rv, bp.left, bp.right, bp.H, bp.W, bp.C, bp.D, bp.ld,
+                                       bp.tau, bp.cost, x0, y, smem_i);
+    }
+}
+
 size_t cost_smem_bytes()
 {
     return sizeof(float) * (size_t)kDC * kStage +
@@ -343,6 +403,30 @@ cudaError_t launch_stats(const CostScratch& sc, const uint8_t* left, const uint8
 }
 
 }  // namespace
+
+int stats_items(int H, int W) { return H; }
+int cost_items(int H, int W) { return H * ((W + kXS - 1) / kXS); }
+size_t cost_kernel_smem() { return cost_smem_bytes(); }
+
+cudaError_t prepare_cost_batched()
+{
+    return cudaFuncSetAttribute(cost_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)cost_smem_bytes());
+}
+
+cudaError_t launch_stats_batched(const BatchPair* pairs, int npairs, int nitems, int* counter, int grid,
+                                 cudaStream_t stream)
+{
+    grey_stats_batched_kernel<<<grid, 256, 0, stream>>>(pairs, npairs, nitems, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cost_batched(const BatchPair* pairs, int npairs, int nitems, int* counter, int grid,
+                                cudaStream_t stream)
+{
+    cost_batched_kernel<<<grid, kThreads, cost_smem_bytes(), stream>>>(pairs, npairs, nitems, counter);
+    return cudaGetLastError();
+}
 
 size_t cost_scratch_bytes(int H, int W)
 {

@@ -71,6 +71,46 @@ cudaError_t launch_hwd_to_xblock16(const float* in, int H, int W, int D, bool bf
 // Rows D .. Dp-1 of every block of the x-blocked volume (zeros and the ones row).
 cudaError_t launch_xblock16_pad_rows(int H, int W, int D, bool bf16, void* out, cudaStream_t stream);
 
+// ---- batched form: one persistent launch per stage over many pairs ------------
+// Device-side description of one pair of a batch.  *_off is the index of the
+// pair's first work item in each batched kernel (items of a pair contiguous,
+// pairs in batch order, offsets ascending).
+struct BatchPair {
+    const uint8_t* left;
+    const uint8_t* right;
+    int H, W, C, D, radius, ld, mode;
+    float neg_ks, neg_kr, tau;
+    CostScratch sc;
+    float* cost;
+    int32_t* disp_int;
+    float* disp_sub;
+    int stat_off, cost_off, agg_off;
+};
+#ifdef __CUDACC__
+__device__ __forceinline__ int find_pair(const BatchPair* pairs, int n, int item, int BatchPair::*off)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pairs[mid].*off <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+#endif
+// work items per pair
+int stats_items(int H, int W);
+int cost_items(int H, int W);
+int agg_f32_tiles(int H, int W);
+size_t cost_kernel_smem();
+cudaError_t prepare_cost_batched();
+cudaError_t launch_stats_batched(const BatchPair* pairs, int npairs, int nitems, int* counter, int grid,
+                                 cudaStream_t stream);
+cudaError_t launch_cost_batched(const BatchPair* pairs, int npairs, int nitems, int* counter, int grid,
+                                cudaStream_t stream);
+cudaError_t prepare_aggregate_f32_batched(int max_radius, size_t* smem_out);
+cudaError_t launch_aggregate_f32_batched(const BatchPair* pairs, int npairs, int nitems, int* counter, int grid,
+                                         size_t smem, cudaStream_t stream);
+
 // ---- context helpers for entry points defined outside fbs_api.cu -------------
 // Host-side checks of fbs_compute_disparity's arguments (sets the message).
 fbs_status check_path_args(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C,

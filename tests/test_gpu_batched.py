@@ -1,0 +1,106 @@
+"""Batched form through the C ABI: uneven pairs in one persistent launch per
+stage must reproduce fbs_compute_disparity bit for bit (same tile code, same
+data, same order), and the autotuner's choice must persist."""
+
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fbs():
+    from paper_1807_02044_gb300 import build as b
+    b.build()
+    import paper_1807_02044_gb300 as m
+    return m
+
+
+def _batch(seed, n=9):
+    rng = np.random.default_rng(seed)
+    pairs = []
+    for i in range(n):
+        H, W = int(rng.integers(20, 90)), int(rng.integers(33, 160))
+        C = int(rng.choice([1, 3]))
+        D = int(rng.choice([8, 16, 21, 32, 40, 70]))
+        r = int(rng.choice([0, 1, 2, 4, 7]))
+        L = rng.integers(0, 256, size=(H, W, C)).astype(np.uint8)
+        R = np.roll(L, -int(rng.integers(0, 6)), axis=1)
+        pairs.append(dict(left=torch.from_numpy(L).cuda(), right=torch.from_numpy(R).cuda(), H=H, W=W, C=C, D=D,
+                          radius=r, sigma_s=float(max(r, 1)), sigma_r=12.0, tau=20.0,
+                          disp_int=torch.empty((H, W), dtype=torch.int32, device="cuda"),
+                          disp_subpix=torch.empty((H, W), dtype=torch.float32, device="cuda")))
+    return pairs
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batched_equals_per_pair_bit_for_bit(fbs, mode):
+    pairs = _batch(3 + mode)
+    with fbs.Context(0, cost=mode) as ctx:
+        ref = []
+        for q in pairs:
+            di, ds = ctx.compute_disparity(q["left"], q["right"], q["D"], q["radius"], q["sigma_s"], q["sigma_r"],
+                                           q["tau"])
+            ref.append((di, ds))
+        torch.cuda.synchronize()
+        fbs.fbs_compute_disparity_batched(ctx.ctx, pairs, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        fbs.fbs_sync(ctx.ctx)
+        for q, (di, ds) in zip(pairs, ref):
+            assert torch.equal(q["disp_int"], di)
+            assert torch.equal(q["disp_subpix"], ds)
+        plan = fbs.fbs_batch_plan(ctx.ctx, pairs)
+        assert 0 <= plan < 4
+        # replay with fresh output buffers and new images of the same shapes
+        pairs2 = _batch(3 + mode)
+        for q in pairs2:
+            q["left"] = torch.flip(q["left"], dims=[0]).contiguous()
+        fbs.fbs_compute_disparity_batched(ctx.ctx, pairs2, torch.cuda.current_stream())
+        for q in pairs2:
+            di, ds = ctx.compute_disparity(q["left"], q["right"], q["D"], q["radius"], q["sigma_s"], q["sigma_r"],
+                                           q["tau"])
+            torch.cuda.synchronize()
+            assert torch.equal(q["disp_int"], di)
+            assert torch.equal(q["disp_subpix"], ds)
+
+
+def test_batched_matches_oracle_on_a_member(fbs, oracle_mod):
+    from tests._compare import check_disparities
+    pairs = _batch(11, n=4)
+    with fbs.Context(0) as ctx:
+        fbs.fbs_compute_disparity_batched(ctx.ctx, pairs, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+    for q in pairs:
+        L, R = q["left"].cpu().numpy(), q["right"].cpu().numpy()
+        ref_di, ref_ds, ref_agg = oracle_mod.fbs(L, R, q["D"], q["radius"], q["sigma_s"], q["sigma_r"], want_agg=True)
+        check_disparities(q["disp_int"].cpu().numpy(), q["disp_subpix"].cpu().numpy(), ref_agg, ref_di, ref_ds, 2.0)
+
+
+def test_autotune_choice_is_stored_and_reloaded(fbs, tmp_path):
+    path = str(tmp_path / "tune.txt")
+    pairs = _batch(5, n=5)
+    with fbs.Context(0, autotune_cache_path=path) as ctx:
+        assert fbs.fbs_batch_plan(ctx.ctx, pairs) == -1
+        fbs.fbs_compute_disparity_batched(ctx.ctx, pairs, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        plan = fbs.fbs_batch_plan(ctx.ctx, pairs)
+    assert os.path.exists(path) and open(path).read().strip().endswith(str(plan))
+    with fbs.Context(0, autotune_cache_path=path) as ctx2:
+        assert fbs.fbs_batch_plan(ctx2.ctx, pairs) == plan
+
+
+def test_batched_rejects_bad_pairs(fbs):
+    pairs = _batch(7, n=3)
+    pairs[1]["radius"] = 40
+    with fbs.Context(0) as ctx:
+        with pytest.raises(fbs.FBSError) as ei:
+            fbs.fbs_compute_disparity_batched(ctx.ctx, pairs)
+        assert ei.value.status == fbs.FBS_ERR_INVALID_ARG and "pair 1" in str(ei.value)
+        ctx.set_options(prec=fbs.FBS_PREC_BF16)
+        pairs[1]["radius"] = 2
+        with pytest.raises(fbs.FBSError) as ei:
+            fbs.fbs_compute_disparity_batched(ctx.ctx, pairs)
+        assert ei.value.status == fbs.FBS_ERR_UNSUPPORTED
