@@ -68,6 +68,10 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
+    ap.add_argument("--batched", action="store_true",
+                    help="time the batched form on 64 uneven pairs (320..1024 x 240..768, D in {32,64,128,192}, "
+                         "radius in {4,7,11}) instead of the single-pair workload")
+    ap.add_argument("--batch-size", type=int, default=64)
     return ap.parse_args()
 
 
@@ -441,10 +445,106 @@ def run_ours(args):
     return 0
 
 
+def _render_batch_member(spec):
+    from synth import make_pair
+    p = make_pair("rgb640x480_d64_r7", spec["seed"], H=spec["H"], W=spec["W"], D=spec["D"], radius=spec["radius"])
+    return p.left, p.right
+
+
+def run_batched(args):
+    """One step = one batch of uneven pairs through fbs_compute_disparity_batched
+    (FP32, one CUDA graph of three persistent launches).  Beside it: the same
+    pairs as sequential per-pair calls, FP32 and BF16 tensor-core form."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    from synth import random_batch_specs
+    specs = random_batch_specs(args.seed, args.batch_size)
+    # render in worker processes started with spawn, before the first GPU call
+    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
+        imgs = list(ex.map(_render_batch_member, specs))
+    import torch
+
+    import paper_1807_02044_gb300 as fbs
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    steps = args.steps if args.steps is not None else 10
+    warmup = max(3, args.warmup if args.warmup is not None else 3)
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    pairs = []
+    for spec, (L, R) in zip(specs, imgs):
+        H, W = spec["H"], spec["W"]
+        pairs.append(dict(left=torch.from_numpy(L).to(dev), right=torch.from_numpy(R).to(dev), H=H, W=W, C=3,
+                          D=spec["D"], radius=spec["radius"], sigma_s=spec["sigma_s"], sigma_r=spec["sigma_r"],
+                          tau=spec["tau"], disp_int=torch.empty((H, W), dtype=torch.int32, device=dev),
+                          disp_subpix=torch.empty((H, W), dtype=torch.float32, device=dev)))
+    taps = sum(q["H"] * q["W"] * q["D"] * (2 * q["radius"] + 1) ** 2 for q in pairs)
+
+    def timed(fn, ctx):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                flush.fill_(1)
+                fn()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            torch.cuda.synchronize()
+            fbs.fbs_profile(ctx.ctx, 1)
+            for a, b in evs:
+                flush.fill_(1)
+                a.record(stream)
+                fn()
+                b.record(stream)
+            torch.cuda.synchronize()
+            fbs.fbs_profile(ctx.ctx, 0)
+        fbs.fbs_sync(ctx.ctx)
+        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+        launches = sum(fbs.fbs_profile_read(ctx.ctx, k)[1] for k in range(fbs.FBS_KERNEL_KINDS))
+        return ms, launches
+
+    arr = fbs.make_pairs(pairs)
+    with fbs.Context(0) as ctx:
+        t_batch, launches = timed(lambda: fbs.fbs_compute_disparity_batched(ctx.ctx, arr, stream), ctx)
+        plan = fbs.fbs_batch_plan(ctx.ctx, arr)
+        ref = [(q["disp_int"].clone(), q["disp_subpix"].clone()) for q in pairs]
+
+        def seq():
+            for q in pairs:
+                fbs.fbs_compute_disparity(ctx.ctx, q["left"], q["right"], q["H"], q["W"], 3, q["D"], q["radius"],
+                                          q["sigma_s"], q["sigma_r"], q["tau"], q["disp_int"], q["disp_subpix"],
+                                          stream)
+        t_seq, _ = timed(seq, ctx)
+        torch.cuda.synchronize()
+        identical = all(torch.equal(q["disp_int"], r[0]) and torch.equal(q["disp_subpix"], r[1])
+                        for q, r in zip(pairs, ref))
+    with fbs.Context(0, prec=fbs.FBS_PREC_BF16) as ctx16:
+        def seq16():
+            for q in pairs:
+                fbs.fbs_compute_disparity(ctx16.ctx, q["left"], q["right"], q["H"], q["W"], 3, q["D"], q["radius"],
+                                          q["sigma_s"], q["sigma_r"], q["tau"], q["disp_int"], q["disp_subpix"],
+                                          stream)
+        t_seq16, _ = timed(seq16, ctx16)
+    n = len(pairs)
+    out = {"metric": METRIC, "value": taps / (t_batch * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": steps,
+           "warmup": warmup, "ms_per_step": t_batch, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"batch{n}_uneven_320-1024x240-768_d32-192_r4-11", "pairs": n, "taps": taps,
+                      "seed": args.seed, "plan": plan, "graph": "stats + cost + aggregation, persistent",
+                      "l2": "512 MiB flush write before every step, outside the per-step CUDA-event timing"},
+           "pairs_per_s": n / (t_batch * 1e-3), "gpu_launches": launches,
+           "batched_equals_sequential_bitwise": identical,
+           "sequential_f32": {"ms_per_batch": t_seq, "gtaps_per_s": taps / (t_seq * 1e-3) / 1e9},
+           "sequential_bf16": {"ms_per_batch": t_seq16, "gtaps_per_s": taps / (t_seq16 * 1e-3) / 1e9},
+           "roofline": None, "cpu_baseline": None, "e2e": None}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batched:
+        return run_batched(args)
     return run_ours(args)
 
 
