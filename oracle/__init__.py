@@ -2,9 +2,11 @@
 
 Only the tests, the smoke check and the benchmark's CPU-baseline leg may
 import this package.  The product path (the CUDA library and its binding)
-never does.  The C source ``fbs_oracle.c`` holds the arithmetic; this module
-compiles it with gcc on first use (or from ``build()``) and wraps it with
-ctypes, plus the e_PEP metric of Eq. (11)-(12).
+never does.  The C sources ``fbs_oracle.c`` (the method) and
+``band_oracle.c`` (the band form's features, bands and targets) hold the
+arithmetic; this module compiles them with gcc on first use (or from
+``build()``) and wraps them with ctypes, plus the e_PEP metric of
+Eq. (11)-(12).  The band network's FP64 oracle is ``band_net.py``.
 """
 
 from __future__ import annotations
@@ -17,7 +19,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "fbs_oracle.c")
+_SRCS = [os.path.join(_HERE, "fbs_oracle.c"), os.path.join(_HERE, "band_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -30,10 +32,11 @@ COST_TAD = 1
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain -O2, no fast-math, no vector ISA flags)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(f) for f in _SRCS)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math",
-                               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+                               "-ffp-contract=off", *_SRCS, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -60,6 +63,13 @@ def _load():
             lib.oracle_fbs_rows.restype = I
             lib.oracle_fbs_points.argtypes = [P, P, I, I, I, I, I, Dd, Dd, Dd, I, I, P, P, P, P, P]
             lib.oracle_fbs_points.restype = I
+            lib.oracle_band_downsample.argtypes = [P, I, I, I, P]
+            lib.oracle_band_features.argtypes = [P, P, I, I, I, I, P, P]
+            lib.oracle_band_features.restype = I
+            lib.oracle_band_limits.argtypes = [P, P, I, I, I, ctypes.c_float, P, P]
+            lib.oracle_fbs_band_points.argtypes = [P, P, I, I, I, I, I, Dd, Dd, I, P, P, P, P, P, P, P]
+            lib.oracle_fbs_band_points.restype = I
+            lib.oracle_band_targets.argtypes = [P, P, I, I, I, I, P, P, P]
             _lib = lib
     return _lib
 
@@ -159,6 +169,79 @@ def fbs_points(left, right, D, radius, sigma_s, sigma_r, xs, ys, tau=0.0, mode=C
     if rc != 0:
         raise MemoryError("oracle_fbs_points could not allocate")
     return di, ds, agg
+
+
+# ---------------------------------------------------------------------------
+# Band form (readings B1-B6 of band_oracle.c)
+# ---------------------------------------------------------------------------
+def quarter_shape(H, W, D):
+    return (H + 3) // 4, (W + 3) // 4, (D + 3) // 4
+
+
+def band_downsample(img):
+    """B1: quarter-resolution intensity (int32, Hq x Wq)."""
+    I = _img(img)
+    H, W, C = I.shape
+    out = np.empty(((H + 3) // 4, (W + 3) // 4), np.int32)
+    _load().oracle_band_downsample(_ptr(I), H, W, C, _ptr(out))
+    return out
+
+
+def band_features(left, right, D):
+    """B1-B3: features [Hq][Wq][6] (float32) and the coarse winner e* (int32)."""
+    L, R = _img(left), _img(right)
+    H, W, C = L.shape
+    Hq, Wq, _ = quarter_shape(H, W, D)
+    feat = np.empty((Hq, Wq, 6), np.float32)
+    est = np.empty((Hq, Wq), np.int32)
+    if _load().oracle_band_features(_ptr(L), _ptr(R), H, W, C, D, _ptr(feat), _ptr(est)) != 0:
+        raise MemoryError("oracle_band_features could not allocate")
+    return feat, est
+
+
+def band_limits(centre, conf, D, half_band, theta):
+    """B4: per-pixel band [lo, hi] (int32 arrays of the input's shape)."""
+    c = np.ascontiguousarray(centre, np.float32)
+    k = np.ascontiguousarray(conf, np.float32)
+    lo = np.empty(c.shape, np.int32)
+    hi = np.empty(c.shape, np.int32)
+    _load().oracle_band_limits(_ptr(c), _ptr(k), c.size, D, int(half_band), float(theta), _ptr(lo), _ptr(hi))
+    return lo, hi
+
+
+def fbs_band_points(left, right, D, radius, sigma_s, sigma_r, xs, ys, lo, hi):
+    """B5 at isolated pixels with bands [lo_i, hi_i]; returns (d_int, d_sub, agg[n, D])
+    with NaN outside each band."""
+    L, R = _img(left), _img(right)
+    H, W, C = L.shape
+    xs = np.ascontiguousarray(xs, np.int32)
+    ys = np.ascontiguousarray(ys, np.int32)
+    lo = np.ascontiguousarray(lo, np.int32)
+    hi = np.ascontiguousarray(hi, np.int32)
+    n = xs.size
+    di = np.empty(n, np.int32)
+    ds = np.empty(n, np.float64)
+    agg = np.empty((n, D), np.float64)
+    rc = _load().oracle_fbs_band_points(_ptr(L), _ptr(R), H, W, C, D, int(radius), float(sigma_s),
+                                        float(sigma_r), n, _ptr(xs), _ptr(ys), _ptr(lo), _ptr(hi),
+                                        _ptr(agg), _ptr(di), _ptr(ds))
+    if rc != 0:
+        raise MemoryError("oracle_fbs_band_points could not allocate")
+    return di, ds, agg
+
+
+def band_targets(label_int, label_sub, D, half_band, centre_q):
+    """B6: centre target t (float64) and confidence target y (int32), Hq x Wq."""
+    li = np.ascontiguousarray(label_int, np.int32)
+    ls = np.ascontiguousarray(label_sub, np.float64)
+    H, W = li.shape
+    cq = np.ascontiguousarray(centre_q, np.float64)
+    Hq, Wq = (H + 3) // 4, (W + 3) // 4
+    assert cq.shape == (Hq, Wq)
+    t = np.empty((Hq, Wq), np.float64)
+    y = np.empty((Hq, Wq), np.int32)
+    _load().oracle_band_targets(_ptr(li), _ptr(ls), H, W, D, int(half_band), _ptr(cq), _ptr(t), _ptr(y))
+    return t, y
 
 
 def e_pep(estimate, truth, eps, mask=None):

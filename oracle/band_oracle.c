@@ -1,0 +1,251 @@
+/*
+ * Oracle of the learned band proposal (TEST INFRASTRUCTURE ONLY; nothing on
+ * the product path links, loads or calls this file, and it shares no code
+ * with the CUDA path).
+ *
+ * The paper names, as future work (Sec. V), restricting the disparity search
+ * range of each pixel to cut the aggregation work.  The band form does this:
+ * a small network proposes a per-pixel disparity centre and a confidence; a
+ * pixel with enough confidence aggregates only the disparities of a band
+ * around its centre, every other pixel keeps the full range.  This file
+ * holds the plain definitions of the non-network parts:
+ *
+ *   quarter-resolution input features   oracle_band_features
+ *   per-pixel band from centre/conf     oracle_band_limits
+ *   Eq. (6)-(10) restricted to a band   oracle_fbs_band_points
+ *   training targets from plain FBS     oracle_band_targets
+ *
+ * The network itself (six 3x3 convolutions, its loss and gradients, Adam)
+ * is written in numpy in band_net.py.
+ *
+ * Readings (also listed in the design notes):
+ *   B1  quarter resolution: Hq = ceil(H/4), Wq = ceil(W/4), Dq = ceil(D/4);
+ *       the quarter-resolution intensity of block (X, Y) is the integer sum of
+ *       the channel sums over the 4x4 block, its pixels clamped to the image.
+ *   B2  coarse cost: Eq. (1)-(3) with varrho = 1 on the quarter-resolution
+ *       intensity, quarter disparities e in [0, Dq), the same boundary rules
+ *       as the full-resolution cost (clamped blocks, cost 2 when X - e < 0,
+ *       c = 0 for a flat block); cost K = 1 - c.  Sums are exact integers;
+ *       the normalisation is evaluated in FP32 with correctly rounded
+ *       operations in a fixed order, so the kernels reach the same bits and
+ *       the same winners (the winner is an integer decided by floating point,
+ *       and both sides decide it in the same precision).
+ *   B3  features per quarter pixel (all FP32, same operation order):
+ *         f0 = G_l / (16 * 255 * C) - 0.5      (left intensity)
+ *         f1 = e* / Dq                         (coarse winner, smallest e on ties)
+ *         f2 = K(e*)                           (its cost)
+ *         f3 = min(K2 - K(e*), 1)              (margin to the best e with |e - e*| >= 2;
+ *                                               K2 = 2 when there is none)
+ *         f4 = K(e* - 1) - K(e*)   (2 - K(e*) at e* = 0)
+ *         f5 = K(e* + 1) - K(e*)   (2 - K(e*) at e* = Dq - 1)
+ *   B4  band of a full-resolution pixel from its centre c and confidence k:
+ *       full range [0, D-1] when !(k >= theta) or c is not finite; otherwise
+ *       m = floor(c + 0.5) in FP32, clamped to [0, D-1], band
+ *       [max(m - h, 0), min(m + h, D - 1)].
+ *   B5  band FBS: Agg(p, d) of Eq. (6) for d in the band only; the winner is
+ *       the smallest d of the band with the least Agg; Eq. (10) is applied
+ *       only when both neighbours d* - 1 and d* + 1 lie in the band (the band
+ *       ends play the role of 0 and D - 1).
+ *   B6  targets of quarter pixel i from plain full-range FBS (integer d*,
+ *       subpixel ds) over the in-image pixels of its 4x4 block: centre target
+ *       t = mean of ds (FP64 here); confidence target y = 1 iff every d* of
+ *       the block lies in [m - h + 1, m + h - 1], m being the band centre of
+ *       B4 for the predicted centre c_i = 4 (e*_i + o0_i), so that the band
+ *       holds every winner and both of its neighbours.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+static int bclampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* B1: quarter-resolution intensity plane of one image, Hq x Wq int32. */
+void oracle_band_downsample(const uint8_t *img, int H, int W, int C, int32_t *gq)
+{
+    const int Hq = (H + 3) / 4, Wq = (W + 3) / 4;
+    for (int Y = 0; Y < Hq; ++Y) {
+        for (int X = 0; X < Wq; ++X) {
+            int32_t s = 0;
+            for (int j = 0; j < 4; ++j) {
+                const int y = bclampi(4 * Y + j, 0, H - 1);
+                for (int i = 0; i < 4; ++i) {
+                    const int x = bclampi(4 * X + i, 0, W - 1);
+                    for (int c = 0; c < C; ++c) s += img[((size_t)y * W + x) * C + c];
+                }
+            }
+            gq[(size_t)Y * Wq + X] = s;
+        }
+    }
+}
+
+/* B2: coarse cost K(X, Y, e) from the two quarter-resolution planes. */
+static float coarse_cost(const int32_t *gl, const int32_t *gr, int Hq, int Wq, int X, int Y, int e)
+{
+    if (X - e < 0) return 2.0f;
+    int64_t Sl = 0, Ql = 0, Sr = 0, Qr = 0, P = 0;
+    for (int j = -1; j <= 1; ++j) {
+        const int y = bclampi(Y + j, 0, Hq - 1);
+        for (int i = -1; i <= 1; ++i) {
+            const int64_t a = gl[(size_t)y * Wq + bclampi(X + i, 0, Wq - 1)];
+            const int64_t b = gr[(size_t)y * Wq + bclampi(X - e + i, 0, Wq - 1)];
+            Sl += a;
+            Ql += a * a;
+            Sr += b;
+            Qr += b * b;
+            P += a * b;
+        }
+    }
+    const int64_t Vl = 9 * Ql - Sl * Sl;
+    const int64_t Vr = 9 * Qr - Sr * Sr;
+    if (Vl == 0 || Vr == 0) return 1.0f;
+    const int64_t num = 9 * P - Sl * Sr;
+    const float vv = (float)Vl * (float)Vr;
+    const float c = (float)num / sqrtf(vv);
+    return 1.0f - c;
+}
+
+/*
+ * B1-B3: features [Hq][Wq][6] (FP32) and the coarse winner e* [Hq][Wq] of a
+ * pair.  Scratch is allocated here.  Returns 0, or -1 when out of memory.
+ */
+int oracle_band_features(const uint8_t *L, const uint8_t *R, int H, int W, int C, int D, float *feat,
+                         int32_t *estar)
+{
+    const int Hq = (H + 3) / 4, Wq = (W + 3) / 4, Dq = (D + 3) / 4;
+    int32_t *gl = (int32_t *)malloc(sizeof(int32_t) * (size_t)Hq * Wq);
+    int32_t *gr = (int32_t *)malloc(sizeof(int32_t) * (size_t)Hq * Wq);
+    float *K = (float *)malloc(sizeof(float) * (size_t)Dq);
+    if (!gl || !gr || !K) { free(gl); free(gr); free(K); return -1; }
+    oracle_band_downsample(L, H, W, C, gl);
+    oracle_band_downsample(R, H, W, C, gr);
+    const float gscale = (float)(16 * 255 * C);
+    for (int Y = 0; Y < Hq; ++Y) {
+        for (int X = 0; X < Wq; ++X) {
+            for (int e = 0; e < Dq; ++e) K[e] = coarse_cost(gl, gr, Hq, Wq, X, Y, e);
+            int best = 0;
+            for (int e = 1; e < Dq; ++e)
+                if (K[e] < K[best]) best = e;
+            float k2 = 2.0f;
+            for (int e = 0; e < Dq; ++e)
+                if (abs(e - best) >= 2 && K[e] < k2) k2 = K[e];
+            const float k1 = K[best];
+            const float km = best > 0 ? K[best - 1] : 2.0f;
+            const float kp = best < Dq - 1 ? K[best + 1] : 2.0f;
+            float *f = feat + ((size_t)Y * Wq + X) * 6;
+            f[0] = (float)gl[(size_t)Y * Wq + X] / gscale - 0.5f;
+            f[1] = (float)best / (float)Dq;
+            f[2] = k1;
+            const float margin = k2 - k1;
+            f[3] = margin < 1.0f ? margin : 1.0f;
+            f[4] = km - k1;
+            f[5] = kp - k1;
+            estar[(size_t)Y * Wq + X] = best;
+        }
+    }
+    free(gl);
+    free(gr);
+    free(K);
+    return 0;
+}
+
+/* B4: band [lo, hi] of every pixel of an H x W centre/confidence pair. */
+void oracle_band_limits(const float *centre, const float *conf, int n, int D, int h, float theta, int32_t *lo,
+                        int32_t *hi)
+{
+    for (int p = 0; p < n; ++p) {
+        const float c = centre[p], k = conf[p];
+        if (!(k >= theta) || !isfinite(c)) {
+            lo[p] = 0;
+            hi[p] = D - 1;
+            continue;
+        }
+        float m = floorf(c + 0.5f);
+        if (m < 0.0f) m = 0.0f;
+        if (m > (float)(D - 1)) m = (float)(D - 1);
+        const int mi = (int)m;
+        lo[p] = mi - h < 0 ? 0 : mi - h;
+        hi[p] = mi + h > D - 1 ? D - 1 : mi + h;
+    }
+}
+
+/* Eq. (1)-(3) cost and Eq. (7)-(8) weight: the pinned definitions of fbs_oracle.c. */
+double oracle_cost(const uint8_t *L, const uint8_t *R, int H, int W, int C, int u, int v, int d, int mode,
+                   double tau);
+double oracle_weight(const uint8_t *guide, int W, int C, int u, int v, int x, int y, double gamma_d,
+                     double gamma_r);
+
+/*
+ * B5 at isolated pixels (xs[i], ys[i]) with band [lo_i, hi_i] each (NCC cost).
+ * agg_out (nullable) receives n x D values, NaN outside each band.
+ */
+int oracle_fbs_band_points(const uint8_t *L, const uint8_t *R, int H, int W, int C, int D, int rho, double gamma_d,
+                           double gamma_r, int n, const int32_t *xs, const int32_t *ys, const int32_t *lo,
+                           const int32_t *hi, double *agg_out, int32_t *d_int, double *d_sub)
+{
+    double *a = (double *)malloc(sizeof(double) * (size_t)D);
+    if (!a) return -1;
+    for (int i = 0; i < n; ++i) {
+        const int u = xs[i], v = ys[i], b0 = lo[i], b1 = hi[i];
+        for (int d = 0; d < D; ++d) a[d] = NAN;
+        for (int d = b0; d <= b1; ++d) {
+            double num = 0.0, den = 0.0;
+            for (int y = v - rho; y <= v + rho; ++y) {
+                if (y < 0 || y >= H) continue;
+                for (int x = u - rho; x <= u + rho; ++x) {
+                    if (x < 0 || x >= W) continue;
+                    const double w = oracle_weight(L, W, C, u, v, x, y, gamma_d, gamma_r);
+                    num += w * oracle_cost(L, R, H, W, C, x, y, d, 0, 0.0);
+                    den += w;
+                }
+            }
+            a[d] = num / den;
+        }
+        int best = b0;
+        for (int d = b0 + 1; d <= b1; ++d)
+            if (a[d] < a[best]) best = d;
+        double ds = (double)best;
+        if (best > b0 && best < b1) {
+            const double den = 2.0 * a[best - 1] + 2.0 * a[best + 1] - 4.0 * a[best];
+            if (den > 0.0) ds = best + (a[best - 1] - a[best + 1]) / den;
+        }
+        d_int[i] = best;
+        d_sub[i] = ds;
+        if (agg_out) memcpy(agg_out + (size_t)i * D, a, sizeof(double) * (size_t)D);
+    }
+    free(a);
+    return 0;
+}
+
+/*
+ * B6: targets of every quarter pixel.  label_int / label_sub are the plain
+ * FBS outputs (H x W); centre_q is the predicted centre 4 (e* + o0) per
+ * quarter pixel (Hq x Wq).  Writes t (FP64) and y (0/1).
+ */
+void oracle_band_targets(const int32_t *label_int, const double *label_sub, int H, int W, int D, int h,
+                         const double *centre_q, double *t, int32_t *y)
+{
+    const int Hq = (H + 3) / 4, Wq = (W + 3) / 4;
+    for (int Y = 0; Y < Hq; ++Y) {
+        for (int X = 0; X < Wq; ++X) {
+            const size_t i = (size_t)Y * Wq + X;
+            float m = floorf((float)centre_q[i] + 0.5f);
+            if (!(m >= 0.0f)) m = 0.0f;
+            if (m > (float)(D - 1)) m = (float)(D - 1);
+            const int mi = (int)m;
+            double s = 0.0;
+            int cnt = 0, ok = 1;
+            for (int yy = 4 * Y; yy < 4 * Y + 4 && yy < H; ++yy) {
+                for (int xx = 4 * X; xx < 4 * X + 4 && xx < W; ++xx) {
+                    const size_t p = (size_t)yy * W + xx;
+                    s += label_sub[p];
+                    ++cnt;
+                    if (label_int[p] < mi - h + 1 || label_int[p] > mi + h - 1) ok = 0;
+                }
+            }
+            t[i] = s / cnt;
+            y[i] = ok;
+        }
+    }
+}
