@@ -222,7 +222,8 @@ typedef enum {
     FBS_KERNEL_AGG_TC = 2,      /* tensor-core aggregation + WTA + Eq. (10) */
     FBS_KERNEL_OTHER = 3,       /* every other kernel of the library */
     FBS_KERNEL_BATCH = 4,       /* one batch graph (timed as a whole; its kernels count as COST and AGG_F32) */
-    FBS_KERNEL_KINDS = 5
+    FBS_KERNEL_NET = 5,         /* band form: features, network, loss, optimiser, band planning */
+    FBS_KERNEL_KINDS = 6
 } fbs_kernel_kind;
 
 fbs_status fbs_profile(fbs_ctx *ctx, int enable);

@@ -26,6 +26,12 @@ of band_oracle.c (reading B6):
 Gradients are written out by the chain rule, layer by layer; the optimiser is
 Adam (Kingma & Ba) with bias correction.  The flat parameter vector holds,
 for l = 1..6, W_l as [3][3][Cin_l][Cout_l] followed by b_l [Cout_l].
+
+``bf16=True`` rounds, to BF16 (round to nearest even), exactly the operands
+that a BF16 tensor-core implementation holds in 16 bits -- the network input,
+the weights, every hidden activation, and the gradients flowing backwards --
+while every sum stays FP64.  That isolates the effect of the 16-bit operands
+from the effect of the accumulation order.
 """
 
 from __future__ import annotations
@@ -63,6 +69,18 @@ def pack(layers):
     return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in layers])
 
 
+def round_bf16(x):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    f = np.ascontiguousarray(x, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return (r.astype(np.uint32)).view(np.float32).astype(np.float64)
+
+
+def _r(x, bf16):
+    return round_bf16(x) if bf16 else x
+
+
 def conv3x3(X, W, b):
     """conv(X; W) + b with zero padding.  X [H][W][Cin] -> [H][W][Cout]."""
     H, Wd, _ = X.shape
@@ -89,14 +107,14 @@ def conv3x3_backward(X, W, G):
     return dXp[1:H + 1, 1:Wd + 1], dW, G.sum(axis=(0, 1))
 
 
-def forward(theta, feat):
+def forward(theta, feat, bf16=False):
     """Network outputs O [Hq][Wq][2] and the layer inputs (for the backward pass)."""
     layers = unpack(theta)
-    X = np.asarray(feat, np.float64)
+    X = _r(np.asarray(feat, np.float64), bf16)
     acts = [X]
     for l, (W, b) in enumerate(layers):
-        Z = conv3x3(X, W, b)
-        X = np.maximum(Z, 0.0) if l < N_LAYERS - 1 else Z
+        Z = conv3x3(X, _r(W, bf16), b)
+        X = _r(np.maximum(Z, 0.0), bf16) if l < N_LAYERS - 1 else Z
         acts.append(X)
     return X, acts
 
@@ -118,17 +136,17 @@ def loss_and_output_grad(O, estar, t, y):
     return L, dO
 
 
-def backward(theta, acts, dO):
+def backward(theta, acts, dO, bf16=False):
     """Gradient of the loss w.r.t. the flat parameter vector, given dL/dO."""
     layers = unpack(theta)
     grads = [None] * N_LAYERS
-    G = dO
+    G = _r(dO, bf16)
     for l in range(N_LAYERS - 1, -1, -1):
         W, _ = layers[l]
-        dX, dW, db = conv3x3_backward(acts[l], W, G)
+        dX, dW, db = conv3x3_backward(acts[l], _r(W, bf16), G)
         grads[l] = (dW, db)
         if l > 0:
-            G = dX * (acts[l] > 0.0)   # ReLU of layer l (acts[l] = Y_l)
+            G = _r(dX * (acts[l] > 0.0), bf16)   # ReLU of layer l (acts[l] = Y_l)
     return pack(grads)
 
 

@@ -2,7 +2,7 @@
 
 The binding only marshals arguments: every step of the path runs in the CUDA
 kernels of ``libfbs.so`` (built by ``build.py``).  Functions carry the names
-of the C ABI in ``include/fbs.h``.  Pointer arguments accept a CUDA tensor
+of the C ABI in ``include/fbs.h`` and ``include/fbs_band.h``.  Pointer arguments accept a CUDA tensor
 (its ``data_ptr()``), a plain integer address, or None for NULL.  Streams
 accept a ``torch.cuda.Stream``, a raw ``cudaStream_t`` integer, or None (the
 context's own stream).  A non-OK status raises FBSError with the library's
@@ -39,8 +39,14 @@ FBS_KERNEL_AGG_F32 = 1
 FBS_KERNEL_AGG_TC = 2
 FBS_KERNEL_OTHER = 3
 FBS_KERNEL_BATCH = 4
-FBS_KERNEL_KINDS = 5
-KERNEL_NAMES = {0: "cost_build", 1: "aggregate_f32", 2: "aggregate_tc", 3: "other", 4: "batch_graph"}
+FBS_KERNEL_NET = 5
+FBS_KERNEL_KINDS = 6
+KERNEL_NAMES = {0: "cost_build", 1: "aggregate_f32", 2: "aggregate_tc", 3: "other", 4: "batch_graph",
+                5: "band_net"}
+
+FBS_BAND_FEATURES = 6
+FBS_BAND_WIDTH = 32
+FBS_BAND_LAYERS = 6
 
 # Every function the header declares, with (restype, argtypes).
 _P = ctypes.c_void_p
@@ -75,6 +81,19 @@ SIGNATURES = {
     "fbs_batch_plan": (_I, [_P, _I, _P, ctypes.POINTER(_I)]),
     "fbs_profile": (_I, [_P, _I]),
     "fbs_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    # fbs_band.h
+    "fbs_band_net_param_count": (_Z, []),
+    "fbs_band_net_init": (_I, [_P, ctypes.c_uint64]),
+    "fbs_band_net_set_params": (_I, [_P, _P, _Z]),
+    "fbs_band_net_get_params": (_I, [_P, _P, _Z]),
+    "fbs_band_net_save": (_I, [_P, ctypes.c_char_p]),
+    "fbs_band_net_load": (_I, [_P, ctypes.c_char_p]),
+    "fbs_band_features": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
+    "fbs_band_net_forward": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P, _P, _P]),
+    "fbs_band_net_train_step": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P, _I, _F, _P, _P, _P]),
+    "fbs_band_limits": (_I, [_P, _P, _P, _I, _I, _I, _F, _P, _P, _P]),
+    "fbs_compute_disparity_banded": (_I, [_P, _P, _P, _P, _I, _F, _P]),
+    "fbs_compute_disparity_learned": (_I, [_P, _P, _I, _F, _P]),
 }
 
 
@@ -246,6 +265,69 @@ def fbs_profile_read(ctx, kind):
     n = ctypes.c_longlong()
     _check(ctx, lib().fbs_profile_read(ctx, kind, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+# ---- band form (fbs_band.h) ---------------------------------------------------
+def fbs_band_net_param_count():
+    return int(lib().fbs_band_net_param_count())
+
+
+def fbs_band_net_init(ctx, seed=0):
+    _check(ctx, lib().fbs_band_net_init(ctx, int(seed)))
+
+
+def fbs_band_net_set_params(ctx, params):
+    """params: float32 numpy array of fbs_band_net_param_count() values (host)."""
+    _check(ctx, lib().fbs_band_net_set_params(ctx, _addr(params), params.size))
+
+
+def fbs_band_net_get_params(ctx, out):
+    _check(ctx, lib().fbs_band_net_get_params(ctx, _addr(out), out.size))
+
+
+def fbs_band_net_save(ctx, path):
+    _check(ctx, lib().fbs_band_net_save(ctx, os.fsencode(path)))
+
+
+def fbs_band_net_load(ctx, path):
+    _check(ctx, lib().fbs_band_net_load(ctx, os.fsencode(path)))
+
+
+def fbs_band_features(ctx, left, right, H, W, C, D, feat, estar, stream=None):
+    _check(ctx, lib().fbs_band_features(ctx, _addr(left), _addr(right), H, W, C, D, _addr(feat), _addr(estar),
+                                       _stream(stream)))
+
+
+def fbs_band_net_forward(ctx, left, right, H, W, C, D, out_q, centre, conf, stream=None):
+    _check(ctx, lib().fbs_band_net_forward(ctx, _addr(left), _addr(right), H, W, C, D, _addr(out_q),
+                                          _addr(centre), _addr(conf), _stream(stream)))
+
+
+def fbs_band_net_train_step(ctx, left, right, H, W, C, D, label_int, label_sub, half_band, lr, loss=None,
+                            grad=None, stream=None):
+    """loss: a 1-element float32 numpy array or None; grad: a float32 numpy array
+    of fbs_band_net_param_count() values or None (both host)."""
+    _check(ctx, lib().fbs_band_net_train_step(ctx, _addr(left), _addr(right), H, W, C, D, _addr(label_int),
+                                             _addr(label_sub), half_band, lr, _addr(loss), _addr(grad),
+                                             _stream(stream)))
+
+
+def fbs_band_limits(ctx, centre, conf, n, D, half_band, conf_threshold, lo, hi, stream=None):
+    _check(ctx, lib().fbs_band_limits(ctx, _addr(centre), _addr(conf), n, D, half_band, conf_threshold,
+                                     _addr(lo), _addr(hi), _stream(stream)))
+
+
+def fbs_compute_disparity_banded(ctx, pair, centre, conf, half_band, conf_threshold, stream=None):
+    """pair: a dict as for make_pairs (or a one-element fbs_pair array)."""
+    arr = pair if isinstance(pair, ctypes.Array) else make_pairs([pair])
+    _check(ctx, lib().fbs_compute_disparity_banded(ctx, ctypes.cast(arr, _P), _addr(centre), _addr(conf),
+                                                  half_band, conf_threshold, _stream(stream)))
+
+
+def fbs_compute_disparity_learned(ctx, pair, half_band, conf_threshold, stream=None):
+    arr = pair if isinstance(pair, ctypes.Array) else make_pairs([pair])
+    _check(ctx, lib().fbs_compute_disparity_learned(ctx, ctypes.cast(arr, _P), half_band, conf_threshold,
+                                                   _stream(stream)))
 
 
 class Context:

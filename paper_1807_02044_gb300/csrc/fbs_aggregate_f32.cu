@@ -32,8 +32,8 @@
 namespace fbs {
 namespace {
 
-constexpr int kTX = 32;        // tile width (pixels)
-constexpr int kTY = 4;         // tile height (rows)
+constexpr int kTX = kAggTileX;   // tile width (pixels)
+constexpr int kTY = kAggTileY;   // tile height (rows)
 constexpr int kPX = 4;         // pixels per thread along x
 constexpr int kThreads = 256;  // 8 warps
 constexpr int kNPix = kTX * kTY;
@@ -72,7 +72,8 @@ __host__ __device__ inline size_t smem_bytes(int rho)
     return sizeof(float) * (a + 2 * (size_t)kTY * weight_stride(rho) + 2 * kNPix) + sizeof(float4) * 3 * NC;
 }
 
-// Load cost row r, columns x0-rho .. x0-rho+NC-1, disparities dc0 .. dc0+DC-1.
+// Load cost row r, columns x0-rho .. x0-rho+NC-1, disparities dc0 .. dc0+DC-1;
+// disparities >= D (the end of the range being aggregated) are zero-filled.
 template <int DC, bool VEC>
 __device__ __forceinline__ void load_cost_row(float* dst, const float* __restrict__ cost, int ld, int W,
                                               int D, int r, int x0, int rho, int NC, int dc0)
@@ -120,14 +121,18 @@ __device__ __forceinline__ void load_guide_row(float4* dst, const uint8_t* __res
     }
 }
 
-// One 32 x 4 tile with top-left pixel (x0, y0), all disparities; ends with a
-// __syncthreads, so a CTA may call it for several tiles in a row.
+// One 32 x 4 tile with top-left pixel (x0, y0), disparities [d_begin, d_end)
+// (the full range: 0, D); ends with a __syncthreads, so a CTA may call it for
+// several tiles in a row.  band (nullable) restricts the WTA and Eq. (10) of
+// each pixel to its own band [lo, hi], a sub-range of [d_begin, d_end);
+// without it every pixel uses [0, D-1].  d_begin must be a multiple of 4.
 template <int KD, bool VEC>
 __device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, int ld,
                                                const uint8_t* __restrict__ guide, int H, int W, int C, int D,
                                                int rho, float neg_ks, float neg_kr, float* __restrict__ agg_out,
                                                int32_t* __restrict__ disp_int, float* __restrict__ disp_sub, int x0,
-                                               int y0, float4* smem_f4)
+                                               int y0, float4* smem_f4, int d_begin, int d_end,
+                                               const uint32_t* __restrict__ band)
 {
     constexpr int DC = 8 * KD;   // disparities per chunk
     constexpr int NQ = KD / 4;   // float4 groups per thread
@@ -170,7 +175,16 @@ __device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, i
 
     // WTA role (tid < kNPix): state of pixel tid carried across chunks
     float best = __int_as_float(0x7f800000), a_prev = 0.f, a_next = 0.f, last = 0.f;
-    int bidx = 0;
+    int blo = 0, bhi = D - 1;
+    if (band != nullptr && tid < kNPix) {
+        const int oy = y0 + tid / kTX, ox = x0 + tid % kTX;
+        if (oy < H && ox < W) {
+            const uint32_t b = band[(size_t)oy * W + ox];
+            blo = (int)(b & 0xffffu);
+            bhi = (int)(b >> 16);
+        }
+    }
+    int bidx = blo;
     bool pending = false;
 
     // consumer role
@@ -179,7 +193,7 @@ __device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, i
     const int r_hi = min(H - 1, y0 + kTY - 1 + rho);
     const int nr = r_hi - r_lo + 1;
 
-    for (int dc0 = 0; dc0 < D; dc0 += DC) {
+    for (int dc0 = d_begin; dc0 < d_end; dc0 += DC) {
         float4 acc[kPX][NQ];
 #pragma unroll
         for (int i = 0; i < kPX; ++i)
@@ -187,7 +201,7 @@ __device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, i
             for (int q = 0; q < NQ; ++q) acc[i][q] = make_float4(0.f, 0.f, 0.f, 0.f);
         float den_part = 0.f;
 
-        load_cost_row<DC, VEC>(cring, cost, ld, W, D, r_lo, x0, rho, NC, dc0);
+        load_cost_row<DC, VEC>(cring, cost, ld, W, d_end, r_lo, x0, rho, NC, dc0);
         cp_async_commit();
         load_guide_row(gring, guide, W, C, r_lo, x0, rho, NC);
         __syncthreads();
@@ -196,7 +210,7 @@ __device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, i
             const int r = r_lo + s;
             // (A) prefetch the next cost row, (B) the next guide row
             if (s + 1 < nr) {
-                load_cost_row<DC, VEC>(cring + ((s + 1) % 3) * cslot, cost, ld, W, D, r + 1, x0, rho, NC, dc0);
+                load_cost_row<DC, VEC>(cring + ((s + 1) % 3) * cslot, cost, ld, W, d_end, r + 1, x0, rho, NC, dc0);
                 load_guide_row(gring + ((s + 1) % 3) * NC, guide, W, C, r + 1, x0, rho, NC);
             }
             cp_async_commit();
@@ -281,7 +295,7 @@ __device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, i
             }
         }
         __syncthreads();
-        const int nd = min(DC, D - dc0);
+        const int nd = min(DC, d_end - dc0);
         if (agg_out != nullptr) {
             for (int e = tid; e < kNPix * nd; e += kThreads) {
                 const int pix = e / nd, j = e - pix * nd;
@@ -291,7 +305,8 @@ __device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, i
         }
         if (tid < kNPix) {
             const float* st = stage + tid * (DC + 1);
-            for (int j = 0; j < nd; ++j) {
+            const int j0 = max(0, blo - dc0), j1 = min(nd, bhi + 1 - dc0);
+            for (int j = j0; j < j1; ++j) {
                 const float v = st[j];
                 if (pending) {
                     a_next = v;
@@ -313,7 +328,7 @@ __device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, i
         const int oy = y0 + tid / kTX, ox = x0 + tid % kTX;
         if (oy < H && ox < W) {
             float ds = (float)bidx;
-            if (bidx > 0 && bidx < D - 1) {
+            if (bidx > blo && bidx < bhi) {
                 const float den = 2.f * a_prev + 2.f * a_next - 4.f * best;
                 if (den > 0.f) ds = (float)bidx + (a_prev - a_next) / den;
             }
@@ -333,7 +348,25 @@ aggregate_f32_kernel(const float* __restrict__ cost, int ld, const uint8_t* __re
 {
     extern __shared__ float4 smem_f4[];
     aggregate_tile<KD, VEC>(cost, ld, guide, H, W, C, D, rho, neg_ks, neg_kr, agg_out, disp_int, disp_sub,
-                            blockIdx.x * kTX, blockIdx.y * kTY, smem_f4);
+                            blockIdx.x * kTX, blockIdx.y * kTY, smem_f4, 0, D, nullptr);
+}
+
+// Band form: tile t aggregates its range tile_range[t] (chunks of 32 or 64
+// disparities) and each pixel takes its winner inside its own band.
+__global__ void __launch_bounds__(kThreads, 2)
+aggregate_band_kernel(const float* __restrict__ cost, int ld, const uint8_t* __restrict__ guide, int H, int W,
+                      int C, int D, int rho, float neg_ks, float neg_kr, const int2* __restrict__ tile_range,
+                      const uint32_t* __restrict__ band, int32_t* __restrict__ disp_int,
+                      float* __restrict__ disp_sub)
+{
+    extern __shared__ float4 smem_f4[];
+    const int2 r = tile_range[(size_t)blockIdx.y * gridDim.x + blockIdx.x];
+    if (r.y - r.x > 32)
+        aggregate_tile<8, true>(cost, ld, guide, H, W, C, D, rho, neg_ks, neg_kr, nullptr, disp_int, disp_sub,
+                                blockIdx.x * kTX, blockIdx.y * kTY, smem_f4, r.x, r.y, band);
+    else
+        aggregate_tile<4, true>(cost, ld, guide, H, W, C, D, rho, neg_ks, neg_kr, nullptr, disp_int, disp_sub,
+                                blockIdx.x * kTX, blockIdx.y * kTY, smem_f4, r.x, r.y, band);
 }
 
 // Persistent form over a batch: CTAs claim (pair, tile) items from a counter;
@@ -355,7 +388,8 @@ aggregate_f32_batched_kernel(const BatchPair* __restrict__ pairs, int npairs, in
         const int t = item - bp.agg_off;
         const int ntx = (bp.W + kTX - 1) / kTX;
         aggregate_tile<8, true>(bp.cost, bp.ld, bp.left, bp.H, bp.W, bp.C, bp.D, bp.radius, bp.neg_ks, bp.neg_kr,
-                                nullptr, bp.disp_int, bp.disp_sub, (t % ntx) * kTX, (t / ntx) * kTY, smem_f4);
+                                nullptr, bp.disp_int, bp.disp_sub, (t % ntx) * kTX, (t / ntx) * kTY, smem_f4, 0,
+                                bp.D, nullptr);
     }
 }
 
@@ -389,6 +423,22 @@ cudaError_t launch_aggregate_f32_batched(const BatchPair* pairs, int npairs, int
                                          size_t smem, cudaStream_t stream)
 {
     aggregate_f32_batched_kernel<<<grid, kThreads, smem, stream>>>(pairs, npairs, nitems, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aggregate_band(const float* cost, int ld, const uint8_t* guide, int H, int W, int C, int D,
+                                  int radius, float sigma_s, float sigma_r, const int2* tile_range,
+                                  const uint32_t* band, int32_t* disp_int, float* disp_sub, cudaStream_t stream)
+{
+    const double log2e = 1.4426950408889634;
+    const float neg_ks = (float)(-log2e / ((double)sigma_s * sigma_s));
+    const float neg_kr = (float)(-log2e / ((double)sigma_r * sigma_r));
+    const size_t smem = smem_bytes<64>(radius);
+    cudaError_t e = cudaFuncSetAttribute(aggregate_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY);
+    aggregate_band_kernel<<<grid, kThreads, smem, stream>>>(cost, ld, guide, H, W, C, D, radius, neg_ks, neg_kr,
+                                                            tile_range, band, disp_int, disp_sub);
     return cudaGetLastError();
 }
 

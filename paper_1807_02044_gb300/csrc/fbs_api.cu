@@ -182,6 +182,7 @@ fbs_status fbs_destroy(fbs_ctx* ctx)
         if (ctx->bstage[k]) cudaFreeHost(ctx->bstage[k]);
         if (ctx->bstage_done[k]) cudaEventDestroy(ctx->bstage_done[k]);
     }
+    fbs::band_free(ctx);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return FBS_OK;

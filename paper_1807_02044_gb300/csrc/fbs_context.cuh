@@ -52,6 +52,10 @@ struct fbs_ctx {
     std::map<std::string, int> btuned;                 // batch shape -> chosen plan
     std::map<std::string, fbs_batch_graph> bgraphs;    // plan-specific graph per slot
     bool btuned_loaded = false;
+    // band form: the network's state and the band scratch (grown on demand)
+    struct fbs_band_state* band = nullptr;
+    void* band_ws = nullptr;
+    size_t band_ws_bytes = 0;
 };
 
 namespace fbs_detail {
@@ -176,7 +180,7 @@ inline fbs_status ensure(fbs_ctx* ctx, void** buf, size_t* have, size_t need, co
 {
     if (need <= *have) return FBS_OK;
     const size_t cap = ctx->opt.workspace_cap;
-    if (cap && ctx->ws_bytes + ctx->io_bytes - *have + need > cap)
+    if (cap && ctx->ws_bytes + ctx->io_bytes + ctx->band_ws_bytes - *have + need > cap)
         return fail(ctx, FBS_ERR_OOM, "%s needs %zu bytes; workspace cap is %zu", what, need, cap);
     if (*buf) {
         cudaError_t e = cudaDeviceSynchronize();   // the old buffer may still be in use

@@ -147,12 +147,13 @@ __device__ __forceinline__ void store8(T* o, const T (&v)[8])
 
 // MODE 0: NCC from the statistics planes; MODE 1: TAD from the raw images.
 // PLANAR false: out is [H][W][ld] (T = float); true: out is x-blocked [H][ld][D][8] with ld = ceil(W/8).
-// One row y and 128 pixels from x0, all disparities; ends with a __syncthreads.
+// One row y and 128 pixels from x0, disparities [d_begin, d_end) (all: 0, D);
+// ends with a __syncthreads.
 template <int MODE, typename T, bool PLANAR>
 __device__ __forceinline__ void cost_tile(const int16_t* __restrict__ gplane, const int* __restrict__ splane,
                                           const float* __restrict__ rvplane, const uint8_t* __restrict__ L,
                                           const uint8_t* __restrict__ R, int H, int W, int C, int D, int ld, float tau,
-                                          T* __restrict__ out, int x0, int y, int* smem_i)
+                                          T* __restrict__ out, int x0, int y, int* smem_i, int d_begin, int d_end)
 {
     const int tid = threadIdx.x;
     const int nxs = min(kXS, W - x0);
@@ -191,7 +192,7 @@ __device__ __forceinline__ void cost_tile(const int16_t* __restrict__ gplane, co
         }
     }
 
-    for (int dc = 0; dc < D; dc += kDC) {
+    for (int dc = d_begin; dc < d_end; dc += kDC) {
         // right columns for this pass: virtual columns rb .. rb + NRG - 1 with
         // rb = x0 - dc - kDC - 1; the right block of (x, d) spans x-d-1 .. x-d+1
         const int rb = x0 - dc - kDC - 1;
@@ -307,7 +308,7 @@ __device__ __forceinline__ void cost_tile(const int16_t* __restrict__ gplane, co
         }
         __syncthreads();
 
-        const int nd = min(kDC, D - dc);
+        const int nd = min(kDC, d_end - dc);
         if (PLANAR) {
             // out[((y*ld + xb)*D + d)*8 + xi]: one lane stores the 8 columns of a
             // block for one disparity (16 bytes), a warp 32 consecutive disparities
@@ -326,7 +327,7 @@ __device__ __forceinline__ void cost_tile(const int16_t* __restrict__ gplane, co
             }
         } else {
             // out[(y*W + x)*ld + d]; padding d in [D, ld) of the last pass written as 0
-            const int ndw = (dc + kDC >= D) ? (ld - dc) : kDC;
+            const int ndw = (dc + kDC >= d_end) ? (d_end == D ? ld - dc : d_end - dc) : kDC;
             const int warp = tid >> 5, lane = tid & 31;
             for (int x = warp; x < nxs; x += kThreads / 32) {
                 T* o = out + ((size_t)y * W + x0 + x) * ld + dc;
@@ -346,7 +347,7 @@ cost_kernel(const int16_t* __restrict__ gplane, const int* __restrict__ splane, 
 {
     extern __shared__ int smem_i[];
     cost_tile<MODE, T, PLANAR>(gplane, splane, rvplane, L, R, H, W, C, D, ld, tau, out, blockIdx.x * kXS, blockIdx.y,
-                               smem_i);
+                               smem_i, 0, D);
 }
 
 // Batched FP32 cost volumes [H][W][ld]: an item is (row, 128-pixel segment) of a pair.
@@ -367,11 +368,51 @@ cost_batched_kernel(const BatchPair* __restrict__ pairs, int npairs, int nitems,
         const int x0 = (t % nseg) * kXS, y = t / nseg;
         if (bp.mode == 0)
             cost_tile<0, float, false>(bp.sc.g, bp.sc.s, bp.sc.rv, bp.left, bp.right, bp.H, bp.W, bp.C, bp.D, bp.ld,
-                                       bp.tau, bp.cost, x0, y, smem_i);
+                                       bp.tau, bp.cost, x0, y, smem_i, 0, bp.D);
         else
             cost_tile<1, float, false>(bp.sc.g, bp.sc.s, bp.sc.rv, bp.left, bp.right, bp.H, bp.W, bp.C, bp.D, bp.ld,
-                                       bp.tau, bp.cost, x0, y, smem_i);
+                                       bp.tau, bp.cost, x0, y, smem_i, 0, bp.D);
     }
+}
+
+// Band form: NCC costs of row y, pixels x0 .. x0+127, for the disparities
+// that some aggregation tile reading this segment needs: the hull of the
+// ranges [d_begin, d_end) of every tile whose window halo (the tile grown by
+// rho) overlaps the segment.  Entries outside that hull are not written.
+__global__ void __launch_bounds__(kThreads)
+cost_band_kernel(const int16_t* __restrict__ gplane, const int* __restrict__ splane,
+                 const float* __restrict__ rvplane, int H, int W, int D, int ld, int rho,
+                 const int2* __restrict__ tile_range, int ntx, int nty, float* __restrict__ out)
+{
+    extern __shared__ int smem_i[];
+    __shared__ int lo_s, hi_s;
+    const int x0 = blockIdx.x * kXS, y = blockIdx.y;
+    if (threadIdx.x == 0) {
+        lo_s = D;
+        hi_s = 0;
+    }
+    __syncthreads();
+    // tiles ty with 4ty - rho <= y <= 4ty + 3 + rho, tx with halo columns meeting [x0, x0 + 127]
+    const int ty0 = max(0, (y - rho + kAggTileY * 64) / kAggTileY - 64);
+    const int ty1 = min(nty - 1, (y + rho) / kAggTileY);
+    const int tx0 = max(0, (x0 - rho + kAggTileX * 64) / kAggTileX - 64);
+    const int tx1 = min(ntx - 1, (x0 + kXS - 1 + rho) / kAggTileX);
+    const int nx = tx1 - tx0 + 1;
+    int lo = D, hi = 0;
+    for (int i = threadIdx.x; i < (ty1 - ty0 + 1) * nx; i += kThreads) {
+        const int2 r = tile_range[(size_t)(ty0 + i / nx) * ntx + tx0 + i % nx];
+        lo = min(lo, r.x);
+        hi = max(hi, r.y);
+    }
+    if (ty0 <= ty1 && tx0 <= tx1) {
+        atomicMin(&lo_s, lo);
+        atomicMax(&hi_s, hi);
+    }
+    __syncthreads();
+    const int d_begin = lo_s, d_end = hi_s;
+    if (d_begin >= d_end) return;
+    cost_tile<0, float, false>(gplane, splane, rvplane, nullptr, nullptr, H, W, 1, D, ld, 0.f, out, x0, y, smem_i,
+                               d_begin, d_end);
 }
 
 size_t cost_smem_bytes()
@@ -476,6 +517,21 @@ cudaError_t launch_cost_build(const CostScratch& sc, const uint8_t* left, const 
         return launch_cost_kernel<0, float, false>(sc, left, right, H, W, C, D, ld, tau, cost, stream);
     }
     return launch_cost_kernel<1, float, false>(sc, left, right, H, W, C, D, ld, tau, cost, stream);
+}
+
+cudaError_t launch_cost_band(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H, int W,
+                             int C, int D, int ld, int radius, const int2* tile_range, float* cost, cudaStream_t stream)
+{
+    cudaError_t e = launch_stats(sc, left, right, H, W, C, stream);
+    if (e != cudaSuccess) return e;
+    const size_t smem = cost_smem_bytes();
+    e = cudaFuncSetAttribute(cost_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int ntx = (W + kAggTileX - 1) / kAggTileX, nty = (H + kAggTileY - 1) / kAggTileY;
+    dim3 grid((W + kXS - 1) / kXS, H);
+    cost_band_kernel<<<grid, kThreads, smem, stream>>>(sc.g, sc.s, sc.rv, H, W, D, ld, radius, tile_range, ntx, nty,
+                                                       cost);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cost_build_xblock16(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H,

@@ -49,6 +49,9 @@ cudaError_t launch_cost_build_xblock16(const CostScratch& sc, const uint8_t* lef
                                        cudaStream_t stream);
 
 // ---- steps 2-4 in FP32: Eq. (6)-(8), WTA, Eq. (10) ----------------------------
+// Pixel tile of the FP32 aggregation (also the unit of the band form's ranges).
+constexpr int kAggTileX = 32;
+constexpr int kAggTileY = 4;
 // agg_out (nullable) is written with row pitch D (caller layout [H][W][D]).
 cudaError_t launch_aggregate_f32(const float* cost, int ld, const uint8_t* guide, int H, int W,
                                  int C, int D, int radius, float sigma_s, float sigma_r,
@@ -70,6 +73,20 @@ cudaError_t launch_pack_rgbx(const uint8_t* img, int H, int W, int C, uint2* rgb
 cudaError_t launch_hwd_to_xblock16(const float* in, int H, int W, int D, bool bf16, void* out, cudaStream_t stream);
 // Rows D .. Dp-1 of every block of the x-blocked volume (zeros and the ones row).
 cudaError_t launch_xblock16_pad_rows(int H, int W, int D, bool bf16, void* out, cudaStream_t stream);
+
+// ---- band form: per-pixel disparity bands ---------------------------------------
+// band[p] = lo | (hi << 16): pixel p searches [lo, hi].  tile_range[t] =
+// (d_begin, d_end) of aggregation tile t (kAggTileX x kAggTileY pixels,
+// row-major tiles): d_begin = min lo rounded down to a multiple of 4, d_end =
+// max hi + 1.  The statistics pre-pass runs inside launch_cost_band.
+cudaError_t launch_band_tiles(const float* centre, const float* conf, int H, int W, int D, int half_band,
+                              float theta, uint32_t* band, int2* tile_range, cudaStream_t stream);
+cudaError_t launch_cost_band(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H, int W,
+                             int C, int D, int ld, int radius, const int2* tile_range, float* cost,
+                             cudaStream_t stream);
+cudaError_t launch_aggregate_band(const float* cost, int ld, const uint8_t* guide, int H, int W, int C, int D,
+                                  int radius, float sigma_s, float sigma_r, const int2* tile_range,
+                                  const uint32_t* band, int32_t* disp_int, float* disp_sub, cudaStream_t stream);
 
 // ---- batched form: one persistent launch per stage over many pairs ------------
 // Device-side description of one pair of a batch.  *_off is the index of the
@@ -122,5 +139,7 @@ int ctx_precision(const fbs_ctx* ctx);
 cudaStream_t ctx_stream(fbs_ctx* ctx, void* cuda_stream);
 fbs_status ctx_error(fbs_ctx* ctx, fbs_status st, const char* msg);
 void ctx_count_launch(fbs_ctx* ctx, int kind);
+// Release the band form's state (called by fbs_destroy).
+void band_free(fbs_ctx* ctx);
 
 }  // namespace fbs

@@ -1,0 +1,345 @@
+"""The learned band form on the GPU against the FP64 oracle.
+
+Features and band limits are decided in the kernels' precision with the same
+correctly rounded operations as the oracle, so they must match bit for bit.
+The band-restricted path must match the oracle's band definition with the
+tolerances of the plain path (integer winners identical except near ties,
+subpixel within 1e-3).  The network runs on BF16 operands: its outputs and
+gradients are compared with the FP64 network in relative L2 norm, with the
+bound derived in the test below.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import band_net as bn
+from tests._compare import check_disparities
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fbs():
+    from paper_1807_02044_gb300 import build as b
+    b.build()
+    import paper_1807_02044_gb300 as m
+    return m
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rand_pair(seed, H, W, C=3, shift=5):
+    rng = np.random.default_rng(seed)
+    L = rng.integers(0, 256, size=(H, W, C)).astype(np.uint8)
+    R = np.roll(L, -shift, axis=1)
+    R = np.clip(R.astype(np.int16) + rng.integers(-6, 7, size=R.shape), 0, 255).astype(np.uint8)
+    return L, R
+
+
+# ---------------------------------------------------------------------------
+# Features and band limits: bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("H,W,C,D", [(37, 45, 3, 40), (64, 200, 3, 128), (23, 530, 1, 64), (8, 8, 3, 4)])
+def test_features_bit_exact(fbs, oracle_mod, H, W, C, D):
+    L, R = _rand_pair(H * W + D, H, W, C, shift=9)
+    Hq, Wq, _ = oracle_mod.quarter_shape(H, W, D)
+    feat = torch.empty((Hq, Wq, 6), dtype=torch.float32, device="cuda")
+    est = torch.empty((Hq, Wq), dtype=torch.int32, device="cuda")
+    with fbs.Context(0) as ctx:
+        fbs.fbs_band_features(ctx.ctx, _dev(L), _dev(R), H, W, C, D, feat, est)
+        torch.cuda.synchronize()
+        fbs.fbs_sync(ctx.ctx)
+    rf, re = oracle_mod.band_features(L, R, D)
+    assert np.array_equal(est.cpu().numpy(), re)
+    assert np.array_equal(feat.cpu().numpy().view(np.uint32), rf.view(np.uint32))
+
+
+def test_features_of_a_shift_by_four_k(fbs, oracle_mod):
+    from synth import shifted_texture_pair
+    H, W, D, k = 96, 256, 128, 7
+    L, R = shifted_texture_pair(H, W, 3, 4 * k, seed=3)
+    Hq, Wq, _ = oracle_mod.quarter_shape(H, W, D)
+    est = torch.empty((Hq, Wq), dtype=torch.int32, device="cuda")
+    with fbs.Context(0) as ctx:
+        fbs.fbs_band_features(ctx.ctx, _dev(L), _dev(R), H, W, 3, D, None, est)
+        torch.cuda.synchronize()
+    assert np.all(est.cpu().numpy()[1:-1, k + 1:-1] == k)
+
+
+def test_band_limits_bit_exact(fbs, oracle_mod):
+    rng = np.random.default_rng(4)
+    n, D, h, th = 5000, 100, 8, 0.5
+    c = rng.uniform(-20, 120, n).astype(np.float32)
+    c[:50] = np.floor(c[:50]) + 0.5          # exact halves
+    c[50:60] = [np.nan, np.inf, -np.inf, 3e38, -3e38, 0.0, -0.0, 99.49, 99.5, 1e-30]
+    k = rng.uniform(0, 1, n).astype(np.float32)
+    k[60:70] = [np.nan, th, np.nextafter(np.float32(th), np.float32(0)), 1, 0, np.inf, -np.inf, 0.5, 0.5, 0.5]
+    lo = torch.empty(n, dtype=torch.int32, device="cuda")
+    hi = torch.empty(n, dtype=torch.int32, device="cuda")
+    with fbs.Context(0) as ctx:
+        fbs.fbs_band_limits(ctx.ctx, _dev(c), _dev(k), n, D, h, th, lo, hi)
+        torch.cuda.synchronize()
+    rlo, rhi = oracle_mod.band_limits(c, k, D, h, th)
+    assert np.array_equal(lo.cpu().numpy(), rlo)
+    assert np.array_equal(hi.cpu().numpy(), rhi)
+
+
+# ---------------------------------------------------------------------------
+# Band-restricted path
+# ---------------------------------------------------------------------------
+def _banded(fbs, ctx, L, R, D, r, ss, sr, centre, conf, h, th):
+    H, W, C = L.shape
+    di = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    ds = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    pair = dict(left=_dev(L), right=_dev(R), H=H, W=W, C=C, D=D, radius=r, sigma_s=ss, sigma_r=sr, tau=0.0,
+                disp_int=di, disp_subpix=ds)
+    fbs.fbs_compute_disparity_banded(ctx.ctx, pair, _dev(centre), _dev(conf), h, th)
+    torch.cuda.synchronize()
+    fbs.fbs_sync(ctx.ctx)
+    return di.cpu().numpy(), ds.cpu().numpy()
+
+
+def _check_band(di, ds, ragg, rdi, rds, lo, hi):
+    """The plain path's rules with each pixel's candidates limited to its band
+    (the oracle leaves NaN outside the band; +inf keeps them out of every
+    minimum, and makes Eq. (10) at a band end count as not checkable)."""
+    assert np.all((di >= lo) & (di <= hi))
+    a = np.where(np.isnan(ragg), np.inf, ragg)
+    return check_disparities(di, ds, a, rdi, rds, 2.0)
+
+
+@pytest.mark.parametrize("H,W,D,r,h", [(29, 70, 48, 3, 4), (40, 131, 96, 5, 8), (17, 33, 20, 2, 3)])
+def test_banded_matches_oracle_whole_frame(fbs, oracle_mod, H, W, D, r, h):
+    L, R = _rand_pair(3 * H + W, H, W, 3, shift=6)
+    rng = np.random.default_rng(H + D)
+    centre = rng.uniform(-5, D + 5, (H, W)).astype(np.float32)
+    centre[: H // 2] = 6.0 + rng.uniform(-3, 3, (H // 2, W)).astype(np.float32)   # bands around the truth
+    conf = rng.uniform(0, 1, (H, W)).astype(np.float32)
+    th = 0.3
+    with fbs.Context(0) as ctx:
+        di, ds = _banded(fbs, ctx, L, R, D, r, float(r), 12.0, centre, conf, h, th)
+    lo, hi = oracle_mod.band_limits(centre.ravel(), conf.ravel(), D, h, th)
+    ys, xs = np.mgrid[0:H, 0:W]
+    rdi, rds, ragg = oracle_mod.fbs_band_points(L, R, D, r, float(r), 12.0, xs.ravel(), ys.ravel(), lo, hi)
+    _check_band(di.ravel(), ds.ravel(), ragg, rdi, rds, lo, hi)
+
+
+def test_banded_with_no_confident_pixel_equals_the_plain_path_bitwise(fbs):
+    H, W, D, r = 45, 170, 72, 4
+    L, R = _rand_pair(9, H, W, 3, shift=11)
+    centre = np.full((H, W), 20.0, np.float32)
+    conf = np.zeros((H, W), np.float32)
+    with fbs.Context(0) as ctx:
+        di, ds = _banded(fbs, ctx, L, R, D, r, 4.0, 12.0, centre, conf, 8, 0.5)
+        pdi, pds = ctx.compute_disparity(_dev(L), _dev(R), D, r, 4.0, 12.0)
+        torch.cuda.synchronize()
+    assert np.array_equal(di, pdi.cpu().numpy())
+    assert np.array_equal(ds.view(np.uint32), pds.cpu().numpy().view(np.uint32))
+
+
+def test_banded_full_size_sampled(fbs, oracle_mod):
+    """1920x1080 RGB, D=256, radius 9, half band 8: bands around a coarse
+    estimate with 20% of the pixels falling back to the full range; 200
+    sampled pixels against the oracle."""
+    from synth import make_pair
+    p = make_pair("rgb1920x1080_d256_r9", 1)
+    rng = np.random.default_rng(2)
+    centre = (p.gt + rng.normal(0, 3, p.gt.shape)).astype(np.float32)
+    conf = (rng.uniform(0, 1, p.gt.shape) > 0.2).astype(np.float32)
+    with fbs.Context(0) as ctx:
+        di, ds = _banded(fbs, ctx, p.left, p.right, p.D, p.radius, p.sigma_s, p.sigma_r, centre, conf, 8, 0.5)
+    ys = rng.integers(0, p.H, 200)
+    xs = rng.integers(0, p.W, 200)
+    lo, hi = oracle_mod.band_limits(centre[ys, xs], conf[ys, xs], p.D, 8, 0.5)
+    rdi, rds, ragg = oracle_mod.fbs_band_points(p.left, p.right, p.D, p.radius, p.sigma_s, p.sigma_r, xs, ys,
+                                                lo, hi)
+    _check_band(di[ys, xs], ds[ys, xs], ragg, rdi, rds, lo, hi)
+
+
+# ---------------------------------------------------------------------------
+# Network: forward outputs and gradients against the FP64 network
+# ---------------------------------------------------------------------------
+# Two references.  (1) The FP64 network with every operand the kernels hold
+# in 16 bits rounded to BF16 at the same place (input, weights, activations,
+# backward gradients) and all sums in FP64: the kernels differ from it only by
+# FP32 accumulation order (relative ~1e-6 over K = 288 products and the
+# pixel sums) and by the rare ReLU or band-target decision that this flips,
+# so the bound is 1e-3 in relative L2 norm.  (2) The unrounded FP64 network:
+# the difference is the effect of BF16 operands, reported and bounded loosely
+# (unit roundoff u = 2^-9; six forward layers compound to ~6-12u in norm for
+# the outputs; a weight gradient passes through up to eleven roundings and
+# the ReLU masks of the forward pass).
+EMU_TOL = 1e-3
+OUT_TOL = 0.03
+GRAD_TOL = 0.15
+
+
+def _params(seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    th = np.zeros(bn.param_count())
+    o = 0
+    for ci, co in zip(bn.CIN, bn.COUT):
+        n = 9 * ci * co
+        th[o:o + n] = rng.standard_normal(n) * np.sqrt(2.0 / (9 * ci)) * scale
+        th[o + n:o + n + co] = rng.uniform(-0.1, 0.1, co)
+        o += n + co
+    return th.astype(np.float32)
+
+
+def test_param_layout_matches_the_oracle(fbs):
+    assert fbs.fbs_band_net_param_count() == bn.param_count()
+
+
+@pytest.mark.parametrize("H,W,D", [(96, 160, 64), (53, 77, 40)])
+def test_forward_matches_fp64_network(fbs, oracle_mod, H, W, D):
+    L, R = _rand_pair(H + W, H, W, 3, shift=12)
+    theta = _params(1)
+    Hq, Wq, _ = oracle_mod.quarter_shape(H, W, D)
+    out = torch.empty((Hq, Wq, 2), dtype=torch.float32, device="cuda")
+    centre = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    conf = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    with fbs.Context(0) as ctx:
+        fbs.fbs_band_net_set_params(ctx.ctx, theta)
+        fbs.fbs_band_net_forward(ctx.ctx, _dev(L), _dev(R), H, W, 3, D, out, centre, conf)
+        torch.cuda.synchronize()
+        fbs.fbs_sync(ctx.ctx)
+    feat, est = oracle_mod.band_features(L, R, D)
+    O, _ = bn.forward(theta.astype(np.float64), feat.astype(np.float64))
+    Oe, _ = bn.forward(theta.astype(np.float64), feat.astype(np.float64), bf16=True)
+    g = out.cpu().numpy()
+    for c in range(2):
+        emu = np.linalg.norm(g[..., c] - Oe[..., c]) / np.linalg.norm(Oe[..., c])
+        err = np.linalg.norm(g[..., c] - O[..., c]) / np.linalg.norm(O[..., c])
+        print(f"output {c}: rel. L2 vs BF16-operand FP64 net {emu:.2e}, vs FP64 net {err:.2e}")
+        assert emu <= EMU_TOL, (c, emu)
+        assert err <= OUT_TOL, (c, err)
+    # the head: centre = 4 (e* + o0) in FP32 and conf = sigmoid(z) of the
+    # quarter pixel (x / 4, y / 4), from the kernel's own outputs
+    up = bn.upsample(np.arange(Hq * Wq).reshape(Hq, Wq), H, W)
+    o0 = g[..., 0].ravel()[up]
+    z = g[..., 1].ravel()[up]
+    expect_c = np.float32(4.0) * (est.ravel()[up].astype(np.float32) + o0)
+    assert np.array_equal(centre.cpu().numpy(), expect_c)
+    np.testing.assert_allclose(conf.cpu().numpy(), 1.0 / (1.0 + np.exp(-z.astype(np.float64))), rtol=0, atol=1e-6)
+
+
+def test_gradients_match_fp64_network(fbs, oracle_mod):
+    H, W, D, h = 120, 176, 64, 8
+    L, R = _rand_pair(5, H, W, 3, shift=20)
+    theta = _params(2)
+    rng = np.random.default_rng(6)
+    li = rng.integers(0, D, (H, W)).astype(np.int32)
+    li[:, : W // 2] = 20                         # a region the band can cover
+    ls = (li + rng.uniform(-0.5, 0.5, (H, W))).astype(np.float32)
+    grad = np.zeros(bn.param_count(), np.float32)
+    loss = np.zeros(1, np.float32)
+    with fbs.Context(0) as ctx:
+        fbs.fbs_band_net_set_params(ctx.ctx, theta)
+        fbs.fbs_band_net_train_step(ctx.ctx, _dev(L), _dev(R), H, W, 3, D, _dev(li), _dev(ls), h, 0.0, loss, grad)
+        fbs.fbs_sync(ctx.ctx)
+    feat, est = oracle_mod.band_features(L, R, D)
+    th64 = theta.astype(np.float64)
+    res = {}
+    for mode in (True, False):
+        O, acts = bn.forward(th64, feat.astype(np.float64), bf16=mode)
+        cq, _ = bn.centre_conf(O, est)
+        t, y = oracle_mod.band_targets(li, ls.astype(np.float64), D, h, cq)
+        Lref, dO = bn.loss_and_output_grad(O, est, t, y)
+        res[mode] = (Lref, bn.backward(th64, acts, dO, bf16=mode))
+    Le, ge = res[True]
+    Lf, gf = res[False]
+    assert abs(loss[0] - Le) <= EMU_TOL * abs(Le)
+    assert abs(loss[0] - Lf) <= OUT_TOL * abs(Lf)
+    o = 0
+    for l, (ci, co) in enumerate(zip(bn.CIN, bn.COUT)):
+        n = 9 * ci * co + co
+        g = grad[o:o + n]
+        emu = np.linalg.norm(g - ge[o:o + n]) / np.linalg.norm(ge[o:o + n])
+        err = np.linalg.norm(g - gf[o:o + n]) / np.linalg.norm(gf[o:o + n])
+        print(f"layer {l + 1}: rel. L2 vs BF16-operand FP64 net {emu:.2e}, vs FP64 net {err:.2e}")
+        assert emu <= EMU_TOL, (l, emu)
+        assert err <= GRAD_TOL, (l, err)
+        o += n
+
+
+def test_training_steps_reduce_the_loss(fbs, oracle_mod):
+    """Labels 4 e* + 3 (a constant correction of the coarse winner that the
+    network can represent through its biases): 100 Adam steps on one pair
+    must cut the loss by more than half."""
+    H, W, D = 160, 256, 128
+    L, R = _rand_pair(21, H, W, 3, shift=24)
+    _, est = oracle_mod.band_features(L, R, D)
+    li = (4 * bn.upsample(est, H, W) + 3).astype(np.int32)
+    ls = (li + 0.25).astype(np.float32)
+    with fbs.Context(0) as ctx:
+        dl, dr = _dev(L), _dev(R)
+        fbs.fbs_band_net_init(ctx.ctx, 7)
+        losses = []
+        for it in range(100):
+            loss = np.zeros(1, np.float32)
+            fbs.fbs_band_net_train_step(ctx.ctx, dl, dr, H, W, 3, D, _dev(li), _dev(ls), 8, 1e-2, loss, None)
+            losses.append(float(loss[0]))
+    print("loss", losses[0], "->", losses[-1])
+    assert np.all(np.isfinite(losses))
+    assert np.mean(losses[-5:]) < 0.5 * np.mean(losses[:5]), losses
+
+
+def test_params_round_trip_and_file(fbs, tmp_path):
+    theta = _params(3)
+    back = np.zeros_like(theta)
+    with fbs.Context(0) as ctx:
+        fbs.fbs_band_net_set_params(ctx.ctx, theta)
+        fbs.fbs_band_net_get_params(ctx.ctx, back)
+        assert np.array_equal(theta, back)
+        path = str(tmp_path / "net.bin")
+        fbs.fbs_band_net_save(ctx.ctx, path)
+    with fbs.Context(0) as ctx:
+        fbs.fbs_band_net_load(ctx.ctx, path)
+        back2 = np.zeros_like(theta)
+        fbs.fbs_band_net_get_params(ctx.ctx, back2)
+        assert np.array_equal(theta, back2)
+        fbs.fbs_band_net_init(ctx.ctx, 11)
+        a = np.zeros_like(theta)
+        fbs.fbs_band_net_get_params(ctx.ctx, a)
+        fbs.fbs_band_net_init(ctx.ctx, 11)
+        b = np.zeros_like(theta)
+        fbs.fbs_band_net_get_params(ctx.ctx, b)
+        assert np.array_equal(a, b) and np.all(np.isfinite(a)) and np.any(a != 0)
+
+
+def test_learned_entry_equals_forward_then_banded(fbs):
+    H, W, D = 120, 200, 64
+    L, R = _rand_pair(12, H, W, 3, shift=14)
+    with fbs.Context(0) as ctx:
+        fbs.fbs_band_net_set_params(ctx.ctx, _params(4, 0.5))
+        dl, dr = _dev(L), _dev(R)
+        centre = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        conf = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        fbs.fbs_band_net_forward(ctx.ctx, dl, dr, H, W, 3, D, None, centre, conf)
+        a = [torch.empty((H, W), dtype=torch.int32, device="cuda"), torch.empty((H, W), device="cuda")]
+        b = [torch.empty((H, W), dtype=torch.int32, device="cuda"), torch.empty((H, W), device="cuda")]
+        base = dict(left=dl, right=dr, H=H, W=W, C=3, D=D, radius=5, sigma_s=5.0, sigma_r=12.0, tau=0.0)
+        fbs.fbs_compute_disparity_banded(ctx.ctx, dict(base, disp_int=a[0], disp_subpix=a[1]), centre, conf, 8, 0.5)
+        fbs.fbs_compute_disparity_learned(ctx.ctx, dict(base, disp_int=b[0], disp_subpix=b[1]), 8, 0.5)
+        torch.cuda.synchronize()
+        fbs.fbs_sync(ctx.ctx)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+def test_band_argument_validation(fbs):
+    with fbs.Context(0) as ctx:
+        x = torch.zeros((8, 8, 3), dtype=torch.uint8, device="cuda")
+        o = torch.zeros((8, 8), dtype=torch.int32, device="cuda")
+        c = torch.zeros((8, 8), device="cuda")
+        pair = dict(left=x, right=x, H=8, W=8, C=3, D=16, radius=2, sigma_s=2.0, sigma_r=10.0, disp_int=o)
+        with pytest.raises(fbs.FBSError):
+            fbs.fbs_compute_disparity_banded(ctx.ctx, pair, c, c, 0, 0.5)
+        with pytest.raises(fbs.FBSError):
+            fbs.fbs_compute_disparity_banded(ctx.ctx, pair, None, c, 8, 0.5)
+        with pytest.raises(fbs.FBSError):      # no weights yet
+            fbs.fbs_compute_disparity_learned(ctx.ctx, pair, 8, 0.5)
+        with pytest.raises(fbs.FBSError):
+            fbs.fbs_band_net_set_params(ctx.ctx, np.zeros(5, np.float32))

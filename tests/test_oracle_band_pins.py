@@ -227,3 +227,33 @@ def test_upsample_nearest():
     up = bn.upsample(q, 7, 10)
     assert up.shape == (7, 10)
     assert up[6, 9] == q[1, 2] and up[3, 3] == q[0, 0] and up[4, 4] == q[1, 1]
+
+
+def test_round_bf16_matches_torch_conversion():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(9)
+    x = np.concatenate([rng.standard_normal(10000) * 10.0 ** rng.integers(-8, 8, 10000),
+                        [0.0, -0.0, 1.0, 1.00390625, 1.005859375, 3e38, -1e-38]])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(bn.round_bf16(x), ref)
+
+
+def test_bf16_mode_changes_only_operands():
+    """With every operand already a BF16 value and biases / inputs chosen so
+    that all activations stay BF16-exact (integers of small magnitude), the
+    rounded network equals the plain one."""
+    rng = np.random.default_rng(10)
+    theta = np.zeros(bn.param_count())
+    o = 0
+    for ci, co in zip(bn.CIN, bn.COUT):
+        n = 9 * ci * co
+        theta[o:o + n] = rng.integers(-1, 2, n) * (rng.random(n) < 0.05)
+        o += n + co
+    feat = rng.integers(0, 3, (5, 6, bn.N_FEATURES)).astype(np.float64)
+    O1, a1 = bn.forward(theta, feat)
+    O2, a2 = bn.forward(theta, feat, bf16=True)
+    if max(np.abs(a).max() for a in a1) >= 256:
+        pytest.skip("activations left the exactly representable range")
+    assert np.array_equal(O1, O2)
+    dO = rng.integers(-2, 3, O1.shape).astype(np.float64)
+    assert np.array_equal(bn.backward(theta, a1, dO), bn.backward(theta, a2, dO, bf16=True))
