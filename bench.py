@@ -72,6 +72,11 @@ def _args():
                     help="time the batched form on 64 uneven pairs (320..1024 x 240..768, D in {32,64,128,192}, "
                          "radius in {4,7,11}) instead of the single-pair workload")
     ap.add_argument("--batch-size", type=int, default=64)
+    ap.add_argument("--band", action="store_true",
+                    help="time the learned band form on the 1920x1080 RGB pair, D=256, radius 9 (network proposal "
+                         "plus band-restricted path) against the plain full-range forms on the same pair")
+    ap.add_argument("--band-threshold", type=float, default=None,
+                    help="confidence threshold of the band form (default: the one shipped with the weights)")
     return ap.parse_args()
 
 
@@ -539,12 +544,186 @@ def run_batched(args):
     return 0
 
 
+def _time_call(fbs, torch, ctx, call, stream, flush, steps, warmup):
+    """Warm up, then time exactly `steps` calls with per-step CUDA events on the
+    launch stream (the L2 flush outside them); per-kind kernel times from the
+    library's accounting."""
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            flush.fill_(1)
+            call()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        fbs.fbs_profile(ctx.ctx, 1)
+        t0 = time.time()
+        for a, b in evs:
+            flush.fill_(1)
+            a.record(stream)
+            call()
+            b.record(stream)
+        torch.cuda.synchronize()
+        t1 = time.time()
+        fbs.fbs_profile(ctx.ctx, 0)
+    fbs.fbs_sync(ctx.ctx)
+    kt = {fbs.KERNEL_NAMES[k]: fbs.fbs_profile_read(ctx.ctx, k) for k in range(fbs.FBS_KERNEL_KINDS)}
+    return dict(step_ms=sum(a.elapsed_time(b) for a, b in evs) / steps, kt=kt, t0=t0, t1=t1)
+
+
+BAND_WORKLOAD = "rgb1920x1080_d256_r9"
+HALF_BAND = 8
+
+
+def run_band(args):
+    """One step = one 1920x1080 pair through fbs_compute_disparity_learned:
+    quarter-resolution features, the six-layer network (tensor cores), the
+    per-pixel bands, the band-restricted cost and aggregation with WTA and
+    Eq. (10).  Beside it: the plain full-range FP32 and BF16 forms on the
+    same pair.  Gtaps/s counts the full-range taps H*W*D*(2r+1)^2 that the
+    step replaces (the band path computes only part of them; the fraction is
+    in config.work_fraction)."""
+    import numpy as np
+    import torch
+
+    import paper_1807_02044_gb300 as fbs
+    from synth import make_pair
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    steps = args.steps if args.steps is not None else 200
+    warmup = max(3, args.warmup if args.warmup is not None else 5)
+    p = make_pair(BAND_WORKLOAD, args.seed)
+    stream = torch.cuda.Stream(dev)
+    dl = torch.from_numpy(p.left).to(dev)
+    dr = torch.from_numpy(p.right).to(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    H, W, D = p.H, p.W, p.D
+    thr = args.band_threshold if args.band_threshold is not None else fbs.default_band_threshold()
+    taps = _taps(p)
+    outs = {k: (torch.empty((H, W), dtype=torch.int32, device=dev), torch.empty((H, W), device=dev))
+            for k in ("band", "f32", "bf16")}
+    sampler = None if args.no_clocks else ClockSampler(dev.index, os.path.join(ROOT, "_bench_clocks.csv"))
+    ctx = fbs.Context(0)
+    fbs.fbs_band_net_load(ctx.ctx, fbs.default_band_net_path())
+    arr = fbs.make_pairs([dict(left=dl, right=dr, H=H, W=W, C=3, D=D, radius=p.radius, sigma_s=p.sigma_s,
+                               sigma_r=p.sigma_r, tau=p.tau, disp_int=outs["band"][0], disp_subpix=outs["band"][1])])
+    band = _time_call(fbs, torch, ctx, lambda: fbs.fbs_compute_disparity_learned(ctx.ctx, arr, HALF_BAND, thr, stream),
+                      stream, flush, steps, warmup)
+    plain = {}
+    for form in ("f32", "bf16"):
+        c = fbs.Context(0, prec=FORM_PREC[form])
+        di, ds = outs[form]
+        plain[form] = _time_call(fbs, torch, c, lambda: fbs.fbs_compute_disparity(
+            c.ctx, dl, dr, H, W, 3, D, p.radius, p.sigma_s, p.sigma_r, p.tau, di, ds, stream),
+            stream, flush, max(3, steps // 10), warmup)
+        c.close()
+    if sampler is not None:
+        sampler.stop()
+    # the bands of this pair and the work they leave
+    centre = torch.empty((H, W), device=dev)
+    conf = torch.empty((H, W), device=dev)
+    fbs.fbs_band_net_forward(ctx.ctx, dl, dr, H, W, 3, D, None, centre, conf)
+    lo = torch.empty((H, W), dtype=torch.int32, device=dev)
+    hi = torch.empty((H, W), dtype=torch.int32, device=dev)
+    fbs.fbs_band_limits(ctx.ctx, centre, conf, H * W, D, HALF_BAND, thr, lo, hi)
+    torch.cuda.synchronize()
+    work = float(((hi - lo + 1).double().sum() / (H * W * D)).item())
+    fallback = float((conf < thr).float().mean().item())
+    ds_f32 = outs["f32"][1].cpu().numpy()
+    res = {}
+    for k in ("band", "bf16"):
+        res[k] = 100.0 * float(np.mean(np.abs(outs[k][1].cpu().numpy() - ds_f32) > 1.0))
+    # against the FP64 oracle on sampled pixels (full range)
+    ns = 0 if args.no_oracle_check else 100
+    rng = np.random.default_rng(1234)
+    xs, ys = rng.integers(0, W, ns), rng.integers(0, H, ns)
+    vs_oracle = None
+    if ns:
+        import oracle
+        oracle.build()
+        _, ref_ds, _ = oracle.fbs_points(p.left, p.right, D, p.radius, p.sigma_s, p.sigma_r, xs, ys)
+        vs_oracle = {k: 100.0 * float(np.mean(np.abs(outs[k][1].cpu().numpy()[ys, xs] - ref_ds) > 1.0))
+                     for k in ("band", "f32", "bf16")}
+    peaks, peak_src = _peaks()
+    kt = band["kt"]
+    agg_ms, agg_n = kt["aggregate_f32"]
+    agg_launch_ms = agg_ms / max(1, agg_n)
+    fp32_peak = GB300_SMS * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    band_flops = 2.0 * taps * work
+    roofline = {"kernel": "aggregate_band_kernel", "bound": "alu",
+                "achieved": band_flops / (agg_launch_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                "peak_source": f"derived: {GB300_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                               f"{peaks['sm_max_mhz']:.0f} MHz (max SM clock, {peak_src})",
+                "algorithmic": "2 flop per tap of each pixel's own band (sum of band widths x (2r+1)^2)",
+                "avg_launch_ms": agg_launch_ms, "launches": agg_n, "traffic": None}
+    roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    clocks = sampler.summary(band["t0"], band["t1"]) if sampler is not None else None
+    if sampler is not None:
+        try:
+            os.remove(sampler.path)
+        except OSError:
+            pass
+    e2e = None
+    if not args.no_e2e:
+        hl = torch.from_numpy(p.left).pin_memory()
+        hr = torch.from_numpy(p.right).pin_memory()
+        hs = torch.empty((H, W), dtype=torch.float32).pin_memory()
+        hd = torch.empty((H, W), dtype=torch.int32).pin_memory()
+
+        def e2e_call():
+            with torch.cuda.stream(stream):
+                dl.copy_(hl, non_blocking=True)
+                dr.copy_(hr, non_blocking=True)
+                fbs.fbs_compute_disparity_learned(ctx.ctx, arr, HALF_BAND, thr, stream)
+                hd.copy_(outs["band"][0], non_blocking=True)
+                hs.copy_(outs["band"][1], non_blocking=True)
+            stream.synchronize()
+        for _ in range(3):
+            e2e_call()
+        n_e2e = min(steps, 50)
+        tot = 0.0
+        for _ in range(n_e2e):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            e2e_call()
+            tot += time.perf_counter() - t
+        e2e = {"value": taps / (tot / n_e2e) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * H * W * 3,
+               "d2h_bytes_per_step": 8 * H * W, "steps": n_e2e,
+               "call": "pinned host images copied in, fbs_compute_disparity_learned, disparities copied out, "
+                       "stream synchronised; all inside the timed region"}
+    cpu = None if args.no_cpu_baseline else cpu_baseline(p, args.cpu_seconds, 0)
+    step_ms = band["step_ms"]
+    out = {"metric": METRIC, "value": taps / (step_ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": steps,
+           "warmup": warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 (network bf16)", "data": "synthetic",
+           "config": {"workload": BAND_WORKLOAD, "H": H, "W": W, "C": 3, "D": D, "radius": p.radius,
+                      "half_band": HALF_BAND, "conf_threshold": thr, "seed": args.seed,
+                      "weights": os.path.relpath(fbs.default_band_net_path(), ROOT),
+                      "work_fraction": work, "fallback_pct": 100.0 * fallback,
+                      "l2": "512 MiB flush write before every step, outside the per-step CUDA-event timing",
+                      "inputs": "resident in HBM before the timed region"},
+           "fps": 1e3 / step_ms, "form": "learned band",
+           "forms": {"band": {"gtaps_per_s": taps / (step_ms * 1e-3) / 1e9, "fps": 1e3 / step_ms,
+                              "bad_px_vs_f32_pct": res["band"],
+                              "kernel_ms_per_step": {k: v[0] / steps for k, v in kt.items() if v[1]}},
+                     **{f: {"gtaps_per_s": taps / (plain[f]["step_ms"] * 1e-3) / 1e9, "fps": 1e3 / plain[f]["step_ms"],
+                            "ms_per_step": plain[f]["step_ms"]} for f in plain}},
+           "bad_px_vs_oracle_pct_sampled": vs_oracle, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": sum(n for _, n in kt.values()), "clocks": clocks}
+    out["forms"]["bf16"]["bad_px_vs_f32_pct"] = res["bf16"]
+    print(json.dumps(out))
+    ctx.close()
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
     if args.batched:
         return run_batched(args)
+    if args.band:
+        return run_band(args)
     return run_ours(args)
 
 

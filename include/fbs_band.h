@@ -28,11 +28,13 @@
  *
  * The network is trained by the library's own kernels on disparity maps of
  * the plain full-range path: loss per quarter pixel
- *   huber(c - t) + bce(z, y),
- * t = mean subpixel label over the 4x4 block, y = 1 iff every integer label
- * of the block lies in [m - h + 1, m + h - 1] for the predicted band centre m
- * (so the band holds the winner and both of its neighbours); Adam updates
- * FP32 master weights, which are rounded to BF16 for the MMAs.
+ *   y huber(c - t) + bce(z, y),
+ * t = median subpixel label over the 4x4 block, y = the share of the block's
+ * integer labels in [m - h + 1, m + h - 1] for the predicted band centre m
+ * (pixels whose band holds the winner and both of its neighbours; y also
+ * weights the centre term so that blocks no band can serve are left to the
+ * fallback); Adam updates FP32 master weights, which are rounded to BF16 for
+ * the MMAs.
  *
  * Conventions are those of fbs.h (status codes, device pointers owned by the
  * caller, asynchronous on the given stream, host-side validation).  The

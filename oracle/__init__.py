@@ -231,15 +231,15 @@ def fbs_band_points(left, right, D, radius, sigma_s, sigma_r, xs, ys, lo, hi):
 
 
 def band_targets(label_int, label_sub, D, half_band, centre_q):
-    """B6: centre target t (float64) and confidence target y (int32), Hq x Wq."""
+    """B6: centre target t and confidence target y (both float64), Hq x Wq."""
     li = np.ascontiguousarray(label_int, np.int32)
-    ls = np.ascontiguousarray(label_sub, np.float64)
+    ls = np.ascontiguousarray(label_sub, np.float32)
     H, W = li.shape
     cq = np.ascontiguousarray(centre_q, np.float64)
     Hq, Wq = (H + 3) // 4, (W + 3) // 4
     assert cq.shape == (Hq, Wq)
     t = np.empty((Hq, Wq), np.float64)
-    y = np.empty((Hq, Wq), np.int32)
+    y = np.empty((Hq, Wq), np.float64)
     _load().oracle_band_targets(_ptr(li), _ptr(ls), H, W, D, int(half_band), _ptr(cq), _ptr(t), _ptr(y))
     return t, y
 

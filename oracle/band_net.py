@@ -19,9 +19,14 @@ Loss over the N = Hq*Wq quarter pixels, with the predicted centre
 c_i = 4 (e*_i + o0_i) in full-resolution disparities and the targets t_i, y_i
 of band_oracle.c (reading B6):
 
-    L = (1/N) sum_i [ huber(c_i - t_i) + bce(z_i, y_i) ],
+    L = (1/N) sum_i [ y_i huber(c_i - t_i) + bce(z_i, y_i) ],
     huber(e) = e^2/2 for |e| <= 1, |e| - 1/2 otherwise,
     bce(z, y) = max(z, 0) - z y + log(1 + exp(-|z|)).
+
+The centre term is weighted by the confidence target y (a constant of the
+step): a block whose winners no band around the prediction can hold -- an
+occlusion, a depth edge, the unmatched strip at the left border -- is left
+to the full-range fallback instead of pulling the centre towards it.
 
 Gradients are written out by the chain rule, layer by layer; the optimiser is
 Adam (Kingma & Ba) with bias correction.  The flat parameter vector holds,
@@ -124,14 +129,14 @@ def loss_and_output_grad(O, estar, t, y):
     o0, z = O[..., 0], O[..., 1]
     N = o0.size
     c = 4.0 * (np.asarray(estar, np.float64) + o0)
+    y = np.asarray(y, np.float64)
     e = c - t
     ae = np.abs(e)
     huber = np.where(ae <= 1.0, 0.5 * e * e, ae - 0.5)
-    y = np.asarray(y, np.float64)
     bce = np.maximum(z, 0.0) - z * y + np.log1p(np.exp(-np.abs(z)))
-    L = float((huber.sum() + bce.sum()) / N)
+    L = float(((y * huber).sum() + bce.sum()) / N)
     dO = np.empty_like(O)
-    dO[..., 0] = 4.0 * np.clip(e, -1.0, 1.0) / N
+    dO[..., 0] = 4.0 * y * np.clip(e, -1.0, 1.0) / N
     dO[..., 1] = (1.0 / (1.0 + np.exp(-z)) - y) / N
     return L, dO
 

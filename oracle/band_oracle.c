@@ -30,14 +30,20 @@
  *       operations in a fixed order, so the kernels reach the same bits and
  *       the same winners (the winner is an integer decided by floating point,
  *       and both sides decide it in the same precision).
- *   B3  features per quarter pixel (all FP32, same operation order):
+ *   B3  coarse aggregation: Kbar(X, Y, e) = the mean of K(X', Y', e) over the
+ *       5x5 quarter-resolution window around (X, Y) clipped to the image,
+ *       evaluated in FP32 as row sums (X' ascending), then the sum of those
+ *       row sums (Y' ascending), then one division by the number of in-image
+ *       taps -- a box-filter counterpart, at quarter resolution, of the
+ *       aggregation of Sec. II-B, which makes the coarse winner reliable.
+ *       Features per quarter pixel (all FP32, same operation order):
  *         f0 = G_l / (16 * 255 * C) - 0.5      (left intensity)
- *         f1 = e* / Dq                         (coarse winner, smallest e on ties)
- *         f2 = K(e*)                           (its cost)
- *         f3 = min(K2 - K(e*), 1)              (margin to the best e with |e - e*| >= 2;
+ *         f1 = e* / Dq                         (coarse winner of Kbar, smallest e on ties)
+ *         f2 = Kbar(e*)                        (its cost)
+ *         f3 = min(K2 - Kbar(e*), 1)           (margin to the best e with |e - e*| >= 2;
  *                                               K2 = 2 when there is none)
- *         f4 = K(e* - 1) - K(e*)   (2 - K(e*) at e* = 0)
- *         f5 = K(e* + 1) - K(e*)   (2 - K(e*) at e* = Dq - 1)
+ *         f4 = Kbar(e* - 1) - Kbar(e*)   (2 - Kbar(e*) at e* = 0)
+ *         f5 = Kbar(e* + 1) - Kbar(e*)   (2 - Kbar(e*) at e* = Dq - 1)
  *   B4  band of a full-resolution pixel from its centre c and confidence k:
  *       full range [0, D-1] when !(k >= theta) or c is not finite; otherwise
  *       m = floor(c + 0.5) in FP32, clamped to [0, D-1], band
@@ -48,10 +54,12 @@
  *       ends play the role of 0 and D - 1).
  *   B6  targets of quarter pixel i from plain full-range FBS (integer d*,
  *       subpixel ds) over the in-image pixels of its 4x4 block: centre target
- *       t = mean of ds (FP64 here); confidence target y = 1 iff every d* of
- *       the block lies in [m - h + 1, m + h - 1], m being the band centre of
- *       B4 for the predicted centre c_i = 4 (e*_i + o0_i), so that the band
- *       holds every winner and both of its neighbours.
+ *       t = median of ds (for an even count the mean of the two middle
+ *       values), robust to the block's outlier winners; confidence target
+ *       y = the fraction of the block's d* that lie in [m - h + 1, m + h - 1],
+ *       m being the band centre of B4 for the predicted centre
+ *       c_i = 4 (e*_i + o0_i) -- the share of pixels whose winner and both of
+ *       its neighbours the band holds (a soft target of the logistic loss).
  */
 #include <math.h>
 #include <stddef.h>
@@ -106,6 +114,8 @@ static float coarse_cost(const int32_t *gl, const int32_t *gr, int Hq, int Wq, i
     return 1.0f - c;
 }
 
+#define BAND_AGG_R 2   /* 5x5 coarse aggregation window */
+
 /*
  * B1-B3: features [Hq][Wq][6] (FP32) and the coarse winner e* [Hq][Wq] of a
  * pair.  Scratch is allocated here.  Returns 0, or -1 when out of memory.
@@ -114,25 +124,49 @@ int oracle_band_features(const uint8_t *L, const uint8_t *R, int H, int W, int C
                          int32_t *estar)
 {
     const int Hq = (H + 3) / 4, Wq = (W + 3) / 4, Dq = (D + 3) / 4;
-    int32_t *gl = (int32_t *)malloc(sizeof(int32_t) * (size_t)Hq * Wq);
-    int32_t *gr = (int32_t *)malloc(sizeof(int32_t) * (size_t)Hq * Wq);
-    float *K = (float *)malloc(sizeof(float) * (size_t)Dq);
-    if (!gl || !gr || !K) { free(gl); free(gr); free(K); return -1; }
+    const size_t nq = (size_t)Hq * Wq;
+    int32_t *gl = (int32_t *)malloc(sizeof(int32_t) * nq);
+    int32_t *gr = (int32_t *)malloc(sizeof(int32_t) * nq);
+    float *K = (float *)malloc(sizeof(float) * nq * Dq);
+    float *Kh = (float *)malloc(sizeof(float) * nq * Dq);
+    if (!gl || !gr || !K || !Kh) { free(gl); free(gr); free(K); free(Kh); return -1; }
     oracle_band_downsample(L, H, W, C, gl);
     oracle_band_downsample(R, H, W, C, gr);
+    for (int Y = 0; Y < Hq; ++Y)
+        for (int X = 0; X < Wq; ++X)
+            for (int e = 0; e < Dq; ++e) K[((size_t)Y * Wq + X) * Dq + e] = coarse_cost(gl, gr, Hq, Wq, X, Y, e);
+    /* B3: row sums, then column sums of the row sums, then the mean */
+    for (int Y = 0; Y < Hq; ++Y)
+        for (int X = 0; X < Wq; ++X)
+            for (int e = 0; e < Dq; ++e) {
+                float s = 0.0f;
+                for (int x = X - BAND_AGG_R; x <= X + BAND_AGG_R; ++x)
+                    if (x >= 0 && x < Wq) s += K[((size_t)Y * Wq + x) * Dq + e];
+                Kh[((size_t)Y * Wq + X) * Dq + e] = s;
+            }
     const float gscale = (float)(16 * 255 * C);
+    float *Kb = K;   /* K is no longer needed: reuse it for one pixel's Kbar */
     for (int Y = 0; Y < Hq; ++Y) {
+        const int y0 = Y - BAND_AGG_R < 0 ? 0 : Y - BAND_AGG_R;
+        const int y1 = Y + BAND_AGG_R > Hq - 1 ? Hq - 1 : Y + BAND_AGG_R;
         for (int X = 0; X < Wq; ++X) {
-            for (int e = 0; e < Dq; ++e) K[e] = coarse_cost(gl, gr, Hq, Wq, X, Y, e);
+            const int x0 = X - BAND_AGG_R < 0 ? 0 : X - BAND_AGG_R;
+            const int x1 = X + BAND_AGG_R > Wq - 1 ? Wq - 1 : X + BAND_AGG_R;
+            const float n = (float)((y1 - y0 + 1) * (x1 - x0 + 1));
+            for (int e = 0; e < Dq; ++e) {
+                float s = 0.0f;
+                for (int y = y0; y <= y1; ++y) s += Kh[((size_t)y * Wq + X) * Dq + e];
+                Kb[e] = s / n;
+            }
             int best = 0;
             for (int e = 1; e < Dq; ++e)
-                if (K[e] < K[best]) best = e;
+                if (Kb[e] < Kb[best]) best = e;
             float k2 = 2.0f;
             for (int e = 0; e < Dq; ++e)
-                if (abs(e - best) >= 2 && K[e] < k2) k2 = K[e];
-            const float k1 = K[best];
-            const float km = best > 0 ? K[best - 1] : 2.0f;
-            const float kp = best < Dq - 1 ? K[best + 1] : 2.0f;
+                if (abs(e - best) >= 2 && Kb[e] < k2) k2 = Kb[e];
+            const float k1 = Kb[best];
+            const float km = best > 0 ? Kb[best - 1] : 2.0f;
+            const float kp = best < Dq - 1 ? Kb[best + 1] : 2.0f;
             float *f = feat + ((size_t)Y * Wq + X) * 6;
             f[0] = (float)gl[(size_t)Y * Wq + X] / gscale - 0.5f;
             f[1] = (float)best / (float)Dq;
@@ -147,6 +181,7 @@ int oracle_band_features(const uint8_t *L, const uint8_t *R, int H, int W, int C
     free(gl);
     free(gr);
     free(K);
+    free(Kh);
     return 0;
 }
 
@@ -221,10 +256,16 @@ int oracle_fbs_band_points(const uint8_t *L, const uint8_t *R, int H, int W, int
 /*
  * B6: targets of every quarter pixel.  label_int / label_sub are the plain
  * FBS outputs (H x W); centre_q is the predicted centre 4 (e* + o0) per
- * quarter pixel (Hq x Wq).  Writes t (FP64) and y (0/1).
+ * quarter pixel (Hq x Wq).  Writes t and y (both FP64).
  */
-void oracle_band_targets(const int32_t *label_int, const double *label_sub, int H, int W, int D, int h,
-                         const double *centre_q, double *t, int32_t *y)
+static int cmp_double(const void *a, const void *b)
+{
+    const double x = *(const double *)a, y = *(const double *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+void oracle_band_targets(const int32_t *label_int, const float *label_sub, int H, int W, int D, int h,
+                         const double *centre_q, double *t, double *y)
 {
     const int Hq = (H + 3) / 4, Wq = (W + 3) / 4;
     for (int Y = 0; Y < Hq; ++Y) {
@@ -234,18 +275,18 @@ void oracle_band_targets(const int32_t *label_int, const double *label_sub, int 
             if (!(m >= 0.0f)) m = 0.0f;
             if (m > (float)(D - 1)) m = (float)(D - 1);
             const int mi = (int)m;
-            double s = 0.0;
-            int cnt = 0, ok = 1;
+            double v[16];
+            int cnt = 0, in = 0;
             for (int yy = 4 * Y; yy < 4 * Y + 4 && yy < H; ++yy) {
                 for (int xx = 4 * X; xx < 4 * X + 4 && xx < W; ++xx) {
                     const size_t p = (size_t)yy * W + xx;
-                    s += label_sub[p];
-                    ++cnt;
-                    if (label_int[p] < mi - h + 1 || label_int[p] > mi + h - 1) ok = 0;
+                    v[cnt++] = label_sub[p];
+                    if (label_int[p] >= mi - h + 1 && label_int[p] <= mi + h - 1) ++in;
                 }
             }
-            t[i] = s / cnt;
-            y[i] = ok;
+            qsort(v, (size_t)cnt, sizeof(double), cmp_double);
+            t[i] = (cnt & 1) ? v[cnt / 2] : 0.5 * (v[cnt / 2 - 1] + v[cnt / 2]);
+            y[i] = (double)in / cnt;
         }
     }
 }

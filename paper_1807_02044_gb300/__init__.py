@@ -268,6 +268,21 @@ def fbs_profile_read(ctx, kind):
 
 
 # ---- band form (fbs_band.h) ---------------------------------------------------
+def default_band_net_path():
+    """Weights of the band network trained by train_band_net.py for the
+    1920x1080 RGB, D = 256, radius 9 workload (shipped with the package)."""
+    return os.path.join(_HERE, "band_net_1920x1080_d256.bin")
+
+
+def default_band_threshold():
+    """Confidence threshold recorded with the shipped weights: the smallest one
+    whose extra bad-pixel rate stayed under the training run's target on the
+    held-out scenes."""
+    import json
+    with open(os.path.join(_HERE, "band_net_1920x1080_d256.json")) as f:
+        return float(json.load(f)["threshold"])
+
+
 def fbs_band_net_param_count():
     return int(lib().fbs_band_net_param_count())
 

@@ -58,119 +58,140 @@ __device__ __forceinline__ float coarse_from_sums(long long P9, long long Sl, lo
     return __fsub_rn(1.f, c);
 }
 
-__device__ float coarse_cost_at(const int32_t* __restrict__ gl, const int32_t* __restrict__ gr, int Hq, int Wq, int X,
-                                int Y, int e)
-{
-    if (X - e < 0) return 2.f;
-    long long Sl = 0, Ql = 0, Sr = 0, Qr = 0, P = 0;
-    for (int j = -1; j <= 1; ++j) {
-        const int y = clampi(Y + j, 0, Hq - 1);
-        for (int i = -1; i <= 1; ++i) {
-            const long long a = gl[(size_t)y * Wq + clampi(X + i, 0, Wq - 1)];
-            const long long b = gr[(size_t)y * Wq + clampi(X - e + i, 0, Wq - 1)];
-            Sl += a;
-            Ql += a * a;
-            Sr += b;
-            Qr += b * b;
-            P += a * b;
-        }
-    }
-    return coarse_from_sums(9 * P, Sl, Sr, 9 * Ql - Sl * Sl, 9 * Qr - Sr * Sr);
-}
+// Coarse cost volume K [Hq][Wq][Dq] (FP32).  A CTA covers 64 consecutive
+// quarter pixels of one row; each thread slides its right block one column
+// per e (three new values), and the costs of 32 consecutive e are staged in
+// shared memory so that every warp stores 128 contiguous bytes.
+constexpr int kCoarseX = 64;
+constexpr int kCoarseE = 32;
 
-// One thread per quarter pixel: the right block slides one column per e
-// (three new values), the four smallest (cost, e) pairs are kept in order, and
-// the winner, the best non-adjacent cost and the winner's neighbours give the
-// six features.  x0 receives them as BF16 [P][8] (two zero channels), feat
-// (nullable) as FP32 [P][6], estar the winner.
-__global__ void __launch_bounds__(128)
-band_features_kernel(const int32_t* __restrict__ gq, int H, int W, int C, int D, __nv_bfloat16* __restrict__ x0,
-                     float* __restrict__ feat, int32_t* __restrict__ estar)
+__global__ void __launch_bounds__(kCoarseX)
+band_coarse_cost_kernel(const int32_t* __restrict__ gq, int Hq, int Wq, int Dq, float* __restrict__ K)
 {
-    const int Hq = (H + 3) / 4, Wq = (W + 3) / 4, Dq = (D + 3) / 4;
-    const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
-    if (X >= Wq) return;
+    __shared__ float tile[kCoarseX][kCoarseE + 1];
+    const int X0 = blockIdx.x * kCoarseX, Y = blockIdx.y;
+    const int X = X0 + threadIdx.x;
+    const bool valid = X < Wq;
     const int32_t* gl = gq;
     const int32_t* gr = gq + (size_t)Hq * Wq;
+    const int Xc = valid ? X : Wq - 1;
     int yr[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) yr[j] = clampi(Y - 1 + j, 0, Hq - 1) * Wq;
     long long Sl = 0, Ql = 0;
-    int lw[3][3];
+    int lw[3][3], rw[3][3];
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            lw[j][i] = gl[yr[j] + clampi(X - 1 + i, 0, Wq - 1)];
+            lw[j][i] = gl[yr[j] + clampi(Xc - 1 + i, 0, Wq - 1)];
             Sl += lw[j][i];
             Ql += (long long)lw[j][i] * lw[j][i];
+            rw[j][i] = gr[yr[j] + clampi(Xc - 1 + i, 0, Wq - 1)];
         }
     const long long Vl = 9 * Ql - Sl * Sl;
-    // right window of e = 0: columns X-1, X, X+1 (clamped)
-    int rw[3][3];
+    const int nx = min(kCoarseX, Wq - X0);
+    for (int e0 = 0; e0 < Dq; e0 += kCoarseE) {
+        const int ne = min(kCoarseE, Dq - e0);
+        for (int k = 0; k < ne; ++k) {
+            const int e = e0 + k;
+            if (e > 0) {
+                const int xc = clampi(Xc - e - 1, 0, Wq - 1);
 #pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) rw[j][i] = gr[yr[j] + clampi(X - 1 + i, 0, Wq - 1)];
-    float kv[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
-    int ki[4] = {-1, -1, -1, -1};
-    for (int e = 0; e < Dq; ++e) {
-        if (e > 0) {
-            const int xc = clampi(X - e - 1, 0, Wq - 1);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                rw[j][2] = rw[j][1];
-                rw[j][1] = rw[j][0];
-                rw[j][0] = gr[yr[j] + xc];
-            }
-        }
-        float K;
-        if (X - e < 0) {
-            K = 2.f;
-        } else {
-            long long Sr = 0, Qr = 0, P = 0;
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    Sr += rw[j][i];
-                    Qr += (long long)rw[j][i] * rw[j][i];
-                    P += lw[j][i] * rw[j][i];   // <= 12240^2, exact in int32
+                for (int j = 0; j < 3; ++j) {
+                    rw[j][2] = rw[j][1];
+                    rw[j][1] = rw[j][0];
+                    rw[j][0] = gr[yr[j] + xc];
                 }
-            K = coarse_from_sums(9 * P, Sl, Sr, Vl, 9 * Qr - Sr * Sr);
-        }
-        // insert (K, e) after any equal cost (e grows, so ties keep the smaller e first)
-        if (K < kv[3]) {
-            int pos = 3;
-            while (pos > 0 && K < kv[pos - 1]) {
-                kv[pos] = kv[pos - 1];
-                ki[pos] = ki[pos - 1];
-                --pos;
             }
-            kv[pos] = K;
-            ki[pos] = e;
+            float c = 2.f;
+            if (Xc - e >= 0) {
+                long long Sr = 0, Qr = 0, P = 0;
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        Sr += rw[j][i];
+                        Qr += (long long)rw[j][i] * rw[j][i];
+                        P += lw[j][i] * rw[j][i];   // <= 12240^2, exact in int32
+                    }
+                c = coarse_from_sums(9 * P, Sl, Sr, Vl, 9 * Qr - Sr * Sr);
+            }
+            tile[threadIdx.x][k] = c;
+        }
+        __syncthreads();
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int x = warp; x < nx; x += kCoarseX / 32)
+            if (lane < ne) K[((size_t)Y * Wq + X0 + x) * Dq + e0 + lane] = tile[x][lane];
+        __syncthreads();
+    }
+}
+
+// Reading B3: row sums over the clipped 5-column window (X' ascending) ...
+constexpr int kAggR = 2;
+
+__global__ void band_row_sum_kernel(const float* __restrict__ K, int Hq, int Wq, int Dq, float* __restrict__ Kh)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)Hq * Wq * Dq) return;
+    const int e = (int)(i % Dq);
+    const size_t q = i / Dq;
+    const int X = (int)(q % Wq), Y = (int)(q / Wq);
+    float s = 0.f;
+    for (int x = max(0, X - kAggR); x <= min(Wq - 1, X + kAggR); ++x) s = __fadd_rn(s, K[((size_t)Y * Wq + x) * Dq + e]);
+    Kh[i] = s;
+}
+
+// ... then the sum of the row sums (Y' ascending) divided by the tap count.
+__global__ void band_col_mean_kernel(const float* __restrict__ Kh, int Hq, int Wq, int Dq, float* __restrict__ Kb)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)Hq * Wq * Dq) return;
+    const int e = (int)(i % Dq);
+    const size_t q = i / Dq;
+    const int X = (int)(q % Wq), Y = (int)(q / Wq);
+    const int y0 = max(0, Y - kAggR), y1 = min(Hq - 1, Y + kAggR);
+    const int x0 = max(0, X - kAggR), x1 = min(Wq - 1, X + kAggR);
+    float s = 0.f;
+    for (int y = y0; y <= y1; ++y) s = __fadd_rn(s, Kh[((size_t)y * Wq + X) * Dq + e]);
+    Kb[i] = __fdiv_rn(s, (float)((y1 - y0 + 1) * (x1 - x0 + 1)));
+}
+
+// One thread per quarter pixel: winner of Kbar (smallest e on ties), the best
+// non-adjacent cost and the winner's neighbours give the six features; x0
+// receives them as BF16 [P][8] (two zero channels), feat (nullable) as FP32
+// [P][6], estar the winner.
+__global__ void __launch_bounds__(128)
+band_features_kernel(const int32_t* __restrict__ gq, const float* __restrict__ Kb, int H, int W, int C, int D,
+                     __nv_bfloat16* __restrict__ x0, float* __restrict__ feat, int32_t* __restrict__ estar)
+{
+    const int Hq = (H + 3) / 4, Wq = (W + 3) / 4, Dq = (D + 3) / 4;
+    const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
+    if (X >= Wq) return;
+    const size_t i = (size_t)Y * Wq + X;
+    const float* k = Kb + i * Dq;
+    int best = 0;
+    float k1 = k[0];
+    for (int e = 1; e < Dq; ++e) {
+        const float v = k[e];
+        if (v < k1) {
+            k1 = v;
+            best = e;
         }
     }
-    const int best = ki[0];
-    const float k1 = kv[0];
     float k2 = 2.f;
-#pragma unroll
-    for (int j = 1; j < 4; ++j)
-        if (ki[j] >= 0 && abs(ki[j] - best) >= 2) {
-            k2 = fminf(k2, kv[j]);
-            break;
-        }
-    const float km = best > 0 ? coarse_cost_at(gl, gr, Hq, Wq, X, Y, best - 1) : 2.f;
-    const float kp = best < Dq - 1 ? coarse_cost_at(gl, gr, Hq, Wq, X, Y, best + 1) : 2.f;
+    for (int e = 0; e < Dq; ++e)
+        if (abs(e - best) >= 2 && k[e] < k2) k2 = k[e];
+    const float km = best > 0 ? k[best - 1] : 2.f;
+    const float kp = best < Dq - 1 ? k[best + 1] : 2.f;
     float f[6];
-    f[0] = __fsub_rn(__fdiv_rn((float)gl[(size_t)Y * Wq + X], (float)(16 * 255 * C)), 0.5f);
+    f[0] = __fsub_rn(__fdiv_rn((float)gq[i], (float)(16 * 255 * C)), 0.5f);
     f[1] = __fdiv_rn((float)best, (float)Dq);
     f[2] = k1;
     const float margin = __fsub_rn(k2, k1);
     f[3] = margin < 1.f ? margin : 1.f;
     f[4] = __fsub_rn(km, k1);
     f[5] = __fsub_rn(kp, k1);
-    const size_t i = (size_t)Y * Wq + X;
     estar[i] = best;
     __nv_bfloat162 h[4];
     h[0] = __floats2bfloat162_rn(f[0], f[1]);
@@ -278,6 +299,8 @@ size_t al256(size_t n) { return (n + 255) & ~(size_t)255; }
 // Scratch of one quarter-resolution problem, carved from ctx->band_ws.
 struct NetScratch {
     int32_t* gq;                 // [2][P]
+    float* kq;                   // coarse costs [P][Dq], then their 5x5 means
+    float* kh;                   // row sums [P][Dq]
     int32_t* estar;              // [P]
     __nv_bfloat16* x0;           // [P][8]
     __nv_bfloat16* y[5];         // [P][32]
@@ -291,10 +314,10 @@ struct NetScratch {
     int2* tile_range;
 };
 
-size_t net_scratch_bytes(int H, int W, bool training, bool full_res)
+size_t net_scratch_bytes(int H, int W, int D, bool training, bool full_res)
 {
-    const size_t Hq = (H + 3) / 4, Wq = (W + 3) / 4, P = Hq * Wq;
-    size_t n = al256(2 * P * 4) + al256(P * 4) + al256(P * 16) + 5 * al256(P * 64) + al256(P * 8);
+    const size_t Hq = (H + 3) / 4, Wq = (W + 3) / 4, P = Hq * Wq, Dq = (D + 3) / 4;
+    size_t n = al256(2 * P * 4) + 2 * al256(P * Dq * 4) + al256(P * 4) + al256(P * 16) + 5 * al256(P * 64) + al256(P * 8);
     if (training)
         n += 5 * al256(P * 64) + al256(P * 16) + al256(wgrad_partial_floats((int)Hq, (int)Wq) * 4) +
              al256((size_t)loss_blocks((int)P) * 4);
@@ -306,9 +329,9 @@ size_t net_scratch_bytes(int H, int W, bool training, bool full_res)
     return n;
 }
 
-NetScratch carve_net(void* base, int H, int W, bool training, bool full_res)
+NetScratch carve_net(void* base, int H, int W, int D, bool training, bool full_res)
 {
-    const size_t Hq = (H + 3) / 4, Wq = (W + 3) / 4, P = Hq * Wq;
+    const size_t Hq = (H + 3) / 4, Wq = (W + 3) / 4, P = Hq * Wq, Dq = (D + 3) / 4;
     uint8_t* q = (uint8_t*)base;
     auto take = [&](size_t bytes) {
         void* r = q;
@@ -317,6 +340,8 @@ NetScratch carve_net(void* base, int H, int W, bool training, bool full_res)
     };
     NetScratch s{};
     s.gq = (int32_t*)take(2 * P * 4);
+    s.kq = (float*)take(P * Dq * 4);
+    s.kh = (float*)take(P * Dq * 4);
     s.estar = (int32_t*)take(P * 4);
     s.x0 = (__nv_bfloat16*)take(P * 16);
     for (int l = 0; l < 5; ++l) s.y[l] = (__nv_bfloat16*)take(P * 64);
@@ -416,9 +441,28 @@ fbs_status run_features(fbs_ctx* ctx, const NetScratch& s, const uint8_t* L, con
         fbs::band_downsample_kernel<<<dim3((Wq + 127) / 128, Hq, 2), 128, 0, st>>>(L, R, H, W, C, s.gq);
         e = cudaGetLastError();
     }
+    const int Dq = (D + 3) / 4;
+    const size_t nv = (size_t)Hq * Wq * Dq;
     if (e == cudaSuccess) {
         LaunchScope ls(ctx, FBS_KERNEL_NET, st);
-        fbs::band_features_kernel<<<dim3((Wq + 127) / 128, Hq), 128, 0, st>>>(s.gq, H, W, C, D, s.x0, feat, s.estar);
+        fbs::band_coarse_cost_kernel<<<dim3((Wq + fbs::kCoarseX - 1) / fbs::kCoarseX, Hq), fbs::kCoarseX, 0, st>>>(
+            s.gq, Hq, Wq, Dq, s.kq);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        LaunchScope ls(ctx, FBS_KERNEL_NET, st);
+        fbs::band_row_sum_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(s.kq, Hq, Wq, Dq, s.kh);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        LaunchScope ls(ctx, FBS_KERNEL_NET, st);
+        fbs::band_col_mean_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(s.kh, Hq, Wq, Dq, s.kq);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        LaunchScope ls(ctx, FBS_KERNEL_NET, st);
+        fbs::band_features_kernel<<<dim3((Wq + 127) / 128, Hq), 128, 0, st>>>(s.gq, s.kq, H, W, C, D, s.x0, feat,
+                                                                              s.estar);
         e = cudaGetLastError();
     }
     return e == cudaSuccess ? FBS_OK : cuda_fail(ctx, e, "band feature launch");
@@ -621,9 +665,9 @@ fbs_status fbs_band_features(fbs_ctx* ctx, const uint8_t* left, const uint8_t* r
     if (!feat && !estar) return fail(ctx, FBS_ERR_INVALID_ARG, "both outputs are NULL");
     DeviceGuard g(ctx->device);
     cudaStream_t st = pick_stream(ctx, cuda_stream);
-    s = ensure(ctx, &ctx->band_ws, &ctx->band_ws_bytes, net_scratch_bytes(H, W, false, false), "band scratch");
+    s = ensure(ctx, &ctx->band_ws, &ctx->band_ws_bytes, net_scratch_bytes(H, W, D, false, false), "band scratch");
     if (s != FBS_OK) return s;
-    const NetScratch sc = carve_net(ctx->band_ws, H, W, false, false);
+    const NetScratch sc = carve_net(ctx->band_ws, H, W, D, false, false);
     s = run_features(ctx, sc, left, right, H, W, C, D, feat, st);
     if (s != FBS_OK || !estar) return s;
     const size_t P = (size_t)((H + 3) / 4) * ((W + 3) / 4);
@@ -641,9 +685,9 @@ fbs_status fbs_band_net_forward(fbs_ctx* ctx, const uint8_t* left, const uint8_t
     if ((s = need_ready(ctx)) != FBS_OK) return s;
     DeviceGuard g(ctx->device);
     cudaStream_t st = pick_stream(ctx, cuda_stream);
-    s = ensure(ctx, &ctx->band_ws, &ctx->band_ws_bytes, net_scratch_bytes(H, W, false, false), "band scratch");
+    s = ensure(ctx, &ctx->band_ws, &ctx->band_ws_bytes, net_scratch_bytes(H, W, D, false, false), "band scratch");
     if (s != FBS_OK) return s;
-    const NetScratch sc = carve_net(ctx->band_ws, H, W, false, false);
+    const NetScratch sc = carve_net(ctx->band_ws, H, W, D, false, false);
     const int Hq = (H + 3) / 4, Wq = (W + 3) / 4;
     if ((s = run_features(ctx, sc, left, right, H, W, C, D, nullptr, st)) != FBS_OK) return s;
     if ((s = run_forward(ctx, sc, Hq, Wq, st)) != FBS_OK) return s;
@@ -671,9 +715,9 @@ fbs_status fbs_band_net_train_step(fbs_ctx* ctx, const uint8_t* left, const uint
     if ((s = need_ready(ctx)) != FBS_OK) return s;
     DeviceGuard g(ctx->device);
     cudaStream_t st = pick_stream(ctx, cuda_stream);
-    s = ensure(ctx, &ctx->band_ws, &ctx->band_ws_bytes, net_scratch_bytes(H, W, true, false), "band scratch");
+    s = ensure(ctx, &ctx->band_ws, &ctx->band_ws_bytes, net_scratch_bytes(H, W, D, true, false), "band scratch");
     if (s != FBS_OK) return s;
-    const NetScratch sc = carve_net(ctx->band_ws, H, W, true, false);
+    const NetScratch sc = carve_net(ctx->band_ws, H, W, D, true, false);
     const int Hq = (H + 3) / 4, Wq = (W + 3) / 4;
     fbs_band_state* b = ctx->band;
     if ((s = run_features(ctx, sc, left, right, H, W, C, D, nullptr, st)) != FBS_OK) return s;
@@ -724,10 +768,10 @@ fbs_status fbs_compute_disparity_banded(fbs_ctx* ctx, const fbs_pair* pair, cons
     if (!centre || !conf) return fail(ctx, FBS_ERR_INVALID_ARG, "null centre or confidence");
     DeviceGuard g(ctx->device);
     cudaStream_t st = pick_stream(ctx, cuda_stream);
-    s = ensure(ctx, &ctx->band_ws, &ctx->band_ws_bytes, net_scratch_bytes(pair->H, pair->W, false, true),
+    s = ensure(ctx, &ctx->band_ws, &ctx->band_ws_bytes, net_scratch_bytes(pair->H, pair->W, pair->D, false, true),
                "band scratch");
     if (s != FBS_OK) return s;
-    const NetScratch sc = carve_net(ctx->band_ws, pair->H, pair->W, false, true);
+    const NetScratch sc = carve_net(ctx->band_ws, pair->H, pair->W, pair->D, false, true);
     return run_banded(ctx, pair, centre, conf, half_band, conf_threshold, sc, st);
 }
 
@@ -741,9 +785,9 @@ fbs_status fbs_compute_disparity_learned(fbs_ctx* ctx, const fbs_pair* pair, int
     DeviceGuard g(ctx->device);
     cudaStream_t st = pick_stream(ctx, cuda_stream);
     const int H = pair->H, W = pair->W;
-    s = ensure(ctx, &ctx->band_ws, &ctx->band_ws_bytes, net_scratch_bytes(H, W, false, true), "band scratch");
+    s = ensure(ctx, &ctx->band_ws, &ctx->band_ws_bytes, net_scratch_bytes(H, W, pair->D, false, true), "band scratch");
     if (s != FBS_OK) return s;
-    const NetScratch sc = carve_net(ctx->band_ws, H, W, false, true);
+    const NetScratch sc = carve_net(ctx->band_ws, H, W, pair->D, false, true);
     const int Hq = (H + 3) / 4, Wq = (W + 3) / 4;
     if ((s = run_features(ctx, sc, pair->left, pair->right, H, W, pair->C, pair->D, nullptr, st)) != FBS_OK) return s;
     if ((s = run_forward(ctx, sc, Hq, Wq, st)) != FBS_OK) return s;

@@ -290,24 +290,28 @@ loss_kernel(const float* __restrict__ out, const int32_t* __restrict__ estar, co
         if (!(m >= 0.f)) m = 0.f;
         if (m > (float)(D - 1)) m = (float)(D - 1);
         const int mi = (int)m;
-        float s = 0.f;
-        int cnt = 0, ok = 1;
+        // centre target: median of the block's subpixel labels; confidence
+        // target: share of its integer labels inside [m - h + 1, m + h - 1]
+        float v[16];
+        int cnt = 0, in = 0;
         for (int yy = 4 * Y; yy < 4 * Y + 4 && yy < H; ++yy)
             for (int xx = 4 * X; xx < 4 * X + 4 && xx < W; ++xx) {
                 const size_t p = (size_t)yy * W + xx;
-                s += label_sub[p];
-                ++cnt;
+                float a = label_sub[p];
+                int k = cnt++;
+                for (; k > 0 && v[k - 1] > a; --k) v[k] = v[k - 1];   // insertion sort
+                v[k] = a;
                 const int d = label_int[p];
-                if (d < mi - h + 1 || d > mi + h - 1) ok = 0;
+                if (d >= mi - h + 1 && d <= mi + h - 1) ++in;
             }
-        const float t = s / (float)cnt;
+        const float t = (cnt & 1) ? v[cnt / 2] : 0.5f * (v[cnt / 2 - 1] + v[cnt / 2]);
+        const float y = (float)in / (float)cnt;
         const float e = c - t, ae = fabsf(e);
         const float huber = ae <= 1.f ? 0.5f * e * e : ae - 0.5f;
-        const float y = (float)ok;
         const float bce = fmaxf(z, 0.f) - z * y + log1pf(expf(-fabsf(z)));
-        li = huber + bce;
+        li = y * huber + bce;
         const float invP = 1.f / (float)P;
-        const float g0 = 4.f * fminf(fmaxf(e, -1.f), 1.f) * invP;
+        const float g0 = 4.f * y * fminf(fmaxf(e, -1.f), 1.f) * invP;
         const float g1 = (1.f / (1.f + expf(-z)) - y) * invP;
         reinterpret_cast<uint4*>(G6)[i] = make_uint4(pack_bf16x2(g0, g1), 0u, 0u, 0u);
     }
