@@ -75,6 +75,8 @@ def _args():
     ap.add_argument("--band", action="store_true",
                     help="time the learned band form on the 1920x1080 RGB pair, D=256, radius 9 (network proposal "
                          "plus band-restricted path) against the plain full-range forms on the same pair")
+    ap.add_argument("--band-shape", default=None,
+                    help="WxH of the band workload's pair (default 1920x1080; smaller shapes are for profiling)")
     ap.add_argument("--band-threshold", type=float, default=None,
                     help="confidence threshold of the band form (default: the one shipped with the weights)")
     return ap.parse_args()
@@ -591,7 +593,11 @@ def run_band(args):
     dev = torch.device("cuda", 0)
     steps = args.steps if args.steps is not None else 200
     warmup = max(3, args.warmup if args.warmup is not None else 5)
-    p = make_pair(BAND_WORKLOAD, args.seed)
+    if args.band_shape:
+        bw, bh = (int(v) for v in args.band_shape.lower().split("x"))
+        p = make_pair(BAND_WORKLOAD, args.seed, H=bh, W=bw)
+    else:
+        p = make_pair(BAND_WORKLOAD, args.seed)
     stream = torch.cuda.Stream(dev)
     dl = torch.from_numpy(p.left).to(dev)
     dr = torch.from_numpy(p.right).to(dev)
@@ -696,7 +702,8 @@ def run_band(args):
     out = {"metric": METRIC, "value": taps / (step_ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": steps,
            "warmup": warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32 (network bf16)", "data": "synthetic",
-           "config": {"workload": BAND_WORKLOAD, "H": H, "W": W, "C": 3, "D": D, "radius": p.radius,
+           "config": {"workload": BAND_WORKLOAD if not args.band_shape else f"{BAND_WORKLOAD} at {W}x{H}",
+                      "H": H, "W": W, "C": 3, "D": D, "radius": p.radius,
                       "half_band": HALF_BAND, "conf_threshold": thr, "seed": args.seed,
                       "weights": os.path.relpath(fbs.default_band_net_path(), ROOT),
                       "work_fraction": work, "fallback_pct": 100.0 * fallback,
