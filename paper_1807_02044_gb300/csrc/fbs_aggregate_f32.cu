@@ -176,13 +176,27 @@ __device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, i
     // WTA role (tid < kNPix): state of pixel tid carried across chunks
     float best = __int_as_float(0x7f800000), a_prev = 0.f, a_next = 0.f, last = 0.f;
     int blo = 0, bhi = D - 1;
-    if (band != nullptr && tid < kNPix) {
-        const int oy = y0 + tid / kTX, ox = x0 + tid % kTX;
-        if (oy < H && ox < W) {
-            const uint32_t b = band[(size_t)oy * W + ox];
-            blo = (int)(b & 0xffffu);
-            bhi = (int)(b >> 16);
+    // Disparity range of each 4-column group (the pixels of one consumer
+    // warp): the union of its pixels' bands.  A warp skips the chunks outside
+    // its range, and the weights of its pixels are not generated for them.
+    __shared__ int grp_lo[kTX / kPX], grp_hi[kTX / kPX];
+    if (band != nullptr) {
+        if (tid < kTX / kPX) {
+            grp_lo[tid] = D;
+            grp_hi[tid] = -1;
         }
+        __syncthreads();
+        if (tid < kNPix) {
+            const int oy = y0 + tid / kTX, ox = x0 + tid % kTX;
+            if (oy < H && ox < W) {
+                const uint32_t b = band[(size_t)oy * W + ox];
+                blo = (int)(b & 0xffffu);
+                bhi = (int)(b >> 16);
+                atomicMin(&grp_lo[(tid % kTX) / kPX], blo);
+                atomicMax(&grp_hi[(tid % kTX) / kPX], bhi);
+            }
+        }
+        __syncthreads();
     }
     int bidx = blo;
     bool pending = false;
@@ -194,6 +208,9 @@ __device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, i
     const int nr = r_hi - r_lo + 1;
 
     for (int dc0 = d_begin; dc0 < d_end; dc0 += DC) {
+        // this chunk is needed by the producer's pixel group / the consumer's group
+        const bool p_on = band == nullptr || (grp_hi[ppx / kPX] >= dc0 && grp_lo[ppx / kPX] < dc0 + DC);
+        const bool c_on = band == nullptr || (grp_hi[g] >= dc0 && grp_lo[g] < dc0 + DC);
         float4 acc[kPX][NQ];
 #pragma unroll
         for (int i = 0; i < kPX; ++i)
@@ -217,7 +234,7 @@ __device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, i
             // (C) weights of row r for every tile pixel whose window reaches it
             {
                 const int dy = r - py;
-                if (py < H && dy >= -rho && dy <= rho) {
+                if (p_on && py < H && dy >= -rho && dy <= rho) {
                     const float4* gr = gring + (s % 3) * NC;
                     float* wrow = wring + (s & 1) * wslot + pyi * WS;
                     const int dy2 = dy * dy;
@@ -242,7 +259,7 @@ __device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, i
             __syncthreads();
             // (F) accumulate row r
             const int dy = r - y;
-            if (y < H && dy >= -rho && dy <= rho) {
+            if (c_on && y < H && dy >= -rho && dy <= rho) {
                 const float* cr = cring + (s % 3) * cslot + (kPX * g) * DC + 4 * k;
                 const float* wr = wring + (s & 1) * wslot + yi * WS + kPX * g;
                 float4 win[4][NQ];
