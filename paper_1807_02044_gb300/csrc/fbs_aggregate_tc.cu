@@ -55,7 +55,7 @@ constexpr int kEpilogue = 128;
 constexpr int kTmaWarp = kEpiWarp0 + 4;
 constexpr int kMmaWarp = kTmaWarp + 1;
 constexpr int kThreads = 32 * (kMmaWarp + 1);
-constexpr int kMaxR = 4;          // window rows per stage, at most
+constexpr int kMaxR = 5;          // window rows per stage, at most
 struct TcParams {
     int H, W, C, D;
     int N;          // round_up(D, 16): disparity rows the TMA box loads
@@ -324,7 +324,11 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                     stop = true;
                     break;
                 }
-                for (int r = 0; r < nr; ++r) {
+                // rows unrolled: a thread keeps up to kMaxR * kPasses independent
+                // weight chains in flight
+#pragma unroll
+                for (int r = 0; r < kMaxR; ++r) {
+                    if (r >= nr) break;
                     const int hr = h0 + r;
                     uint8_t* arow = a_base + s * a_stage + r * a_row;
                     const uint2* grow = gt + hr * KW;
@@ -656,7 +660,7 @@ bool tc_plan(int H, int W, int C, int D, int radius, float sigma_s, float sigma_
     const uint32_t base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kM >> 4) << 24);
     p.idesc = base | ((uint32_t)((p.ones_sep ? p.N : p.Nb) >> 3) << 17);
     p.idesc16 = base | (2u << 17);
-    // R window rows per stage and S stages: the largest R (<= 4) with at least
+    // R window rows per stage and S stages: the largest R (<= kMaxR) with at least
     // 3 stages in 227 KB, then as many stages (<= 6) as fit
     for (p.R = kMaxR; p.R >= 1; --p.R) {
         for (p.S = 6; p.S >= 3; --p.S) {
