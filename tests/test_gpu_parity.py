@@ -222,3 +222,39 @@ def test_full_size_bench_workload_sampled(fbs, ctx, oracle_mod):
     err = check_agg(agg[y0:y1], bagg, 2.0)
     stats = check_disparities(di[y0:y1], ds[y0:y1], bagg, bi, bs, 2.0, err)
     assert stats["near_ties"] < 0.01 * stats["pixels"]
+
+
+# ---------------------------------------------------------------------------
+# The other stated workloads
+# ---------------------------------------------------------------------------
+def test_gray160x120_whole_frame(fbs, ctx, oracle_mod):
+    """160x120 grey, D=16, radius 4 (9x9), sigma_s 4, sigma_r 10: every pixel
+    against the oracle."""
+    from synth import make_pair
+    p = make_pair("gray160x120_d16_r4", 0)
+    dl, dr = _dev(p.left), _dev(p.right)
+    cost = ctx.cost_volume(dl, dr, p.D)
+    agg, di, ds = ctx.aggregate(cost, dl, p.radius, p.sigma_s, p.sigma_r)
+    di2, ds2 = ctx.compute_disparity(dl, dr, p.D, p.radius, p.sigma_s, p.sigma_r)
+    torch.cuda.synchronize()
+    ref_di, ref_ds, ref_agg = oracle_mod.fbs(p.left, p.right, p.D, p.radius, p.sigma_s, p.sigma_r, want_agg=True)
+    err = check_agg(agg.cpu().numpy(), ref_agg, 2.0)
+    check_disparities(di2.cpu().numpy(), ds2.cpu().numpy(), ref_agg, ref_di, ref_ds, 2.0, err)
+
+
+def test_full_size_1280x960_sampled(fbs, ctx, oracle_mod):
+    """1280x960 RGB, D=128, radius 15 (31x31): 120 sampled pixels against the
+    oracle's point evaluation."""
+    from synth import make_pair
+    p = make_pair("rgb1280x960_d128_r15", 0)
+    dl, dr = _dev(p.left), _dev(p.right)
+    cost = ctx.cost_volume(dl, dr, p.D)
+    agg, di, ds = ctx.aggregate(cost, dl, p.radius, p.sigma_s, p.sigma_r)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    xs = np.concatenate([rng.integers(0, p.W, 116), [0, p.W - 1, 0, p.W - 1]])
+    ys = np.concatenate([rng.integers(0, p.H, 116), [0, 0, p.H - 1, p.H - 1]])
+    ref_di, ref_ds, ref_agg = oracle_mod.fbs_points(p.left, p.right, p.D, p.radius, p.sigma_s, p.sigma_r, xs, ys)
+    agg_s = agg[torch.from_numpy(ys).cuda(), torch.from_numpy(xs).cuda()].cpu().numpy()
+    err = check_agg(agg_s, ref_agg, 2.0)
+    check_disparities(di.cpu().numpy()[ys, xs], ds.cpu().numpy()[ys, xs], ref_agg, ref_di, ref_ds, 2.0, err)

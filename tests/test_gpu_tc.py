@@ -106,3 +106,32 @@ def test_tc_full_size_bench_workload_bad_pixels(fbs, oracle_mod, prec):
     assert bad16 - bad32 <= 0.005, (bad32, bad16)
     # whole frame against the FP32 path
     assert np.mean(np.abs(out[prec] - out["f32"]) > 1.0) <= 0.005
+
+
+def test_tc_f16_1280x960_d128_r15(fbs, oracle_mod):
+    """The precision-at-scale workload: 1280x960 RGB, D=128, radius 15, FP16
+    operands.  Sampled aggregated costs within the FP16 rounding bound of the
+    FP64 oracle; extra bad pixels (> 1 px) over the FP32 form at most 0.5%."""
+    from synth import make_pair
+    p = make_pair("rgb1280x960_d128_r15", 0)
+    dl, dr = _dev(p.left), _dev(p.right)
+    with fbs.Context(0, prec=fbs.FBS_PREC_F32) as c32:
+        _, ds32 = c32.compute_disparity(dl, dr, p.D, p.radius, p.sigma_s, p.sigma_r)
+        torch.cuda.synchronize()
+    with fbs.Context(0, prec=fbs.FBS_PREC_F16) as c16:
+        _, ds16 = c16.compute_disparity(dl, dr, p.D, p.radius, p.sigma_s, p.sigma_r)
+        cost = c16.cost_volume(dl, dr, p.D)
+        agg, _, _ = c16.aggregate(cost, dl, p.radius, p.sigma_s, p.sigma_r)
+        torch.cuda.synchronize()
+        fbs.fbs_sync(c16.ctx)
+    rng = np.random.default_rng(9)
+    xs, ys = rng.integers(0, p.W, 60), rng.integers(0, p.H, 60)
+    _, _, ref_agg = oracle_mod.fbs_points(p.left, p.right, p.D, p.radius, p.sigma_s, p.sigma_r, xs, ys)
+    agg_s = agg[torch.from_numpy(ys).cuda(), torch.from_numpy(xs).cuda()].cpu().numpy()
+    err = np.abs(agg_s - ref_agg).max()
+    tol = 3 * U["f16"] * 2.0 + 1e-5
+    print(f"1280x960 D=128 r=15 FP16: max |dAgg| vs FP64 oracle {err:.3e} (bound {tol:.3e})")
+    assert err <= tol
+    bad = float(np.mean(np.abs(ds16.cpu().numpy() - ds32.cpu().numpy()) > 1.0))
+    print(f"extra bad pixels over FP32: {100 * bad:.4f}%")
+    assert bad <= 0.005
