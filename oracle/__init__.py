@@ -63,6 +63,9 @@ def _load():
             lib.oracle_fbs_rows.restype = I
             lib.oracle_fbs_points.argtypes = [P, P, I, I, I, I, I, Dd, Dd, Dd, I, I, P, P, P, P, P]
             lib.oracle_fbs_points.restype = I
+            lib.oracle_fbs_right_rows.argtypes = [P, P, I, I, I, I, I, Dd, Dd, Dd, I, I, I, P, P, P]
+            lib.oracle_fbs_right_rows.restype = I
+            lib.oracle_lrc.argtypes = [P, P, I, I, P]
             lib.oracle_band_downsample.argtypes = [P, I, I, I, P]
             lib.oracle_band_features.argtypes = [P, P, I, I, I, I, P, P]
             lib.oracle_band_features.restype = I
@@ -151,6 +154,33 @@ def fbs(left, right, D, radius, sigma_s, sigma_r, tau=0.0, mode=COST_NCC, rows=N
         raise MemoryError("oracle_fbs_rows could not allocate its cost rows")
     assert n == di.size
     return (di, ds, agg) if want_agg else (di, ds)
+
+
+def fbs_right(left, right, D, radius, sigma_s, sigma_r, tau=0.0, mode=COST_NCC, rows=None, want_agg=False):
+    """The right view: the right cost volume C_r(u, v, d) = C_l(u + d, v, d) (max cost
+    where u + d >= W), aggregated with the right image as guide, WTA and Eq. (10)."""
+    L, R = _img(left), _img(right)
+    H, W, C = L.shape
+    y0, y1 = rows if rows is not None else (0, H)
+    di = np.empty((y1 - y0, W), np.int32)
+    ds = np.empty((y1 - y0, W), np.float64)
+    agg = np.empty((y1 - y0, W, D), np.float64) if want_agg else None
+    rc = _load().oracle_fbs_right_rows(_ptr(L), _ptr(R), H, W, C, D, int(radius), float(sigma_s),
+                                       float(sigma_r), float(tau), int(mode), y0, y1,
+                                       _ptr(agg) if want_agg else None, _ptr(di), _ptr(ds))
+    if rc != 0:
+        raise MemoryError("oracle_fbs_right_rows could not allocate its cost rows")
+    return (di, ds, agg) if want_agg else (di, ds)
+
+
+def lrc(d_left, d_right):
+    """Eq. (9): 1 where the left disparity is confirmed by the right map, else 0."""
+    dl = np.ascontiguousarray(d_left, np.int32)
+    dr = np.ascontiguousarray(d_right, np.int32)
+    H, W = dl.shape
+    out = np.empty((H, W), np.int32)
+    _load().oracle_lrc(_ptr(dl), _ptr(dr), H, W, _ptr(out))
+    return out
 
 
 def fbs_points(left, right, D, radius, sigma_s, sigma_r, xs, ys, tau=0.0, mode=COST_NCC):

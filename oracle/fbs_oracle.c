@@ -258,3 +258,52 @@ int oracle_fbs_points(const uint8_t *L, const uint8_t *R, int H, int W, int C, i
     free(num);
     return 0;
 }
+
+/*
+ * Right view (Sec. II-A, Sec. III): the right cost volume stores the same costs
+ * as the left one, C_r(u_r, v, d) = C_l(u_r + d, v, d); where u_r + d >= W no
+ * left pixel exists and the cost is the maximum (2 for NCC, tau for TAD;
+ * reading R6).  The right aggregation is guided by the right image (R5), and
+ * WTA / Eq. (10) follow as on the left.
+ */
+double oracle_cost_right(const uint8_t *L, const uint8_t *R, int H, int W, int C, int ur, int v, int d,
+                         int mode, double tau)
+{
+    if (ur + d >= W) return mode == 0 ? 2.0 : tau;
+    return oracle_cost(L, R, H, W, C, ur + d, v, d, mode, tau);
+}
+
+int oracle_fbs_right_rows(const uint8_t *L, const uint8_t *R, int H, int W, int C, int D, int rho,
+                          double gamma_d, double gamma_r, double tau, int mode, int y0, int y1,
+                          double *agg_out, int32_t *d_int, double *d_sub)
+{
+    int c0 = y0 - rho < 0 ? 0 : y0 - rho;
+    int c1 = y1 + rho > H ? H : y1 + rho;
+    size_t crow = (size_t)W * D;
+    double *cost = (double *)malloc(sizeof(double) * crow * (size_t)(c1 - c0));
+    double *agg = agg_out ? agg_out : (double *)malloc(sizeof(double) * crow * (size_t)(y1 - y0));
+    if (!cost || !agg) { free(cost); if (!agg_out) free(agg); return -1; }
+    for (int v = c0; v < c1; ++v)
+        for (int u = 0; u < W; ++u)
+            for (int d = 0; d < D; ++d)
+                cost[((size_t)(v - c0) * W + u) * D + d] = oracle_cost_right(L, R, H, W, C, u, v, d, mode, tau);
+    oracle_aggregate_rows(cost, c0, R, H, W, C, D, rho, gamma_d, gamma_r, y0, y1, agg);
+    oracle_wta_subpixel(agg, (y1 - y0) * W, D, d_int, d_sub);
+    free(cost);
+    if (!agg_out) free(agg);
+    return 0;
+}
+
+/*
+ * Left-right consistency, Eq. (9): the left disparity d at (u, v) is kept when
+ * u - d >= 0 and the right disparity at (u - d, v) equals d exactly
+ * (reading R14); valid[p] = 1 or 0.
+ */
+void oracle_lrc(const int32_t *d_left, const int32_t *d_right, int H, int W, int32_t *valid)
+{
+    for (int v = 0; v < H; ++v)
+        for (int u = 0; u < W; ++u) {
+            const int d = d_left[(size_t)v * W + u];
+            valid[(size_t)v * W + u] = (u - d >= 0 && d_right[(size_t)v * W + u - d] == d) ? 1 : 0;
+        }
+}

@@ -295,3 +295,50 @@ def test_e_pep_golden(oracle_mod):
 def test_mde_per_s_formula(oracle_mod):
     # Eq. (13): u_max v_max d_max / t * 1e-6
     assert oracle_mod.mde_per_s(450, 375, 60, 0.5) == pytest.approx(20.25)
+
+
+# ---------------------------------------------------------------------------
+# Right view and the left-right consistency check, Eq. (9)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("mode,C", [(0, 3), (1, 1)])
+def test_right_view_is_the_mirrored_left_view_of_the_swapped_pair(oracle_mod, mode, C):
+    """Mirroring both images and swapping them turns the right view into a
+    left view: right_fbs(L, R) = mirror(left_fbs(mirror(R), mirror(L))).  This
+    goes through the pinned left path by an independent route."""
+    rng = np.random.default_rng(31 + mode)
+    H, W, D, r = 9, 23, 7, 2
+    L = _rand_img(rng, H, W, C)
+    R = np.roll(L, -2, axis=1)
+    R[:, -2:] = _rand_img(rng, H, 2, C)
+    di, ds, agg = oracle_mod.fbs_right(L, R, D, r, 2.0, 10.0, tau=25.0, mode=mode, want_agg=True)
+    mi, ms, magg = oracle_mod.fbs(R[:, ::-1], L[:, ::-1], D, r, 2.0, 10.0, tau=25.0, mode=mode, want_agg=True)
+    np.testing.assert_allclose(agg, magg[:, ::-1], rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(di, mi[:, ::-1])
+    np.testing.assert_allclose(ds, ms[:, ::-1], rtol=0, atol=1e-9)
+
+
+def test_lrc_on_a_shifted_texture(oracle_mod):
+    """Right = left shifted by d0 (noise free): every left pixel with a match
+    (x >= d0) away from the borders is confirmed, and the unmatched strip
+    x < d0 - 1 is rejected wherever its left winner is not the true d0."""
+    H, W, D, d0, r = 12, 40, 12, 5, 2
+    L, R = shifted_texture_pair(H, W, 1, d0, seed=4)
+    dl, _ = oracle_mod.fbs(L, R, D, r, 2.0, 10.0)
+    dr, _ = oracle_mod.fbs_right(L, R, D, r, 2.0, 10.0)
+    ok = oracle_mod.lrc(dl, dr)
+    assert np.all(dl[r + 1:-r - 1, d0 + r + 1:-r - 1] == d0)
+    assert np.all(dr[r + 1:-r - 1, r + 1:W - d0 - r - 1] == d0)
+    assert np.all(ok[r + 1:-r - 1, d0 + r + 1:-r - 1] == 1)
+    strip = ok[:, :d0]
+    assert np.all(strip[dl[:, :d0] > np.arange(d0)[None, :]] == 0)   # u - d < 0 is never confirmed
+
+
+def test_lrc_definition_bruteforce(oracle_mod):
+    rng = np.random.default_rng(2)
+    dl = rng.integers(0, 6, (5, 9)).astype(np.int32)
+    dr = rng.integers(0, 6, (5, 9)).astype(np.int32)
+    ok = oracle_mod.lrc(dl, dr)
+    for v in range(5):
+        for u in range(9):
+            d = dl[v, u]
+            assert ok[v, u] == int(u - d >= 0 and dr[v, u - d] == d)
