@@ -75,6 +75,8 @@ def _args():
     ap.add_argument("--band", action="store_true",
                     help="time the learned band form on the 1920x1080 RGB pair, D=256, radius 9 (network proposal "
                          "plus band-restricted path) against the plain full-range forms on the same pair")
+    ap.add_argument("--lr", action="store_true",
+                    help="time both views and the left-right consistency check (FP32) on the default workload")
     ap.add_argument("--band-shape", default=None,
                     help="WxH of the band workload's pair (default 1920x1080; smaller shapes are for profiling)")
     ap.add_argument("--band-threshold", type=float, default=None,
@@ -723,6 +725,56 @@ def run_band(args):
     return 0
 
 
+def run_lr(args):
+    """One step = both disparity maps and the LRC check (Eq. (9)) through
+    fbs_compute_disparity_lr (FP32): one cost pass storing both volumes, two
+    aggregations, the check.  Gtaps/s counts the taps of both views."""
+    import numpy as np
+    import torch
+
+    import paper_1807_02044_gb300 as fbs
+    from synth import make_pair
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    steps = args.steps if args.steps is not None else 500
+    warmup = max(3, args.warmup if args.warmup is not None else 10)
+    p = make_pair(args.workload, args.seed)
+    stream = torch.cuda.Stream(dev)
+    dl = torch.from_numpy(p.left).to(dev)
+    dr = torch.from_numpy(p.right).to(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    H, W, D = p.H, p.W, p.D
+    li = torch.empty((H, W), dtype=torch.int32, device=dev)
+    ls = torch.empty((H, W), device=dev)
+    ri = torch.empty((H, W), dtype=torch.int32, device=dev)
+    rs = torch.empty((H, W), device=dev)
+    ctx = fbs.Context(0)
+    res = _time_call(fbs, torch, ctx, lambda: fbs.fbs_compute_disparity_lr(
+        ctx.ctx, dl, dr, H, W, p.C, D, p.radius, p.sigma_s, p.sigma_r, p.tau, li, ls, ri, rs, True, stream),
+        stream, flush, steps, warmup)
+    one = _time_call(fbs, torch, ctx, lambda: fbs.fbs_compute_disparity(
+        ctx.ctx, dl, dr, H, W, p.C, D, p.radius, p.sigma_s, p.sigma_r, p.tau, ri, rs, stream),
+        stream, flush, steps, warmup)
+    rejected = float((li == -1).float().mean().item())
+    gt_ok = torch.from_numpy(~p.occ).to(dev)
+    occ_rejected = float(((li == -1) & ~gt_ok).float().sum().item() / max(1.0, float((~gt_ok).sum().item())))
+    taps = 2 * _taps(p)
+    kt = res["kt"]
+    out = {"metric": METRIC, "value": taps / (res["step_ms"] * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1,
+           "steps": steps, "warmup": warmup, "ms_per_step": res["step_ms"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": args.workload, "views": "left + right + LRC (Eq. 9)", "seed": args.seed,
+                      "l2": "512 MiB flush write before every step, outside the per-step CUDA-event timing"},
+           "fps": 1e3 / res["step_ms"], "left_only_ms": one["step_ms"],
+           "kernel_ms_per_step": {k: v[0] / steps for k, v in kt.items() if v[1]},
+           "lrc_rejected_pct": 100.0 * rejected, "occluded_px_rejected_pct": 100.0 * occ_rejected,
+           "gpu_launches": sum(n for _, n in kt.values()), "roofline": None, "cpu_baseline": None, "e2e": None}
+    print(json.dumps(out))
+    ctx.close()
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -731,6 +783,8 @@ def main():
         return run_batched(args)
     if args.band:
         return run_band(args)
+    if args.lr:
+        return run_lr(args)
     return run_ours(args)
 
 

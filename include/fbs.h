@@ -110,6 +110,26 @@ fbs_status fbs_compute_disparity_host(fbs_ctx *ctx, const uint8_t *left, const u
                                       int32_t *disp_int, float *disp_subpix);
 
 /*
+ * Both views and the left-right consistency (LRC) check (Sec. II-A, Sec. III,
+ * Eq. (9)).  Each matching cost is computed once and stored twice: in the left
+ * volume at (u, v, d) and in the right volume at (u - d, v, d); where u + d >= W
+ * the right volume holds the maximum cost.  Each volume is aggregated with its
+ * own image as guide (Eq. (6)-(8)), WTA and Eq. (10) give both maps.
+ *   disp_int / disp_subpix: the LEFT map (either may be NULL, not both); with
+ *     lrc != 0 every left pixel whose disparity d fails Eq. (9) -- u - d < 0 or
+ *     the right disparity at (u - d, v) differs from d -- is set to -1 in both.
+ *   disp_int_right / disp_subpix_right (each nullable): the right map.
+ * FP32 arithmetic whatever the context's precision.  Scratch: two cost volumes
+ * (2 * H*W*round_up(D,4)*4 bytes) and two integer maps.
+ */
+fbs_status fbs_compute_disparity_lr(fbs_ctx *ctx, const uint8_t *left, const uint8_t *right,
+                                    int H, int W, int C, int D, int radius,
+                                    float sigma_s, float sigma_r, float tau,
+                                    int32_t *disp_int, float *disp_subpix,
+                                    int32_t *disp_int_right, float *disp_subpix_right, int lrc,
+                                    void *cuda_stream);
+
+/*
  * Step 1 alone, Eq. (1)-(3) (or TAD): writes cost_out[H][W][D] (device,
  * float32, caller-owned).  For u - d < 0 the cost is the maximum (2 for NCC,
  * tau for TAD); a zero-variance block gives c = 0.

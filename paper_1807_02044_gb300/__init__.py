@@ -75,6 +75,7 @@ SIGNATURES = {
     "fbs_compute_disparity": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _F, _P, _P, _P]),
     "fbs_compute_disparity_host": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _F, _P, _P]),
     "fbs_cost_volume": (_I, [_P, _P, _P, _I, _I, _I, _I, _F, _P, _P]),
+    "fbs_compute_disparity_lr": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _F, _P, _P, _P, _P, _I, _P]),
     "fbs_aggregate": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _P, _P, _P, _P]),
     "fbs_compute_disparity_noalloc": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _F, _P, _P, _P]),
     "fbs_compute_disparity_batched": (_I, [_P, _I, _P, _P]),
@@ -217,6 +218,15 @@ def fbs_compute_disparity_noalloc(ctx, left, right, H, W, C, D, radius, sigma_s,
     _check(ctx, lib().fbs_compute_disparity_noalloc(ctx, _addr(left), _addr(right), H, W, C, D, radius, sigma_s,
                                                     sigma_r, tau, _addr(disp_int), _addr(disp_subpix),
                                                     _stream(stream)))
+
+
+def fbs_compute_disparity_lr(ctx, left, right, H, W, C, D, radius, sigma_s, sigma_r, tau, disp_int, disp_subpix,
+                             disp_int_right=None, disp_subpix_right=None, lrc=True, stream=None):
+    """Both views and the left-right consistency check (Eq. (9)); rejected left
+    pixels are -1 in both left outputs when lrc is true."""
+    _check(ctx, lib().fbs_compute_disparity_lr(ctx, _addr(left), _addr(right), H, W, C, D, radius, sigma_s, sigma_r,
+                                              tau, _addr(disp_int), _addr(disp_subpix), _addr(disp_int_right),
+                                              _addr(disp_subpix_right), int(bool(lrc)), _stream(stream)))
 
 
 def fbs_cost_volume(ctx, left, right, H, W, C, D, tau, cost_out, stream=None):

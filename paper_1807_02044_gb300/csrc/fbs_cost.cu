@@ -148,12 +148,14 @@ __device__ __forceinline__ void store8(T* o, const T (&v)[8])
 // MODE 0: NCC from the statistics planes; MODE 1: TAD from the raw images.
 // PLANAR false: out is [H][W][ld] (T = float); true: out is x-blocked [H][ld][D][8] with ld = ceil(W/8).
 // One row y and 128 pixels from x0, disparities [d_begin, d_end) (all: 0, D);
-// ends with a __syncthreads.
+// ends with a __syncthreads.  out_r (nullable, FP32 layout only): the right
+// view's volume, which holds the same costs at (x - d, y, d) (Sec. II-A, Sec. III).
 template <int MODE, typename T, bool PLANAR>
 __device__ __forceinline__ void cost_tile(const int16_t* __restrict__ gplane, const int* __restrict__ splane,
                                           const float* __restrict__ rvplane, const uint8_t* __restrict__ L,
                                           const uint8_t* __restrict__ R, int H, int W, int C, int D, int ld, float tau,
-                                          T* __restrict__ out, int x0, int y, int* smem_i, int d_begin, int d_end)
+                                          T* __restrict__ out, int x0, int y, int* smem_i, int d_begin, int d_end,
+                                          float* __restrict__ out_r = nullptr)
 {
     const int tid = threadIdx.x;
     const int nxs = min(kXS, W - x0);
@@ -334,6 +336,16 @@ __device__ __forceinline__ void cost_tile(const int16_t* __restrict__ gplane, co
                 const int px = stage_pos(x);
                 for (int dd = lane; dd < ndw; dd += 32) o[dd] = to_out<T>(dd < nd ? stage[dd * kStage + px] : 0.f);
             }
+            if (out_r != nullptr) {
+                // right pixel xr = x - d receives the contiguous disparities
+                // max(dc, x0 - xr) .. min(dc + nd - 1, x0 + nxs - 1 - xr) of this pass
+                const int xr_lo = max(0, x0 - dc - nd + 1), xr_hi = x0 + nxs - 1 - dc;
+                for (int xr = xr_lo + warp; xr <= xr_hi; xr += kThreads / 32) {
+                    const int dlo = max(dc, x0 - xr), dhi = min(dc + nd - 1, x0 + nxs - 1 - xr);
+                    float* o = out_r + ((size_t)y * W + xr) * ld;
+                    for (int d = dlo + lane; d <= dhi; d += 32) o[d] = stage[(d - dc) * kStage + stage_pos(xr + d - x0)];
+                }
+            }
         }
         __syncthreads();
     }
@@ -413,6 +425,33 @@ cost_band_kernel(const int16_t* __restrict__ gplane, const int* __restrict__ spl
     if (d_begin >= d_end) return;
     cost_tile<0, float, false>(gplane, splane, rvplane, nullptr, nullptr, H, W, 1, D, ld, 0.f, out, x0, y, smem_i,
                                d_begin, d_end);
+}
+
+// Both views at once (FP32 layouts): the left volume as cost_kernel writes it
+// and the right volume from the same staged costs.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads)
+cost_lr_kernel(const int16_t* __restrict__ gplane, const int* __restrict__ splane, const float* __restrict__ rvplane,
+               const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int H, int W, int C, int D, int ld,
+               float tau, float* __restrict__ out, float* __restrict__ out_r)
+{
+    extern __shared__ int smem_i[];
+    cost_tile<MODE, float, false>(gplane, splane, rvplane, L, R, H, W, C, D, ld, tau, out, blockIdx.x * kXS, blockIdx.y,
+                                  smem_i, 0, D, out_r);
+}
+
+// Right volume entries with no left pixel (xr + d >= W): the maximum cost;
+// d in [D, ld) padding: 0.
+__global__ void right_edge_fill_kernel(int H, int W, int D, int ld, float maxc, float* __restrict__ out_r)
+{
+    const int y = blockIdx.x;
+    const int x_first = max(0, W - D);
+    const int n = (W - x_first) * ld;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int xr = x_first + i / ld, d = i % ld;
+        if (d >= D) out_r[((size_t)y * W + xr) * ld + d] = 0.f;
+        else if (xr + d >= W) out_r[((size_t)y * W + xr) * ld + d] = maxc;
+    }
 }
 
 size_t cost_smem_bytes()
@@ -531,6 +570,32 @@ cudaError_t launch_cost_band(const CostScratch& sc, const uint8_t* left, const u
     dim3 grid((W + kXS - 1) / kXS, H);
     cost_band_kernel<<<grid, kThreads, smem, stream>>>(sc.g, sc.s, sc.rv, H, W, D, ld, radius, tile_range, ntx, nty,
                                                        cost);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cost_build_lr(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H, int W,
+                                 int C, int D, int ld, int mode, float tau, float* cost, float* cost_r,
+                                 cudaStream_t stream)
+{
+    cudaError_t e = cudaSuccess;
+    if (mode == 0) e = launch_stats(sc, left, right, H, W, C, stream);
+    if (e != cudaSuccess) return e;
+    const size_t smem = cost_smem_bytes();
+    dim3 grid((W + kXS - 1) / kXS, H);
+    if (mode == 0) {
+        e = cudaFuncSetAttribute(cost_lr_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            cost_lr_kernel<0><<<grid, kThreads, smem, stream>>>(sc.g, sc.s, sc.rv, left, right, H, W, C, D, ld, tau,
+                                                                cost, cost_r);
+    } else {
+        e = cudaFuncSetAttribute(cost_lr_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            cost_lr_kernel<1><<<grid, kThreads, smem, stream>>>(sc.g, sc.s, sc.rv, left, right, H, W, C, D, ld, tau,
+                                                                cost, cost_r);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    right_edge_fill_kernel<<<H, 256, 0, stream>>>(H, W, D, ld, mode == 0 ? 2.f : tau, cost_r);
     return cudaGetLastError();
 }
 

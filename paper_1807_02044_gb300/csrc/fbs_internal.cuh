@@ -32,6 +32,13 @@ __host__ __device__ inline int rgbx_pitch(int W) { return (W + 1) & ~1; }
 cudaError_t launch_cost_build(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H, int W,
                               int C, int D, int ld, int mode, float tau, float* cost, cudaStream_t stream);
 
+// Both views (Sec. II-A, Sec. III): cost as launch_cost_build, and cost_r
+// [H][W][ld] the right volume, cost_r(x, y, d) = cost(x + d, y, d), the maximum
+// cost where x + d >= W.
+cudaError_t launch_cost_build_lr(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H, int W,
+                                 int C, int D, int ld, int mode, float tau, float* cost, float* cost_r,
+                                 cudaStream_t stream);
+
 // 16-bit x-blocked volume cost[((y*ceil(W/8) + x/8)*Dp + d)*8 + x%8] with
 // Dp = tc_block_rows(D) rows per block: d < D the cost, D <= d < round_up(D,16)
 // zero, and (when Dp > round_up(D,16)) row round_up(D,16) all ones followed by
