@@ -75,6 +75,9 @@ def _args():
     ap.add_argument("--band", action="store_true",
                     help="time the learned band form on the 1920x1080 RGB pair, D=256, radius 9 (network proposal "
                          "plus band-restricted path) against the plain full-range forms on the same pair")
+    ap.add_argument("--sweep", action="store_true",
+                    help="bad-pixel rate (e_PEP, Eq. (11)-(12), eps 2) per region against the scenes' ground truth "
+                         "and runtime, over radius, gamma_d and gamma_r (640x480, D=64)")
     ap.add_argument("--lr", action="store_true",
                     help="time both views and the left-right consistency check (FP32) on the default workload")
     ap.add_argument("--band-shape", default=None,
@@ -775,6 +778,80 @@ def run_lr(args):
     return 0
 
 
+def _regions(p):
+    """Evaluation regions of a synthetic pair: unoccluded pixels; unoccluded and
+    textured (grey standard deviation over a 9x9 window >= 4 levels); unoccluded
+    and away from depth discontinuities (ground-truth jump > 1 between
+    4-neighbours, dilated by a 7x7 window)."""
+    import numpy as np
+    from scipy import ndimage
+    grey = p.left.astype(np.float64).mean(axis=2)
+    m1 = ndimage.uniform_filter(grey, 9)
+    m2 = ndimage.uniform_filter(grey * grey, 9)
+    textured = np.sqrt(np.maximum(m2 - m1 * m1, 0.0)) >= 4.0
+    jump = np.zeros(p.gt.shape, bool)
+    jump[:, 1:] |= np.abs(np.diff(p.gt, axis=1)) > 1.0
+    jump[:, :-1] |= np.abs(np.diff(p.gt, axis=1)) > 1.0
+    jump[1:, :] |= np.abs(np.diff(p.gt, axis=0)) > 1.0
+    jump[:-1, :] |= np.abs(np.diff(p.gt, axis=0)) > 1.0
+    discont = ndimage.maximum_filter(jump, size=7)
+    vis = ~p.occ
+    return {"non_occ": vis, "non_occ_textl": vis & textured, "non_occ_discont": vis & ~discont}
+
+
+def run_sweep(args):
+    """Accuracy against ground truth and runtime over the aggregation
+    parameters: radius (sigma_s = radius), gamma_d at radius 7, gamma_r at
+    radius 7 -- the synthetic counterparts of the paper's parameter studies.
+    e_PEP = % of pixels of a region whose |d - gt| > 2 (Eq. (11)-(12))."""
+    import numpy as np
+    import torch
+
+    import paper_1807_02044_gb300 as fbs
+    from synth import make_pair
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    seeds = [args.seed, args.seed + 1, args.seed + 2]
+    pairs = [make_pair("rgb640x480_d64_r7", s) for s in seeds]
+    regions = [_regions(p) for p in pairs]
+    devs = [(torch.from_numpy(p.left).to(dev), torch.from_numpy(p.right).to(dev)) for p in pairs]
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ctxs = {"f32": fbs.Context(0), "bf16": fbs.Context(0, prec=fbs.FBS_PREC_BF16)}
+
+    def point(radius, gd, gr):
+        row = {"radius": radius, "gamma_d": gd, "gamma_r": gr}
+        for form, ctx in ctxs.items():
+            if form == "bf16" and radius > 24:
+                continue
+            peps = {k: [] for k in regions[0]}
+            for p, reg, (dl, dr) in zip(pairs, regions, devs):
+                di, ds = ctx.compute_disparity(dl, dr, p.D, radius, gd, gr, stream=stream)
+                torch.cuda.synchronize()
+                err = np.abs(ds.cpu().numpy() - p.gt) > 2.0
+                for k, m in reg.items():
+                    peps[k].append(100.0 * float(err[m].mean()))
+            p, (dl, dr) = pairs[0], devs[0]
+            di = torch.empty((p.H, p.W), dtype=torch.int32, device=dev)
+            ds = torch.empty((p.H, p.W), device=dev)
+            t = _time_call(fbs, torch, ctx, lambda: fbs.fbs_compute_disparity(
+                ctx.ctx, dl, dr, p.H, p.W, p.C, p.D, radius, gd, gr, p.tau, di, ds, stream), stream, flush, 20, 3)
+            row[form] = {"e_pep_pct": {k: round(float(np.mean(v)), 3) for k, v in peps.items()},
+                         "ms_per_frame": round(t["step_ms"], 4),
+                         "mde_per_s": round(p.W * p.H * p.D / (t["step_ms"] * 1e-3) * 1e-6, 1)}
+        return row
+
+    out = {"sweep": "e_PEP (eps 2) per region and runtime, 640x480 RGB, D=64, scenes " + str(seeds),
+           "radius": [point(r, float(r), 12.0) for r in (1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 15)],
+           "gamma_d": [point(7, gd, 12.0) for gd in (1.0, 2.0, 3.0, 5.0, 7.0, 10.0, 15.0, 25.0)],
+           "gamma_r": [point(7, 7.0, gr) for gr in (2.0, 4.0, 8.0, 12.0, 16.0, 24.0, 32.0, 64.0)]}
+    print(json.dumps(out))
+    for c in ctxs.values():
+        c.close()
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -785,6 +862,8 @@ def main():
         return run_band(args)
     if args.lr:
         return run_lr(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_ours(args)
 
 
