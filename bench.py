@@ -639,6 +639,25 @@ def run_band(args):
     torch.cuda.synchronize()
     work = float(((hi - lo + 1).double().sum() / (H * W * D)).item())
     fallback = float((conf < thr).float().mean().item())
+    # the non-learned band source (feature points, Sec. V) at a few margin thresholds
+    fp_rows = []
+    fc = torch.empty((H, W), device=dev)
+    fk = torch.empty((H, W), device=dev)
+    fi = torch.empty((H, W), dtype=torch.int32, device=dev)
+    fs = torch.empty((H, W), device=dev)
+    farr = fbs.make_pairs([dict(left=dl, right=dr, H=H, W=W, C=3, D=D, radius=p.radius, sigma_s=p.sigma_s,
+                                sigma_r=p.sigma_r, tau=p.tau, disp_int=fi, disp_subpix=fs)])
+    for th_m in (0.02, 0.05, 0.1, 0.2):
+        def fp_step():
+            fbs.fbs_band_feature_points(ctx.ctx, dl, dr, H, W, 3, D, th_m, fc, fk, stream)
+            fbs.fbs_compute_disparity_banded(ctx.ctx, farr, fc, fk, HALF_BAND, 0.5, stream)
+        t = _time_call(fbs, torch, ctx, fp_step, stream, flush, max(3, steps // 10), 3)
+        fbs.fbs_band_limits(ctx.ctx, fc, fk, H * W, D, HALF_BAND, 0.5, lo, hi, stream)
+        torch.cuda.synchronize()
+        fp_rows.append({"margin_threshold": th_m, "ms_per_step": t["step_ms"], "fps": 1e3 / t["step_ms"],
+                        "fallback_pct": 100.0 * float((fk < 0.5).float().mean().item()),
+                        "work_fraction": float(((hi - lo + 1).double().sum() / (H * W * D)).item()),
+                        "bad_px_vs_f32_pct": 100.0 * float(((fs - outs["f32"][1]).abs() > 1.0).float().mean().item())})
     ds_f32 = outs["f32"][1].cpu().numpy()
     res = {}
     for k in ("band", "bf16"):
@@ -723,6 +742,7 @@ def run_band(args):
            "bad_px_vs_oracle_pct_sampled": vs_oracle, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": sum(n for _, n in kt.values()), "clocks": clocks}
     out["forms"]["bf16"]["bad_px_vs_f32_pct"] = res["bf16"]
+    out["feature_point_band"] = fp_rows
     print(json.dumps(out))
     ctx.close()
     return 0

@@ -105,6 +105,20 @@ fbs_status fbs_band_net_train_step(fbs_ctx *ctx, const uint8_t *left, const uint
                                    float *loss, float *grad, void *cuda_stream);
 
 /*
+ * The non-learned band source the paper names as future work (Sec. V):
+ * reliable feature points suggest the search range of their neighbours.  A
+ * quarter pixel is a feature point when its coarse cost margin (feature f3 of
+ * step 1) is >= margin_threshold; a pixel whose 5x5 quarter neighbourhood
+ * (clipped) holds at least 3 feature points with coarse winners e* spread by
+ * at most 2 gets centre 2 (max e* + min e*) (4x the mid-range) and confidence
+ * 1, every other pixel confidence 0.  centre, conf: [H][W] float32 (device),
+ * to be passed to fbs_compute_disparity_banded with a threshold in (0, 1].
+ */
+fbs_status fbs_band_feature_points(fbs_ctx *ctx, const uint8_t *left, const uint8_t *right,
+                                   int H, int W, int C, int D, float margin_threshold,
+                                   float *centre, float *conf, void *cuda_stream);
+
+/*
  * Step 3's band rule on given centre / confidence planes (n elements, device):
  * writes lo[n], hi[n] (device int32).  1 <= half_band <= 512.
  */

@@ -73,6 +73,8 @@ def _load():
             lib.oracle_fbs_band_points.argtypes = [P, P, I, I, I, I, I, Dd, Dd, I, P, P, P, P, P, P, P]
             lib.oracle_fbs_band_points.restype = I
             lib.oracle_band_targets.argtypes = [P, P, I, I, I, I, P, P, P]
+            lib.oracle_band_feature_points.argtypes = [P, P, I, I, I, I, ctypes.c_float, P, P]
+            lib.oracle_band_feature_points.restype = I
             _lib = lib
     return _lib
 
@@ -272,6 +274,17 @@ def band_targets(label_int, label_sub, D, half_band, centre_q):
     y = np.empty((Hq, Wq), np.float64)
     _load().oracle_band_targets(_ptr(li), _ptr(ls), H, W, D, int(half_band), _ptr(cq), _ptr(t), _ptr(y))
     return t, y
+
+
+def band_feature_points(left, right, D, theta_m):
+    """B7: feature-point centre and confidence (float32, H x W)."""
+    L, R = _img(left), _img(right)
+    H, W, C = L.shape
+    c = np.empty((H, W), np.float32)
+    k = np.empty((H, W), np.float32)
+    if _load().oracle_band_feature_points(_ptr(L), _ptr(R), H, W, C, D, float(theta_m), _ptr(c), _ptr(k)) != 0:
+        raise MemoryError("oracle_band_feature_points could not allocate")
+    return c, k
 
 
 def e_pep(estimate, truth, eps, mask=None):

@@ -52,6 +52,14 @@
  *       the smallest d of the band with the least Agg; Eq. (10) is applied
  *       only when both neighbours d* - 1 and d* + 1 lie in the band (the band
  *       ends play the role of 0 and D - 1).
+ *   B7  feature-point proposal (the paper's future work, Sec. V: reliable
+ *       feature points suggest the search range of their neighbours): a
+ *       quarter pixel is a feature point when its margin f3 >= theta_m (FP32);
+ *       a full-resolution pixel in quarter pixel i takes the feature points of
+ *       the 5x5 quarter window around i (clipped); with at least 3 of them and
+ *       max e* - min e* <= 2 its centre is 2 (max e* + min e*) (= 4 x the
+ *       mid-range, exact in FP32) and its confidence 1, otherwise confidence 0
+ *       (full range).
  *   B6  targets of quarter pixel i from plain full-range FBS (integer d*,
  *       subpixel ds) over the in-image pixels of its 4x4 block: centre target
  *       t = median of ds (for an even count the mean of the two middle
@@ -289,4 +297,46 @@ void oracle_band_targets(const int32_t *label_int, const float *label_sub, int H
             y[i] = (double)in / cnt;
         }
     }
+}
+
+/* B7: feature-point centre and confidence [H][W] (FP32) of a pair. */
+int oracle_band_feature_points(const uint8_t *L, const uint8_t *R, int H, int W, int C, int D, float theta_m,
+                               float *centre, float *conf)
+{
+    const int Hq = (H + 3) / 4, Wq = (W + 3) / 4;
+    float *feat = (float *)malloc(sizeof(float) * (size_t)Hq * Wq * 6);
+    int32_t *est = (int32_t *)malloc(sizeof(int32_t) * (size_t)Hq * Wq);
+    if (!feat || !est || oracle_band_features(L, R, H, W, C, D, feat, est) != 0) {
+        free(feat);
+        free(est);
+        return -1;
+    }
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            const int Y = y / 4, X = x / 4;
+            int n = 0, emin = 1 << 30, emax = -1;
+            for (int j = Y - 2; j <= Y + 2; ++j) {
+                if (j < 0 || j >= Hq) continue;
+                for (int i = X - 2; i <= X + 2; ++i) {
+                    if (i < 0 || i >= Wq) continue;
+                    const size_t q = (size_t)j * Wq + i;
+                    if (!(feat[q * 6 + 3] >= theta_m)) continue;
+                    ++n;
+                    if (est[q] < emin) emin = est[q];
+                    if (est[q] > emax) emax = est[q];
+                }
+            }
+            const size_t p = (size_t)y * W + x;
+            if (n >= 3 && emax - emin <= 2) {
+                centre[p] = 2.0f * (float)(emax + emin);
+                conf[p] = 1.0f;
+            } else {
+                centre[p] = 0.0f;
+                conf[p] = 0.0f;
+            }
+        }
+    }
+    free(feat);
+    free(est);
+    return 0;
 }

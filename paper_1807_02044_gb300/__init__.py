@@ -93,6 +93,7 @@ SIGNATURES = {
     "fbs_band_net_forward": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P, _P, _P]),
     "fbs_band_net_train_step": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P, _I, _F, _P, _P, _P]),
     "fbs_band_limits": (_I, [_P, _P, _P, _I, _I, _I, _F, _P, _P, _P]),
+    "fbs_band_feature_points": (_I, [_P, _P, _P, _I, _I, _I, _I, _F, _P, _P, _P]),
     "fbs_compute_disparity_banded": (_I, [_P, _P, _P, _P, _I, _F, _P]),
     "fbs_compute_disparity_learned": (_I, [_P, _P, _I, _F, _P]),
 }
@@ -335,6 +336,11 @@ def fbs_band_net_train_step(ctx, left, right, H, W, C, D, label_int, label_sub, 
     _check(ctx, lib().fbs_band_net_train_step(ctx, _addr(left), _addr(right), H, W, C, D, _addr(label_int),
                                              _addr(label_sub), half_band, lr, _addr(loss), _addr(grad),
                                              _stream(stream)))
+
+
+def fbs_band_feature_points(ctx, left, right, H, W, C, D, margin_threshold, centre, conf, stream=None):
+    _check(ctx, lib().fbs_band_feature_points(ctx, _addr(left), _addr(right), H, W, C, D, margin_threshold,
+                                             _addr(centre), _addr(conf), _stream(stream)))
 
 
 def fbs_band_limits(ctx, centre, conf, n, D, half_band, conf_threshold, lo, hi, stream=None):

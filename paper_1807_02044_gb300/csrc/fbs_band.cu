@@ -205,6 +205,33 @@ band_features_kernel(const int32_t* __restrict__ gq, const float* __restrict__ K
     }
 }
 
+// ---- feature-point proposal (reading B7) -------------------------------------------
+// Reliable feature points (margin f3 >= theta_m) of the 5x5 quarter window
+// around a pixel's quarter pixel suggest its band: with at least 3 of them and
+// a winner spread <= 2 the centre is 2 (max + min) and the confidence 1.
+__global__ void band_feature_points_kernel(const float* __restrict__ feat, const int32_t* __restrict__ estar,
+                                           int H, int W, float theta_m, float* __restrict__ centre,
+                                           float* __restrict__ conf)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W) return;
+    const int Hq = (H + 3) / 4, Wq = (W + 3) / 4;
+    const int Y = y >> 2, X = x >> 2;
+    int n = 0, emin = 1 << 30, emax = -1;
+    for (int j = max(0, Y - 2); j <= min(Hq - 1, Y + 2); ++j)
+        for (int i = max(0, X - 2); i <= min(Wq - 1, X + 2); ++i) {
+            const size_t q = (size_t)j * Wq + i;
+            if (!(feat[q * 6 + 3] >= theta_m)) continue;
+            ++n;
+            emin = min(emin, estar[q]);
+            emax = max(emax, estar[q]);
+        }
+    const size_t p = (size_t)y * W + x;
+    const bool ok = n >= 3 && emax - emin <= 2;
+    centre[p] = ok ? 2.f * (float)(emax + emin) : 0.f;
+    conf[p] = ok ? 1.f : 0.f;
+}
+
 // ---- band rule (reading B4) and the per-tile ranges -----------------------------
 __device__ __forceinline__ uint32_t band_of(float c, float k, int D, int h, float theta)
 {
@@ -302,6 +329,7 @@ struct NetScratch {
     float* kq;                   // coarse costs [P][Dq], then their 5x5 means
     float* kh;                   // row sums [P][Dq]
     int32_t* estar;              // [P]
+    float* featf;                // [P][6] FP32 features (feature-point proposal)
     __nv_bfloat16* x0;           // [P][8]
     __nv_bfloat16* y[5];         // [P][32]
     float* out;                  // [P][2]
@@ -317,7 +345,7 @@ struct NetScratch {
 size_t net_scratch_bytes(int H, int W, int D, bool training, bool full_res)
 {
     const size_t Hq = (H + 3) / 4, Wq = (W + 3) / 4, P = Hq * Wq, Dq = (D + 3) / 4;
-    size_t n = al256(2 * P * 4) + 2 * al256(P * Dq * 4) + al256(P * 4) + al256(P * 16) + 5 * al256(P * 64) + al256(P * 8);
+    size_t n = al256(2 * P * 4) + 2 * al256(P * Dq * 4) + al256(P * 4) + al256(P * 24) + al256(P * 16) + 5 * al256(P * 64) + al256(P * 8);
     if (training)
         n += 5 * al256(P * 64) + al256(P * 16) + al256(wgrad_partial_floats((int)Hq, (int)Wq) * 4) +
              al256((size_t)loss_blocks((int)P) * 4);
@@ -343,6 +371,7 @@ NetScratch carve_net(void* base, int H, int W, int D, bool training, bool full_r
     s.kq = (float*)take(P * Dq * 4);
     s.kh = (float*)take(P * Dq * 4);
     s.estar = (int32_t*)take(P * 4);
+    s.featf = (float*)take(P * 24);
     s.x0 = (__nv_bfloat16*)take(P * 16);
     for (int l = 0; l < 5; ++l) s.y[l] = (__nv_bfloat16*)take(P * 64);
     s.out = (float*)take(P * 8);
@@ -741,6 +770,27 @@ fbs_status fbs_band_net_train_step(fbs_ctx* ctx, const uint8_t* left, const uint
     }
     if (e == cudaSuccess && (grad || loss)) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? FBS_OK : cuda_fail(ctx, e, "band training step");
+}
+
+fbs_status fbs_band_feature_points(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C,
+                                  int D, float margin_threshold, float* centre, float* conf, void* cuda_stream)
+{
+    if (!ctx) return FBS_ERR_INVALID_ARG;
+    fbs_status s = check_pair_shape(ctx, left, right, H, W, C, D);
+    if (s != FBS_OK) return s;
+    if (!centre || !conf) return fail(ctx, FBS_ERR_INVALID_ARG, "null centre or confidence");
+    if (std::isnan(margin_threshold)) return fail(ctx, FBS_ERR_INVALID_ARG, "margin_threshold is NaN");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = pick_stream(ctx, cuda_stream);
+    s = ensure(ctx, &ctx->band_ws, &ctx->band_ws_bytes, net_scratch_bytes(H, W, D, false, false), "band scratch");
+    if (s != FBS_OK) return s;
+    const NetScratch sc = carve_net(ctx->band_ws, H, W, D, false, false);
+    if ((s = run_features(ctx, sc, left, right, H, W, C, D, sc.featf, st)) != FBS_OK) return s;
+    LaunchScope ls(ctx, FBS_KERNEL_NET, st);
+    fbs::band_feature_points_kernel<<<dim3((W + 255) / 256, H), 256, 0, st>>>(sc.featf, sc.estar, H, W,
+                                                                           margin_threshold, centre, conf);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FBS_OK : cuda_fail(ctx, e, "feature-point proposal launch");
 }
 
 fbs_status fbs_band_limits(fbs_ctx* ctx, const float* centre, const float* conf, int n, int D, int half_band,

@@ -351,3 +351,17 @@ def test_band_argument_validation(fbs):
             fbs.fbs_compute_disparity_learned(ctx.ctx, pair, 8, 0.5)
         with pytest.raises(fbs.FBSError):
             fbs.fbs_band_net_set_params(ctx.ctx, np.zeros(5, np.float32))
+
+
+@pytest.mark.parametrize("H,W,D,shift,th", [(37, 45, 40, 9, 0.05), (64, 200, 128, 24, 0.1), (23, 61, 16, 3, 0.0)])
+def test_feature_points_bit_exact(fbs, oracle_mod, H, W, D, shift, th):
+    L, R = _rand_pair(H + W + shift, H, W, 3, shift=shift)
+    c = torch.empty((H, W), device="cuda")
+    k = torch.empty((H, W), device="cuda")
+    with fbs.Context(0) as ctx:
+        fbs.fbs_band_feature_points(ctx.ctx, _dev(L), _dev(R), H, W, 3, D, th, c, k)
+        torch.cuda.synchronize()
+        fbs.fbs_sync(ctx.ctx)
+    rc, rk = oracle_mod.band_feature_points(L, R, D, th)
+    assert np.array_equal(k.cpu().numpy(), rk)
+    assert np.array_equal(c.cpu().numpy(), rc)

@@ -90,3 +90,34 @@ def test_trained_network_beats_the_coarse_band_at_equal_work(fbs, oracle_mod, se
     assert bad_learned <= 0.005
     assert work <= 0.5
     assert bad_learned < bad_coarse
+
+
+def test_trained_network_beats_the_feature_point_proposal(fbs):
+    """Against the paper's own future-work proposal (reliable feature points
+    suggest their neighbours' range; fbs_band_feature_points, margin 0.2), at a
+    similar fallback share (network threshold 0.9), the network's band leaves
+    fewer extra bad pixels."""
+    from synth import make_pair
+    p = make_pair(WORKLOAD, 13)
+    H, W, D = p.H, p.W, p.D
+    with fbs.Context(0) as ctx:
+        fbs.fbs_band_net_load(ctx.ctx, fbs.default_band_net_path())
+        dl = torch.from_numpy(p.left).cuda()
+        dr = torch.from_numpy(p.right).cuda()
+        _, plain = ctx.compute_disparity(dl, dr, D, p.radius, p.sigma_s, p.sigma_r)
+        c = torch.empty((H, W), device="cuda")
+        k = torch.empty((H, W), device="cuda")
+        fbs.fbs_band_net_forward(ctx.ctx, dl, dr, H, W, 3, D, None, c, k)
+        learned = _banded(fbs, ctx, dl, dr, p, c, k, 0.9)
+        fb_learned = float((k < 0.9).float().mean().item())
+        fbs.fbs_band_feature_points(ctx.ctx, dl, dr, H, W, 3, D, 0.2, c, k)
+        fpts = _banded(fbs, ctx, dl, dr, p, c, k, 0.5)
+        fb_fp = float((k < 0.5).float().mean().item())
+        torch.cuda.synchronize()
+        fbs.fbs_sync(ctx.ctx)
+    bad_l = float(((learned - plain).abs() > 1.0).float().mean().item())
+    bad_f = float(((fpts - plain).abs() > 1.0).float().mean().item())
+    print(f"learned (0.9): fallback {100 * fb_learned:.2f}% extra bad {100 * bad_l:.3f}%; "
+          f"feature points (0.2): fallback {100 * fb_fp:.2f}% extra bad {100 * bad_f:.3f}%")
+    assert abs(fb_learned - fb_fp) < 0.05
+    assert bad_l < bad_f

@@ -264,3 +264,34 @@ def test_bf16_mode_changes_only_operands():
     assert np.array_equal(O1, O2)
     dO = rng.integers(-2, 3, O1.shape).astype(np.float64)
     assert np.array_equal(bn.backward(theta, a1, dO), bn.backward(theta, a2, dO, bf16=True))
+
+
+def test_feature_point_proposal_definition(oracle_mod):
+    """B7 restated with numpy from the pinned features: the 5x5 quarter window
+    of feature points (margin >= theta), their count and winner spread."""
+    rng = np.random.default_rng(12)
+    H, W, D, th = 30, 45, 32, 0.05
+    L = rng.integers(0, 256, size=(H, W, 3)).astype(np.uint8)
+    R = np.roll(L, -8, axis=1)
+    feat, est = oracle_mod.band_features(L, R, D)
+    c, k = oracle_mod.band_feature_points(L, R, D, th)
+    Hq, Wq = est.shape
+    fp = feat[..., 3] >= np.float32(th)
+    for y in range(H):
+        for x in range(W):
+            Y, X = y // 4, x // 4
+            sel = fp[max(0, Y - 2):Y + 3, max(0, X - 2):X + 3]
+            e = est[max(0, Y - 2):Y + 3, max(0, X - 2):X + 3][sel]
+            if e.size >= 3 and e.max() - e.min() <= 2:
+                assert k[y, x] == 1.0 and c[y, x] == 2.0 * (e.max() + e.min())
+            else:
+                assert k[y, x] == 0.0
+
+
+def test_feature_points_on_a_shift_by_four_k(oracle_mod):
+    """Shift by 4k: away from the borders every pixel is confident with centre 4k."""
+    H, W, D, k = 64, 128, 64, 6
+    L, R = shifted_texture_pair(H, W, 3, 4 * k, seed=2)
+    c, conf = oracle_mod.band_feature_points(L, R, D, 0.05)
+    inner = (slice(20, -20), slice(4 * k + 24, -20))
+    assert np.all(conf[inner] == 1.0) and np.all(c[inner] == 4.0 * k)
