@@ -248,6 +248,29 @@ def _traffic_for(kernel_file, kernel_name):
 FORM_PREC = {"f32": 0, "bf16": 1, "f16": 2}
 
 
+def replica_env():
+    """(world, rank, local rank) of a torchrun launch (1, 0, 0 otherwise).  The
+    path does not shard: every rank runs an independent replica on its own
+    pair (scene seed + rank), and only the step time is reduced."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value, dist, device):
+    """The largest per-rank value (the job's step time is its slowest rank's)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, slowest_seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / slowest_seconds
+
+
 def _time_form(fbs, torch, p, form, mode, dev, stream, dl, dr, flush, steps, warmup, dist):
     """Warm up, then time exactly `steps` steps of one form; per-step CUDA events
     on the launch stream, the L2 flush outside them."""
@@ -277,11 +300,7 @@ def _time_form(fbs, torch, p, form, mode, dev, stream, dl, dr, flush, steps, war
         t1 = time.time()
         fbs.fbs_profile(ctx.ctx, 0)
     fbs.fbs_sync(ctx.ctx)
-    step_ms = sum(a.elapsed_time(b) for a, b in evs) / steps
-    if dist:
-        t = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / steps, dist, dev)
     kt = {fbs.KERNEL_NAMES[k]: fbs.fbs_profile_read(ctx.ctx, k) for k in range(fbs.FBS_KERNEL_KINDS)}
     return dict(ctx=ctx, di=di, ds=ds, step_ms=step_ms, kt=kt, t0=t0, t1=t1)
 
@@ -293,9 +312,7 @@ def run_ours(args):
     import paper_1807_02044_gb300 as fbs
     from synth import make_pair
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = replica_env()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -353,7 +370,7 @@ def run_ours(args):
                 form_out["f32"]["bad_px_vs_oracle_pct_sampled"]
 
     step_ms = chosen["step_ms"]
-    value = world * taps / (step_ms * 1e-3) / 1e9
+    value = job_rate(taps, world, step_ms * 1e-3) / 1e9
     kt = chosen["kt"]
     launches = sum(n for _, n in kt.values())
     clocks = sampler.summary(chosen["t0"], chosen["t1"]) if sampler is not None else None
@@ -423,13 +440,9 @@ def run_ours(args):
             t = time.perf_counter()
             host_call()
             tot += time.perf_counter() - t
-        e2e_s = tot / n_e2e
-        if dist:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(tot / n_e2e, dist, dev)
         assert np.array_equal(hi.numpy(), chosen["di"].cpu().numpy())
-        e2e = {"value": world * taps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * p.H * p.W * p.C,
+        e2e = {"value": job_rate(taps, world, e2e_s) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * p.H * p.W * p.C,
                "d2h_bytes_per_step": 8 * p.H * p.W, "steps": n_e2e,
                "call": "fbs_compute_disparity_host (pinned host buffers, copies and sync inside the timed call)"}
 
