@@ -184,6 +184,47 @@ def cpu_baseline(p, seconds, mode):
                       f"single-threaded FP64 C oracle, {t:.1f} s"}
 
 
+_POOL_PAIR = None
+
+
+def _oracle_pool_init(name, seed):
+    global _POOL_PAIR
+    import oracle
+    from synth import make_pair
+    oracle.build()
+    _POOL_PAIR = make_pair(name, seed)
+
+
+def _oracle_rows_job(job):
+    import oracle
+    y0, rows, mode = job
+    p = _POOL_PAIR
+    oracle.fbs(p.left, p.right, p.D, p.radius, p.sigma_s, p.sigma_r, p.tau, mode=mode, rows=(y0, y0 + rows))
+    return rows
+
+
+def cpu_baseline_all_cores(name, seed, p, seconds, mode):
+    """The same oracle on every host core: row bands of the frame spread over a
+    spawned process pool (one band per core, the pool's wall time measured)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    probe = min(4, p.H)
+    t1 = _oracle_band(p, max(0, p.H // 2 - 2), probe, mode) / probe      # seconds per row on one core
+    rows = int(max(1, min(p.H // cores, seconds / max(t1, 1e-6))))
+    jobs = [(min(p.H - rows, i * rows), rows, mode) for i in range(cores)]
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"),
+                                initializer=_oracle_pool_init, initargs=(name, seed)) as ex:
+        list(ex.map(_oracle_rows_job, [(0, 1, mode)] * cores))   # every worker has rendered the pair
+        t = time.perf_counter()
+        list(ex.map(_oracle_rows_job, jobs))
+        wall = time.perf_counter() - t
+    taps = cores * rows * p.W * p.D * (2 * p.radius + 1) ** 2
+    return {"value": taps / wall / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} row bands of {rows} rows of the {p.W}x{p.H} frame, one per core "
+                      f"(spawned process pool), single-threaded FP64 C oracle in each, {wall:.1f} s wall"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -446,9 +487,10 @@ def run_ours(args):
                "d2h_bytes_per_step": 8 * p.H * p.W, "steps": n_e2e,
                "call": "fbs_compute_disparity_host (pinned host buffers, copies and sync inside the timed call)"}
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(p, args.cpu_seconds, mode)
+        cpu_all = cpu_baseline_all_cores(args.workload, args.seed, p, args.cpu_seconds, mode)
 
     cfg = _config(p, args, "ours")
     cfg["forms_timed"] = forms
@@ -457,7 +499,8 @@ def run_ours(args):
            "dtype": args.prec, "data": "synthetic", "config": cfg,
            "fps": world * 1e3 / step_ms, "mde_per_s": world * p.W * p.H * p.D / (step_ms * 1e-3) * 1e-6,
            "form": args.prec, "forms": form_out,
-           "roofline": roofline, "roofline_cost_build": roofline_cost, "cpu_baseline": cpu, "e2e": e2e,
+           "roofline": roofline, "roofline_cost_build": roofline_cost, "cpu_baseline": cpu,
+           "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
            "gpu_launches": launches, "kernel_ms_per_step": {k: v[0] / steps for k, v in kt.items() if v[1]},
            "clocks": clocks, "wall_s_timed_region": chosen["t1"] - chosen["t0"]}
     if rank == 0:
