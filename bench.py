@@ -521,8 +521,9 @@ def _render_batch_member(spec):
 
 def run_batched(args):
     """One step = one batch of uneven pairs through fbs_compute_disparity_batched
-    (FP32, one CUDA graph of three persistent launches).  Beside it: the same
-    pairs as sequential per-pair calls, FP32 and BF16 tensor-core form."""
+    (FP32, one CUDA graph; the autotuner's plan).  Beside it: the same
+    pairs as sequential per-pair calls, FP32 and BF16 tensor-core form, and
+    the BF16 batched form (one graph of every pair's tensor-core launches)."""
     import concurrent.futures as cf
     import multiprocessing as mp
 
@@ -591,17 +592,31 @@ def run_batched(args):
                                           q["sigma_s"], q["sigma_r"], q["tau"], q["disp_int"], q["disp_subpix"],
                                           stream)
         t_seq16, _ = timed(seq16, ctx16)
+        torch.cuda.synchronize()
+        ref16 = [(q["disp_int"].clone(), q["disp_subpix"].clone()) for q in pairs]
+        t_b16, launches16 = timed(lambda: fbs.fbs_compute_disparity_batched(ctx16.ctx, arr, stream), ctx16)
+        plan16 = fbs.fbs_batch_plan(ctx16.ctx, arr)
+        torch.cuda.synchronize()
+        identical16 = all(torch.equal(q["disp_int"], r[0]) and torch.equal(q["disp_subpix"], r[1])
+                          for q, r in zip(pairs, ref16))
     n = len(pairs)
     out = {"metric": METRIC, "value": taps / (t_batch * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": steps,
            "warmup": warmup, "ms_per_step": t_batch, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"batch{n}_uneven_320-1024x240-768_d32-192_r4-11", "pairs": n, "taps": taps,
-                      "seed": args.seed, "plan": plan, "graph": "stats + cost + aggregation, persistent",
+                      "seed": args.seed, "plan": plan,
+                      "graph": ("persistent launches: statistics, cost, aggregation" if plan < 4 else
+                                f"per-pair launches in {[1, 2, 4][plan - 4]} concurrent branches"),
                       "l2": "512 MiB flush write before every step, outside the per-step CUDA-event timing"},
            "pairs_per_s": n / (t_batch * 1e-3), "gpu_launches": launches,
            "batched_equals_sequential_bitwise": identical,
            "sequential_f32": {"ms_per_batch": t_seq, "gtaps_per_s": taps / (t_seq * 1e-3) / 1e9},
            "sequential_bf16": {"ms_per_batch": t_seq16, "gtaps_per_s": taps / (t_seq16 * 1e-3) / 1e9},
+           "batched_bf16": {"ms_per_batch": t_b16, "gtaps_per_s": taps / (t_b16 * 1e-3) / 1e9, "plan": plan16,
+                            "gpu_launches": launches16, "equals_sequential_bf16_bitwise": identical16,
+                            "graph": f"per pair: pad rows, statistics, 16-bit cost, tcgen05 aggregation; "
+                                     f"{[1, 2, 4][plan16 >> 1]} concurrent branches, stage rows "
+                                     f"{'max' if plan16 % 2 == 0 else '<= 3'}"},
            "roofline": None, "cpu_baseline": None, "e2e": None}
     print(json.dumps(out))
     return 0

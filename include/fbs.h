@@ -166,25 +166,43 @@ typedef struct {
 
 /*
  * fbs_compute_disparity for n pairs of uneven size, disparity count and
- * radius (1 <= n <= 4096; pairs is a host array).  Each stage (block
- * statistics, cost volumes, aggregation with WTA and Eq. (10)) is one
- * persistent launch over all pairs, the three replayed as one CUDA graph per
- * batch shape; results are bit-identical to fbs_compute_disparity.  FP32
- * precision only (FBS_ERR_UNSUPPORTED otherwise).  The first call of a new
- * shape (the list of H, W, C, D, radius and the cost mode) runs the
- * library's autotuner: it times each schedule plan on the given data and
- * keeps the fastest (recorded in the options' autotune_cache_path file when
- * set, and read back from it by later contexts).  Scratch: every pair's cost
- * volume at once (sum of H*W*round_up(D,4)*4 bytes plus statistics), owned
- * by ctx.  Asynchronous on cuda_stream; the call returns once the pair table
- * has been staged.
+ * radius (1 <= n <= 4096; pairs is a host array), replayed as one CUDA graph
+ * per batch shape; results are bit-identical to fbs_compute_disparity in the
+ * context's precision.
+ *   FP32: either each stage (block statistics, cost volumes, aggregation
+ *   with WTA and Eq. (10)) is one persistent launch over all pairs, or every
+ *   pair's launches (as in fbs_compute_disparity) run in one graph of 1, 2
+ *   or 4 concurrent branches.  Scratch: every pair's cost volume at once (sum
+ *   of H*W*round_up(D,4)*4 bytes plus statistics).
+ *   BF16 / FP16: every pair's tensor-core launches (as in
+ *   fbs_compute_disparity) in one graph of 1, 2 or 4 concurrent branches.
+ *   Every pair needs D <= 256 and radius <= 24 (FBS_ERR_UNSUPPORTED
+ *   otherwise).  Scratch: every pair's 16-bit volume at once (sum of
+ *   H*ceil(W/8)*8*Dp*2 bytes, Dp = round_up(D,16) (+16 when that stays <= 256),
+ *   plus statistics and the packed guide).
+ *   A branched graph holds the pairs' addresses: a new set of buffers
+ *   captures a new graph (the context keeps up to 32).
+ * The first call of a new shape (the list of H, W, C, D, radius, the cost
+ * mode and, for the tensor cores, the precision) runs the library's
+ * autotuner: it times each schedule plan on the given data and keeps the
+ * fastest (recorded in the options' autotune_cache_path file when set, and
+ * read back from it by later contexts).  Scratch is owned by ctx.
+ * Asynchronous on cuda_stream; the call returns once the work is enqueued.
  */
 fbs_status fbs_compute_disparity_batched(fbs_ctx *ctx, int n, const fbs_pair *pairs, void *cuda_stream);
 
-/* The plan the autotuner chose for this batch shape (0..3), or -1 if none
- * yet.  plan = 2 * order + (aggregation CTAs per SM - 1), order 0 = largest
- * pair first, 1 = as given. */
+/* The plan the autotuner chose for this batch shape, or -1 if none yet.
+ * FP32 (0..6): plans 0..3 persistent, plan = 2 * order + (aggregation CTAs
+ * per SM - 1), order 0 = largest pair first, 1 = as given; plans 4..6
+ * branched with {1, 2, 4}[plan - 4] branches.  BF16 / FP16 (0..5): plan = 2 * b + s,
+ * graph branches {1, 2, 4}[b], window rows per tensor-core pipeline stage
+ * s = 0: the kernel's maximum, s = 1: at most 3. */
 fbs_status fbs_batch_plan(fbs_ctx *ctx, int n, const fbs_pair *pairs, int *plan);
+
+/* Pin the plan of this batch shape in ctx (numbered as above), skipping the
+ * autotuner for it; not written to the autotune cache file.
+ * FBS_ERR_INVALID_ARG for a plan outside the context's precision's range. */
+fbs_status fbs_batch_set_plan(fbs_ctx *ctx, int n, const fbs_pair *pairs, int plan);
 
 /*
  * fbs_compute_disparity_noalloc -- the whole path without allocating device
@@ -233,15 +251,16 @@ fbs_status fbs_compute_disparity_noalloc(fbs_ctx *ctx, const uint8_t *left, cons
  * time of each kernel kind can be read back.  fbs_profile(ctx, 1) clears the
  * counters and starts recording; fbs_profile(ctx, 0) stops.  fbs_profile_read
  * synchronises on the recorded events and returns, for one kind, the summed
- * device milliseconds (0 when profiling was off) and the launch count since
- * the last fbs_profile(ctx, 1).
+ * device milliseconds (0 when profiling was off) and the number of kernels of
+ * that kind launched since the last fbs_profile(ctx, 1) (every kernel counts,
+ * also those a step launches inside one timed scope or a CUDA graph).
  */
 typedef enum {
     FBS_KERNEL_COST = 0,        /* cost-volume build, Eq. (1)-(3) / TAD */
     FBS_KERNEL_AGG_F32 = 1,     /* FP32 aggregation + WTA + Eq. (10) */
     FBS_KERNEL_AGG_TC = 2,      /* tensor-core aggregation + WTA + Eq. (10) */
     FBS_KERNEL_OTHER = 3,       /* every other kernel of the library */
-    FBS_KERNEL_BATCH = 4,       /* one batch graph (timed as a whole; its kernels count as COST and AGG_F32) */
+    FBS_KERNEL_BATCH = 4,       /* one batch graph (timed as a whole; its kernels count under COST, OTHER, AGG_F32 / AGG_TC) */
     FBS_KERNEL_NET = 5,         /* band form: features, network, loss, optimiser, band planning */
     FBS_KERNEL_KINDS = 6
 } fbs_kernel_kind;

@@ -80,6 +80,7 @@ SIGNATURES = {
     "fbs_compute_disparity_noalloc": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _F, _P, _P, _P]),
     "fbs_compute_disparity_batched": (_I, [_P, _I, _P, _P]),
     "fbs_batch_plan": (_I, [_P, _I, _P, ctypes.POINTER(_I)]),
+    "fbs_batch_set_plan": (_I, [_P, _I, _P, _I]),
     "fbs_profile": (_I, [_P, _I]),
     "fbs_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
     # fbs_band.h
@@ -264,6 +265,11 @@ def fbs_batch_plan(ctx, pairs):
     plan = _I()
     _check(ctx, lib().fbs_batch_plan(ctx, len(arr), ctypes.cast(arr, _P), ctypes.byref(plan)))
     return plan.value
+
+
+def fbs_batch_set_plan(ctx, pairs, plan):
+    arr = pairs if isinstance(pairs, ctypes.Array) else make_pairs(pairs)
+    _check(ctx, lib().fbs_batch_set_plan(ctx, len(arr), ctypes.cast(arr, _P), int(plan)))
 
 
 def fbs_profile(ctx, enable):

@@ -420,6 +420,7 @@ cudaError_t launch_kd(const float* cost, int ld, const uint8_t* guide, int H, in
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY);
+    fbs::note_launch();
     aggregate_f32_kernel<KD, VEC><<<grid, kThreads, smem, stream>>>(
         cost, ld, guide, H, W, C, D, rho, neg_ks, neg_kr, agg_out, disp_int, disp_sub);
     return cudaGetLastError();
@@ -439,6 +440,7 @@ cudaError_t prepare_aggregate_f32_batched(int max_radius, size_t* smem_out)
 cudaError_t launch_aggregate_f32_batched(const BatchPair* pairs, int npairs, int nitems, int* counter, int grid,
                                          size_t smem, cudaStream_t stream)
 {
+    fbs::note_launch();
     aggregate_f32_batched_kernel<<<grid, kThreads, smem, stream>>>(pairs, npairs, nitems, counter);
     return cudaGetLastError();
 }
@@ -454,6 +456,7 @@ cudaError_t launch_aggregate_band(const float* cost, int ld, const uint8_t* guid
     cudaError_t e = cudaFuncSetAttribute(aggregate_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY);
+    fbs::note_launch();
     aggregate_band_kernel<<<grid, kThreads, smem, stream>>>(cost, ld, guide, H, W, C, D, radius, neg_ks, neg_kr,
                                                             tile_range, band, disp_int, disp_sub);
     return cudaGetLastError();

@@ -606,6 +606,7 @@ cudaError_t launch_hwd_to_xblock16(const float* in, int H, int W, int D, bool bf
 {
     const size_t n = (size_t)H * ((W + 7) / 8) * D;
     const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    fbs::note_launch();
     if (bf16)
         hwd_to_xblock16_kernel<true><<<blocks, 256, 0, stream>>>(in, H, W, D, (__nv_bfloat16*)out);
     else
@@ -622,13 +623,14 @@ cudaError_t run_tc(const CUtensorMap& map, const CUtensorMap& gmap, const TcPara
     cudaError_t e = cudaFuncSetAttribute(aggregate_tc_kernel<BF16, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)L.total);
     if (e != cudaSuccess) return e;
+    fbs::note_launch();
     aggregate_tc_kernel<BF16, NG><<<grid, kThreads, L.total, stream>>>(map, gmap, p, agg_out, disp_int, disp_sub, err);
     return cudaGetLastError();
 }
 
 // Derived launch parameters; returns false if the case does not fit.
 bool tc_plan(int H, int W, int C, int D, int radius, float sigma_s, float sigma_r, bool bf16, TcParams& p,
-             TcSmem& L)
+             TcSmem& L, int max_rows = kMaxR)
 {
     if (D < 1 || D > 256 || radius < 0 || radius > 24) return false;
     p.H = H;
@@ -662,7 +664,7 @@ bool tc_plan(int H, int W, int C, int D, int radius, float sigma_s, float sigma_
     p.idesc16 = base | (2u << 17);
     // R window rows per stage and S stages: the largest R (<= kMaxR) with at least
     // 3 stages in 227 KB, then as many stages (<= 6) as fit
-    for (p.R = kMaxR; p.R >= 1; --p.R) {
+    for (p.R = max_rows < 1 || max_rows > kMaxR ? kMaxR : max_rows; p.R >= 1; --p.R) {
         for (p.S = 6; p.S >= 3; --p.S) {
             L = tc_smem_layout(p.KW, p.Nb, p.NH, p.R, p.S, p.ones_sep != 0);
             if (L.total <= 227 * 1024) return true;
@@ -677,7 +679,9 @@ int tc_supported(int D, int radius)
 {
     TcParams p;
     TcSmem L;
-    return tc_plan(64, 64, 3, D, radius, 1.f, 1.f, true, p, L) ? 1 : 0;
+    // resolving the tensor-map encoder here keeps later launches free of
+    // driver queries (they may run inside a stream capture)
+    return encode_fn() && tc_plan(64, 64, 3, D, radius, 1.f, 1.f, true, p, L) ? 1 : 0;
 }
 
 cudaError_t launch_xblock16_pad_rows(int H, int W, int D, bool bf16, void* out, cudaStream_t stream)
@@ -686,6 +690,7 @@ cudaError_t launch_xblock16_pad_rows(int H, int W, int D, bool bf16, void* out, 
     if (extra <= 0) return cudaSuccess;
     const size_t n = (size_t)H * ((W + 7) / 8) * extra;
     const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    fbs::note_launch();
     if (bf16)
         xblock16_pad_kernel<true><<<blocks, 256, 0, stream>>>(H, W, D, (__nv_bfloat16*)out);
     else
@@ -695,13 +700,14 @@ cudaError_t launch_xblock16_pad_rows(int H, int W, int D, bool bf16, void* out, 
 
 cudaError_t launch_aggregate_tc(const void* cost, const uint2* rgbx, int H, int W, int C, int D,
                                 int radius, float sigma_s, float sigma_r, bool bf16, float* agg_out,
-                                int32_t* disp_int, float* disp_sub, int* err, int num_sms, cudaStream_t stream)
+                                int32_t* disp_int, float* disp_sub, int* err, int num_sms, cudaStream_t stream,
+                                int max_rows)
 {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     TcParams p;
     TcSmem L;
-    if (!tc_plan(H, W, C, D, radius, sigma_s, sigma_r, bf16, p, L)) return cudaErrorInvalidValue;
+    if (!tc_plan(H, W, C, D, radius, sigma_s, sigma_r, bf16, p, L, max_rows)) return cudaErrorInvalidValue;
 
     // x-blocked volume as a 4-D tensor: (column in block, block row d, block, image row);
     // a box covers all Nb block rows of the KW/8 blocks of R window rows

@@ -103,7 +103,9 @@ int ctx_cost_mode(const fbs_ctx* ctx) { return ctx->opt.cost; }
 int ctx_precision(const fbs_ctx* ctx) { return ctx->opt.prec; }
 cudaStream_t ctx_stream(fbs_ctx* ctx, void* cuda_stream) { return pick_stream(ctx, cuda_stream); }
 fbs_status ctx_error(fbs_ctx* ctx, fbs_status st, const char* msg) { return fail(ctx, st, "%s", msg); }
-void ctx_count_launch(fbs_ctx* ctx, int kind) { ctx->launches[kind]++; }
+void ctx_count_launch(fbs_ctx* ctx, int kind, long long kernels) { ctx->launches[kind] += kernels; }
+
+thread_local long long tl_kernel_launches = 0;
 
 }  // namespace fbs
 
@@ -176,6 +178,11 @@ fbs_status fbs_destroy(fbs_ctx* ctx)
     if (ctx->io) cudaFree(ctx->io);
     if (ctx->derr) cudaFree(ctx->derr);
     for (auto& kv : ctx->bgraphs) cudaGraphExecDestroy(kv.second.exec);
+    for (int k = 0; k < 3; ++k) {
+        if (ctx->bbranch[k]) cudaStreamDestroy(ctx->bbranch[k]);
+        if (ctx->bjoin[k]) cudaEventDestroy(ctx->bjoin[k]);
+    }
+    if (ctx->bfork) cudaEventDestroy(ctx->bfork);
     if (ctx->bpairs) cudaFree(ctx->bpairs);
     if (ctx->bcounters) cudaFree(ctx->bcounters);
     for (int k = 0; k < 2; ++k) {

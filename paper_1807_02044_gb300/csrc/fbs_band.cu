@@ -297,6 +297,7 @@ cudaError_t launch_band_tiles(const float* centre, const float* conf, int H, int
                               float theta, uint32_t* band, int2* tile_range, cudaStream_t stream)
 {
     dim3 grid((W + kAggTileX - 1) / kAggTileX, (H + kAggTileY - 1) / kAggTileY);
+    fbs::note_launch();
     band_tiles_kernel<<<grid, kAggTileX * kAggTileY, 0, stream>>>(centre, conf, H, W, D, half_band, theta, band,
                                                                  tile_range);
     return cudaGetLastError();
@@ -467,6 +468,7 @@ fbs_status run_features(fbs_ctx* ctx, const NetScratch& s, const uint8_t* L, con
     cudaError_t e;
     {
         LaunchScope ls(ctx, FBS_KERNEL_NET, st);
+        fbs::note_launch();
         fbs::band_downsample_kernel<<<dim3((Wq + 127) / 128, Hq, 2), 128, 0, st>>>(L, R, H, W, C, s.gq);
         e = cudaGetLastError();
     }
@@ -474,22 +476,26 @@ fbs_status run_features(fbs_ctx* ctx, const NetScratch& s, const uint8_t* L, con
     const size_t nv = (size_t)Hq * Wq * Dq;
     if (e == cudaSuccess) {
         LaunchScope ls(ctx, FBS_KERNEL_NET, st);
+        fbs::note_launch();
         fbs::band_coarse_cost_kernel<<<dim3((Wq + fbs::kCoarseX - 1) / fbs::kCoarseX, Hq), fbs::kCoarseX, 0, st>>>(
             s.gq, Hq, Wq, Dq, s.kq);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
         LaunchScope ls(ctx, FBS_KERNEL_NET, st);
+        fbs::note_launch();
         fbs::band_row_sum_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(s.kq, Hq, Wq, Dq, s.kh);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
         LaunchScope ls(ctx, FBS_KERNEL_NET, st);
+        fbs::note_launch();
         fbs::band_col_mean_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(s.kh, Hq, Wq, Dq, s.kq);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
         LaunchScope ls(ctx, FBS_KERNEL_NET, st);
+        fbs::note_launch();
         fbs::band_features_kernel<<<dim3((Wq + 127) / 128, Hq), 128, 0, st>>>(s.gq, s.kq, H, W, C, D, s.x0, feat,
                                                                               s.estar);
         e = cudaGetLastError();
@@ -723,6 +729,7 @@ fbs_status fbs_band_net_forward(fbs_ctx* ctx, const uint8_t* left, const uint8_t
     cudaError_t e = cudaSuccess;
     if (centre || conf) {
         LaunchScope ls(ctx, FBS_KERNEL_NET, st);
+        fbs::note_launch();
         fbs::band_head_kernel<<<dim3((W + 255) / 256, H), 256, 0, st>>>(sc.out, sc.estar, H, W, centre, conf);
         e = cudaGetLastError();
     }
@@ -787,6 +794,7 @@ fbs_status fbs_band_feature_points(fbs_ctx* ctx, const uint8_t* left, const uint
     const NetScratch sc = carve_net(ctx->band_ws, H, W, D, false, false);
     if ((s = run_features(ctx, sc, left, right, H, W, C, D, sc.featf, st)) != FBS_OK) return s;
     LaunchScope ls(ctx, FBS_KERNEL_NET, st);
+    fbs::note_launch();
     fbs::band_feature_points_kernel<<<dim3((W + 255) / 256, H), 256, 0, st>>>(sc.featf, sc.estar, H, W,
                                                                            margin_threshold, centre, conf);
     cudaError_t e = cudaGetLastError();
@@ -804,6 +812,7 @@ fbs_status fbs_band_limits(fbs_ctx* ctx, const float* centre, const float* conf,
     DeviceGuard g(ctx->device);
     cudaStream_t st = pick_stream(ctx, cuda_stream);
     LaunchScope ls(ctx, FBS_KERNEL_NET, st);
+    fbs::note_launch();
     fbs::band_limits_kernel<<<(n + 255) / 256, 256, 0, st>>>(centre, conf, n, D, half_band, conf_threshold, lo, hi);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FBS_OK : cuda_fail(ctx, e, "band limits launch");
@@ -843,6 +852,7 @@ fbs_status fbs_compute_disparity_learned(fbs_ctx* ctx, const fbs_pair* pair, int
     if ((s = run_forward(ctx, sc, Hq, Wq, st)) != FBS_OK) return s;
     {
         LaunchScope ls(ctx, FBS_KERNEL_NET, st);
+        fbs::note_launch();
         fbs::band_head_kernel<<<dim3((W + 255) / 256, H), 256, 0, st>>>(sc.out, sc.estar, H, W, sc.centre, sc.conf);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(ctx, e, "band head launch");

@@ -188,6 +188,7 @@ cudaError_t launch_conv_t(const __nv_bfloat16* in, const __nv_bfloat16* image, c
     if (e != cudaSuccess) return e;
     const int ntiles = (Hq * Wq + kM - 1) / kM;
     const int grid = ntiles < 2 * num_sms ? ntiles : 2 * num_sms;
+    fbs::note_launch();
     conv3x3_tc_kernel<CIN, N><<<grid, kConvThreads, smem, stream>>>(in, image, bias, mask, out, nout, Hq, Wq, flip,
                                                                     mode, err);
     return cudaGetLastError();
@@ -410,6 +411,7 @@ cudaError_t launch_wgrad(int l, const __nv_bfloat16* X, const __nv_bfloat16* G, 
     dim3 grid((Wq + kGTX - 1) / kGTX, (Hq + kGTY - 1) / kGTY);
     const int nblk = grid.x * grid.y;
     const int cinp = cin_pad(l), coutp = cout_pad(l);
+    fbs::note_launch();
     if (cinp == 8 && coutp == 32)
         wgrad_kernel<8, 32><<<grid, 9 * 8, 0, stream>>>(X, G, Hq, Wq, partial);
     else if (cinp == 32 && coutp == 32)
@@ -421,6 +423,7 @@ cudaError_t launch_wgrad(int l, const __nv_bfloat16* X, const __nv_bfloat16* G, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int stride = 9 * cinp * coutp + coutp;
+    fbs::note_launch();
     wgrad_reduce_kernel<<<(stride + 255) / 256, 256, 0, stream>>>(partial, nblk, stride, cinp, coutp, cin(l), cout(l),
                                                                    grad + param_offset(l));
     return cudaGetLastError();
@@ -434,10 +437,12 @@ cudaError_t launch_loss(const float* out, const int32_t* estar, const int32_t* l
 {
     const int P = ((H + 3) / 4) * ((W + 3) / 4);
     const int nb = loss_blocks(P);
+    fbs::note_launch();
     loss_kernel<<<nb, kLossThreads, 0, stream>>>(out, estar, label_int, label_sub, H, W, D, half_band, G6,
                                                   loss_partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    fbs::note_launch();
     loss_sum_kernel<<<1, 256, 0, stream>>>(loss_partial, nb, P, loss);
     return cudaGetLastError();
 }
@@ -445,12 +450,14 @@ cudaError_t launch_loss(const float* out, const int32_t* estar, const int32_t* l
 cudaError_t launch_adam(float* theta, float* m, float* v, const float* grad, int n, float lr, float c1, float c2,
                         cudaStream_t stream)
 {
+    fbs::note_launch();
     adam_kernel<<<(n + 255) / 256, 256, 0, stream>>>(theta, m, v, grad, n, lr, c1, c2);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack_images(const float* theta, __nv_bfloat16* images, cudaStream_t stream)
 {
+    fbs::note_launch();
     pack_images_kernel<<<dim3(16, 2 * kLayers), 256, 0, stream>>>(theta, images);
     return cudaGetLastError();
 }

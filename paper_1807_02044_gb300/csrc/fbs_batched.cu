@@ -1,23 +1,34 @@
 // Batched form: many stereo pairs of uneven size, disparity range and radius
-// through one persistent launch per stage (statistics, cost volumes, FP32
-// aggregation with WTA and Eq. (10)), replayed as one CUDA graph.
+// in one call, replayed as one CUDA graph per batch shape.
 //
-// Work decomposition: each stage's kernel walks a flat list of work items
-// (rows, row segments or 32x4 tiles of every pair); CTAs claim items with an
-// atomicAdd on a per-stage counter, so uneven pairs balance themselves and no
-// CTA ever waits on another.  Each pair's results are bit-identical to
-// fbs_compute_disparity in FP32 precision (the same tile code runs on the
-// same data in the same order).
+// FP32 precision: one persistent launch per stage (statistics, cost volumes,
+// FP32 aggregation with WTA and Eq. (10)).  Each stage's kernel walks a flat
+// list of work items (rows, row segments or 32x4 tiles of every pair); CTAs
+// claim items with an atomicAdd on a per-stage counter, so uneven pairs
+// balance themselves and no CTA ever waits on another.  The graph is [copy
+// the pair table from a pinned slot, reset the counters, three persistent
+// launches]; device pointers are read from the table at run time, so one
+// graph serves any buffers of that shape.  These plans differ in pair order
+// (largest first or as given) and in aggregation CTAs per SM (1 or 2).
 //
-// Per batch shape (the list of H, W, C, D, radius and the cost mode) the
-// library keeps a plan chosen by its own autotuner and one CUDA graph per
-// pinned staging slot: [copy the pair table from the slot, reset the
-// counters, three persistent launches].  Device pointers are read from the
-// table at run time, so a graph serves any buffers of that shape.  The plan
-// candidates differ in pair order (largest first or as given) and in the
-// number of aggregation CTAs per SM (1 or 2); the first call of a new shape
-// times each candidate on the caller's data and keeps the fastest, appending
-// "shape plan" to the autotune cache file when one is configured.
+// Branched plans (every precision): each pair runs the launches of the
+// single-pair form over its own slice of one scratch that holds every pair's
+// volume -- FP32: statistics, cost volume, aggregation; BF16 / FP16: pad rows,
+// statistics, 16-bit cost volume, tcgen05 aggregation.  The graph has 1, 2
+// or 4 independent branches; pairs go, largest first, to the branch with the
+// least work so far, so one pair's memory-bound cost build overlaps another's
+// aggregation and small pairs fill the SMs a large pair's last wave leaves
+// idle.  Tensor-core plans also differ in the window rows per pipeline stage
+// (the kernel's maximum, or at most 3: smaller stages, more of them).  The
+// kernels' arguments (and the tensor maps) hold the pairs' addresses, so
+// these graphs are keyed by the buffers too.
+//
+// Either way each pair's results are bit-identical to fbs_compute_disparity
+// in the same precision (the same kernels run on the same data in the same
+// order).  The first call of a new shape (the list of H, W, C, D, radius, the
+// cost mode and the precision) times each plan on the caller's data and keeps
+// the fastest, appending "shape plan" to the autotune cache file when one is
+// configured.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,11 +44,24 @@ using namespace fbs_detail;
 namespace {
 
 constexpr int kMaxPairs = 4096;
-constexpr int kPlans = 4;   // plan = 2 * order + (agg CTAs per SM - 1); order 0 = largest first
+// FP32: plans 0-3 persistent, plan = 2 * order + (agg CTAs per SM - 1), order 0
+// = largest first; plans 4-6 branched with kBranches[plan - 4] branches.
+constexpr int kPersistentPlans = 4;
+constexpr int kPlans = 7;
+// tensor cores: plan = 2 * branch choice + stage choice
+constexpr int kTcPlans = 6;
+constexpr int kBranches[3] = {1, 2, 4};
+constexpr int kTcRowCap[2] = {0, 3};   // window rows per stage: 0 = the kernel's maximum
+constexpr size_t kMaxBranchGraphs = 32;   // branched graphs kept for distinct buffer sets
+
+bool tc_batch(const fbs_ctx* ctx) { return ctx->opt.prec != FBS_PREC_F32; }
+int plan_count(const fbs_ctx* ctx) { return tc_batch(ctx) ? kTcPlans : kPlans; }
 
 std::string batch_signature(fbs_ctx* ctx, int n, const fbs_pair* pairs)
 {
     std::ostringstream os;
+    // FP32 signatures keep their original form; tensor-core ones name the precision
+    if (tc_batch(ctx)) os << (ctx->opt.prec == FBS_PREC_BF16 ? "tb" : "th");
     os << "m" << ctx->opt.cost << ";";
     for (int i = 0; i < n; ++i)
         os << pairs[i].H << "x" << pairs[i].W << "x" << pairs[i].C << "x" << pairs[i].D << "r" << pairs[i].radius
@@ -53,7 +77,7 @@ void load_tuned(fbs_ctx* ctx)
     std::string sig;
     int plan;
     while (f >> sig >> plan)
-        if (plan >= 0 && plan < kPlans) ctx->btuned[sig] = plan;
+        if (plan >= 0 && plan < (sig[0] == 't' ? kTcPlans : kPlans)) ctx->btuned[sig] = plan;
 }
 
 void store_tuned(fbs_ctx* ctx, const std::string& sig, int plan)
@@ -99,19 +123,28 @@ struct Layout {
     int max_radius = 0;
 };
 
+// work of one pair: pixels * disparities * window taps
+double pair_work(const fbs_pair& q)
+{
+    const double t = (2.0 * q.radius + 1) * (2.0 * q.radius + 1);
+    return (double)q.H * q.W * q.D * t;
+}
+
+std::vector<int> largest_first(int n, const fbs_pair* pairs)
+{
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return pair_work(pairs[a]) > pair_work(pairs[b]); });
+    return order;
+}
+
 Layout plan_layout(int n, const fbs_pair* pairs, int order_kind)
 {
     Layout L;
     L.order.resize(n);
     std::iota(L.order.begin(), L.order.end(), 0);
-    if (order_kind == 0) {
-        // largest first: work = pixels * disparities * window taps
-        auto work = [&](int i) {
-            const double t = (2.0 * pairs[i].radius + 1) * (2.0 * pairs[i].radius + 1);
-            return (double)pairs[i].H * pairs[i].W * pairs[i].D * t;
-        };
-        std::stable_sort(L.order.begin(), L.order.end(), [&](int a, int b) { return work(a) > work(b); });
-    }
+    if (order_kind == 0) L.order = largest_first(n, pairs);
     L.off.resize(n);
     for (int k = 0; k < n; ++k) {
         const fbs_pair& q = pairs[L.order[k]];
@@ -220,7 +253,161 @@ fbs_status run_plan(fbs_ctx* ctx, const std::string& sig, int n, const fbs_pair*
     e = cudaGraphLaunch(exec, stream);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->bstage_done[slot], stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batched graph launch");
+    ctx->launches[FBS_KERNEL_COST] += 2;   // statistics and cost
+    ctx->launches[FBS_KERNEL_AGG_F32] += 1;
     return FBS_OK;
+}
+
+// ---- branched plans: every pair's single-pair launches in one graph ----------------
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Scratch of one pair.  Tensor cores: [statistics | packed guide | 16-bit
+// x-blocked volume]; FP32: [statistics | FP32 volume, row pitch padded_ld(D)].
+size_t pair_bytes(const fbs_pair& q, bool tc)
+{
+    if (!tc) return align256(fbs::cost_scratch_bytes(q.H, q.W)) +
+                    align256(sizeof(float) * (size_t)q.H * q.W * fbs::padded_ld(q.D));
+    return align256(fbs::cost_scratch_bytes(q.H, q.W)) + align256(fbs::rgbx_bytes(q.H, q.W)) +
+           align256(fbs::xblock16_bytes(q.H, q.W, q.D));
+}
+
+fbs_status ensure_branches(fbs_ctx* ctx)
+{
+    cudaError_t e = cudaSuccess;
+    if (!ctx->bfork) e = cudaEventCreateWithFlags(&ctx->bfork, cudaEventDisableTiming);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        if (!ctx->bbranch[k]) e = cudaStreamCreateWithFlags(&ctx->bbranch[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !ctx->bjoin[k]) e = cudaEventCreateWithFlags(&ctx->bjoin[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch branch streams");
+    return FBS_OK;
+}
+
+// Capture every pair's launches of the single-pair form of the context's
+// precision, spread over nb branches, into one graph (rows: the tensor-core
+// stage cap).
+fbs_status build_branch_graph(fbs_ctx* ctx, int n, const fbs_pair* pairs, int nb, int rows, fbs_batch_graph* g)
+{
+    const bool tc = tc_batch(ctx);
+    const bool bf16 = ctx->opt.prec == FBS_PREC_BF16;
+    const int mode = ctx->opt.cost;
+    fbs_status st = ensure_branches(ctx);
+    if (st != FBS_OK) return st;
+    const std::vector<int> order = largest_first(n, pairs);
+    cudaStream_t cs = ctx->stream;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "begin graph capture");
+    if (nb > 1) e = cudaEventRecord(ctx->bfork, cs);
+    int joined = 0;   // branches that joined the capture (each must be joined back)
+    for (int k = 1; k < nb && e == cudaSuccess; ++k) {
+        e = cudaStreamWaitEvent(ctx->bbranch[k - 1], ctx->bfork, 0);
+        if (e == cudaSuccess) joined = k;
+    }
+    std::vector<double> load(nb, 0.0);
+    size_t off = 0;
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        const fbs_pair& q = pairs[order[k]];
+        const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[b] += pair_work(q);
+        cudaStream_t s = b == 0 ? cs : ctx->bbranch[b - 1];
+        uint8_t* base = (uint8_t*)ctx->ws + off;
+        off += pair_bytes(q, tc);
+        const size_t stats = align256(fbs::cost_scratch_bytes(q.H, q.W));
+        fbs::CostScratch sc = fbs::carve_cost_scratch(base, q.H, q.W);
+        long long k0 = fbs::launch_count();
+        if (!tc) {
+            const int ld = fbs::padded_ld(q.D);
+            float* cost = (float*)(base + stats);
+            e = fbs::launch_cost_build(sc, q.left, q.right, q.H, q.W, q.C, q.D, ld, mode, q.tau, cost, s);
+            g->kernels[FBS_KERNEL_COST] += fbs::launch_count() - k0;
+            k0 = fbs::launch_count();
+            if (e == cudaSuccess)
+                e = fbs::launch_aggregate_f32(cost, ld, q.left, q.H, q.W, q.C, q.D, q.radius, q.sigma_s, q.sigma_r,
+                                              nullptr, q.disp_int, q.disp_subpix, s);
+            g->kernels[FBS_KERNEL_AGG_F32] += fbs::launch_count() - k0;
+            continue;
+        }
+        sc.rgbx = (uint2*)(base + stats);
+        void* cost = base + stats + align256(fbs::rgbx_bytes(q.H, q.W));
+        if (mode != FBS_COST_NCC) {
+            e = fbs::launch_pack_rgbx(q.left, q.H, q.W, q.C, sc.rgbx, s);
+            g->kernels[FBS_KERNEL_OTHER] += fbs::launch_count() - k0;
+            k0 = fbs::launch_count();
+        }
+        if (e == cudaSuccess)
+            e = fbs::launch_cost_build_xblock16(sc, q.left, q.right, q.H, q.W, q.C, q.D, mode, q.tau, bf16, cost, s);
+        g->kernels[FBS_KERNEL_COST] += fbs::launch_count() - k0;
+        k0 = fbs::launch_count();
+        if (e == cudaSuccess)
+            e = fbs::launch_aggregate_tc(cost, sc.rgbx, q.H, q.W, q.C, q.D, q.radius, q.sigma_s, q.sigma_r, bf16,
+                                         nullptr, q.disp_int, q.disp_subpix, ctx->derr, ctx->num_sms, s, rows);
+        g->kernels[FBS_KERNEL_AGG_TC] += fbs::launch_count() - k0;
+    }
+    // join every branch back, also after a failed launch, so the capture ends cleanly
+    for (int k = 1; k <= joined; ++k) {
+        cudaError_t e1 = cudaEventRecord(ctx->bjoin[k - 1], ctx->bbranch[k - 1]);
+        if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(cs, ctx->bjoin[k - 1], 0);
+        if (e == cudaSuccess) e = e1;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "branched batch graph capture");
+    return FBS_OK;
+}
+
+fbs_status run_branch_plan(fbs_ctx* ctx, const std::string& sig, int n, const fbs_pair* pairs, int plan, int nb,
+                           int rows, cudaStream_t stream)
+{
+    size_t need = 0;
+    for (int i = 0; i < n; ++i) need += pair_bytes(pairs[i], tc_batch(ctx));
+    fbs_status st = ensure(ctx, &ctx->ws, &ctx->ws_bytes, need, "batch cost volumes");
+    if (st != FBS_OK) return st;
+    // graphs that hold the pairs' addresses are keyed by them ("g|" prefix)
+    std::ostringstream key;
+    key << "g|" << sig << "|p" << plan << "|ws" << (uintptr_t)ctx->ws << std::hex;
+    for (int i = 0; i < n; ++i)
+        key << "|" << (uintptr_t)pairs[i].left << "," << (uintptr_t)pairs[i].right << ","
+            << (uintptr_t)pairs[i].disp_int << "," << (uintptr_t)pairs[i].disp_subpix;
+    auto it = ctx->bgraphs.find(key.str());
+    if (it == ctx->bgraphs.end()) {
+        size_t held = 0;
+        for (auto& kv : ctx->bgraphs) held += kv.first.compare(0, 2, "g|") == 0;
+        if (held >= kMaxBranchGraphs) {
+            // too many buffer sets: drop the branched graphs (none is in use on the host side)
+            cudaError_t e = cudaStreamSynchronize(stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise before dropping batch graphs");
+            for (auto g = ctx->bgraphs.begin(); g != ctx->bgraphs.end();) {
+                if (g->first.compare(0, 2, "g|") == 0) {
+                    cudaGraphExecDestroy(g->second.exec);
+                    g = ctx->bgraphs.erase(g);
+                } else {
+                    ++g;
+                }
+            }
+        }
+        fbs_batch_graph g;
+        st = build_branch_graph(ctx, n, pairs, nb, rows, &g);
+        if (st != FBS_OK) return st;
+        it = ctx->bgraphs.emplace(key.str(), g).first;
+    }
+    cudaError_t e = cudaGraphLaunch(it->second.exec, stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "branched batch graph launch");
+    for (int k = 0; k < FBS_KERNEL_KINDS; ++k) ctx->launches[k] += it->second.kernels[k];
+    return FBS_OK;
+}
+
+fbs_status run_any_plan(fbs_ctx* ctx, const std::string& sig, int n, const fbs_pair* pairs, int plan,
+                        cudaStream_t stream)
+{
+    if (tc_batch(ctx))
+        return run_branch_plan(ctx, sig, n, pairs, plan, kBranches[plan >> 1], kTcRowCap[plan & 1], stream);
+    if (plan < kPersistentPlans) return run_plan(ctx, sig, n, pairs, plan, stream);
+    return run_branch_plan(ctx, sig, n, pairs, plan, kBranches[plan - kPersistentPlans], 0, stream);
 }
 
 }  // namespace
@@ -239,8 +426,12 @@ extern "C" fbs_status fbs_compute_disparity_batched(fbs_ctx* ctx, int n, const f
             return fail(ctx, s, "%s", m.c_str());
         }
     }
-    if (ctx->opt.prec != FBS_PREC_F32)
-        return fail(ctx, FBS_ERR_UNSUPPORTED, "the batched form runs the FP32 aggregation only");
+    if (tc_batch(ctx))
+        for (int i = 0; i < n; ++i)
+            if (!fbs::tc_supported(pairs[i].D, pairs[i].radius))
+                return fail(ctx, FBS_ERR_UNSUPPORTED,
+                            "pair %d: tensor-core aggregation supports D <= 256 and radius <= 24 (got D=%d, radius=%d)",
+                            i, pairs[i].D, pairs[i].radius);
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(ctx, FBS_ERR_CUDA, "cannot select device %d", ctx->device);
     fbs_status st = ensure_batch_buffers(ctx, n);
@@ -258,11 +449,11 @@ extern "C" fbs_status fbs_compute_disparity_batched(fbs_ctx* ctx, int n, const f
         if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune events");
         int best = 0;
         float best_ms = 1e30f;
-        for (int plan = 0; plan < kPlans && st == FBS_OK; ++plan) {
-            st = run_plan(ctx, sig, n, pairs, plan, stream);
+        for (int plan = 0; plan < plan_count(ctx) && st == FBS_OK; ++plan) {
+            st = run_any_plan(ctx, sig, n, pairs, plan, stream);
             for (int rep = 0; rep < 3 && st == FBS_OK; ++rep) {
                 cudaEventRecord(a, stream);
-                st = run_plan(ctx, sig, n, pairs, plan, stream);
+                st = run_any_plan(ctx, sig, n, pairs, plan, stream);
                 cudaEventRecord(b, stream);
                 e = cudaEventSynchronize(b);
                 float ms = 0.f;
@@ -281,14 +472,10 @@ extern "C" fbs_status fbs_compute_disparity_batched(fbs_ctx* ctx, int n, const f
         store_tuned(ctx, sig, best);
         tuned = ctx->btuned.find(sig);
     }
-    {
-        LaunchScope ls(ctx, FBS_KERNEL_BATCH, stream);
-        st = run_plan(ctx, sig, n, pairs, tuned->second, stream);
-    }
-    ctx->launches[FBS_KERNEL_COST] += 2;   // the batch graph runs three kernels
-    ctx->launches[FBS_KERNEL_AGG_F32] += 1;
-    ctx->launches[FBS_KERNEL_BATCH] -= 1;
-    return st;
+    if (tuned->second >= plan_count(ctx)) return fail(ctx, FBS_ERR_INVALID_ARG, "bad cached plan");
+    // one timed scope around the graph; its kernels are counted per kind by the plan runners
+    LaunchScope ls(ctx, FBS_KERNEL_BATCH, stream);
+    return run_any_plan(ctx, sig, n, pairs, tuned->second, stream);
 }
 
 extern "C" fbs_status fbs_batch_plan(fbs_ctx* ctx, int n, const fbs_pair* pairs, int* plan)
@@ -297,5 +484,17 @@ extern "C" fbs_status fbs_batch_plan(fbs_ctx* ctx, int n, const fbs_pair* pairs,
     if (!ctx->btuned_loaded) load_tuned(ctx);
     auto it = ctx->btuned.find(batch_signature(ctx, n, pairs));
     *plan = it == ctx->btuned.end() ? -1 : it->second;
+    return FBS_OK;
+}
+
+extern "C" fbs_status fbs_batch_set_plan(fbs_ctx* ctx, int n, const fbs_pair* pairs, int plan)
+{
+    if (!ctx) return FBS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!pairs || n < 1 || n > kMaxPairs) return fail(ctx, FBS_ERR_INVALID_ARG, "batch of %d pairs (1..%d)", n, kMaxPairs);
+    if (plan < 0 || plan >= plan_count(ctx))
+        return fail(ctx, FBS_ERR_INVALID_ARG, "plan %d outside 0..%d for this precision", plan, plan_count(ctx) - 1);
+    if (!ctx->btuned_loaded) load_tuned(ctx);
+    ctx->btuned[batch_signature(ctx, n, pairs)] = plan;
     return FBS_OK;
 }

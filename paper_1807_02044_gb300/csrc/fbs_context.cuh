@@ -20,6 +20,7 @@
 struct fbs_batch_graph {
     cudaGraphExec_t exec = nullptr;
     int slot = 0;
+    long long kernels[FBS_KERNEL_KINDS] = {};   // kernels one replay runs, per kind
 };
 
 struct fbs_ctx {
@@ -52,6 +53,9 @@ struct fbs_ctx {
     std::map<std::string, int> btuned;                 // batch shape -> chosen plan
     std::map<std::string, fbs_batch_graph> bgraphs;    // plan-specific graph per slot
     bool btuned_loaded = false;
+    cudaStream_t bbranch[3] = {nullptr, nullptr, nullptr};   // extra branches of the tensor-core batch graph
+    cudaEvent_t bfork = nullptr;
+    cudaEvent_t bjoin[3] = {nullptr, nullptr, nullptr};
     // band form: the network's state and the band scratch (grown on demand)
     struct fbs_band_state* band = nullptr;
     void* band_ws = nullptr;
@@ -147,12 +151,14 @@ inline cudaEvent_t take_event(fbs_ctx* ctx)
     return e;
 }
 
-// Bracket one kernel launch for the accounting API.
+// Bracket the kernel launches of one step for the accounting API (events
+// around them when profiling; the number of kernels they launched).
 struct LaunchScope {
     fbs_ctx* ctx;
     int kind;
     cudaStream_t st;
     cudaEvent_t a = nullptr;
+    long long k0 = fbs::launch_count();   // kernels noted inside the scope are counted
     LaunchScope(fbs_ctx* c, int k, cudaStream_t s) : ctx(c), kind(k), st(s)
     {
         if (ctx->profiling) {
@@ -162,7 +168,7 @@ struct LaunchScope {
     }
     ~LaunchScope()
     {
-        ctx->launches[kind]++;
+        ctx->launches[kind] += fbs::launch_count() - k0;
         if (a) {
             cudaEvent_t b = take_event(ctx);
             if (b) {

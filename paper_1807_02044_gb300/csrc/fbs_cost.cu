@@ -469,6 +469,7 @@ cudaError_t launch_cost_kernel(const CostScratch& sc, const uint8_t* left, const
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((W + kXS - 1) / kXS, H);
+    fbs::note_launch();
     cost_kernel<MODE, T, PLANAR><<<grid, kThreads, smem, stream>>>(sc.g, sc.s, sc.rv, left, right, H, W, C, D, ld,
                                                                    tau, out);
     return cudaGetLastError();
@@ -478,6 +479,7 @@ cudaError_t launch_stats(const CostScratch& sc, const uint8_t* left, const uint8
                          cudaStream_t stream)
 {
     dim3 grid((W + 255) / 256, H, 2);
+    fbs::note_launch();
     grey_stats_kernel<<<grid, 256, 0, stream>>>(left, right, H, W, C, sc.g, sc.s, sc.rv, sc.rgbx);
     return cudaGetLastError();
 }
@@ -497,6 +499,7 @@ cudaError_t prepare_cost_batched()
 cudaError_t launch_stats_batched(const BatchPair* pairs, int npairs, int nitems, int* counter, int grid,
                                  cudaStream_t stream)
 {
+    fbs::note_launch();
     grey_stats_batched_kernel<<<grid, 256, 0, stream>>>(pairs, npairs, nitems, counter);
     return cudaGetLastError();
 }
@@ -504,6 +507,7 @@ cudaError_t launch_stats_batched(const BatchPair* pairs, int npairs, int nitems,
 cudaError_t launch_cost_batched(const BatchPair* pairs, int npairs, int nitems, int* counter, int grid,
                                 cudaStream_t stream)
 {
+    fbs::note_launch();
     cost_batched_kernel<<<grid, kThreads, cost_smem_bytes(), stream>>>(pairs, npairs, nitems, counter);
     return cudaGetLastError();
 }
@@ -529,6 +533,7 @@ __global__ void pack_rgbx_kernel(const uint8_t* __restrict__ img, int H, int W, 
 cudaError_t launch_pack_rgbx(const uint8_t* img, int H, int W, int C, uint2* rgbx, cudaStream_t stream)
 {
     dim3 grid((W + 255) / 256, H);
+    fbs::note_launch();
     pack_rgbx_kernel<<<grid, 256, 0, stream>>>(img, H, W, C, rgbx);
     return cudaGetLastError();
 }
@@ -568,6 +573,7 @@ cudaError_t launch_cost_band(const CostScratch& sc, const uint8_t* left, const u
     if (e != cudaSuccess) return e;
     const int ntx = (W + kAggTileX - 1) / kAggTileX, nty = (H + kAggTileY - 1) / kAggTileY;
     dim3 grid((W + kXS - 1) / kXS, H);
+    fbs::note_launch();
     cost_band_kernel<<<grid, kThreads, smem, stream>>>(sc.g, sc.s, sc.rv, H, W, D, ld, radius, tile_range, ntx, nty,
                                                        cost);
     return cudaGetLastError();
@@ -584,17 +590,20 @@ cudaError_t launch_cost_build_lr(const CostScratch& sc, const uint8_t* left, con
     dim3 grid((W + kXS - 1) / kXS, H);
     if (mode == 0) {
         e = cudaFuncSetAttribute(cost_lr_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fbs::note_launch();
         if (e == cudaSuccess)
             cost_lr_kernel<0><<<grid, kThreads, smem, stream>>>(sc.g, sc.s, sc.rv, left, right, H, W, C, D, ld, tau,
                                                                 cost, cost_r);
     } else {
         e = cudaFuncSetAttribute(cost_lr_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fbs::note_launch();
         if (e == cudaSuccess)
             cost_lr_kernel<1><<<grid, kThreads, smem, stream>>>(sc.g, sc.s, sc.rv, left, right, H, W, C, D, ld, tau,
                                                                 cost, cost_r);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    fbs::note_launch();
     right_edge_fill_kernel<<<H, 256, 0, stream>>>(H, W, D, ld, mode == 0 ? 2.f : tau, cost_r);
     return cudaGetLastError();
 }

@@ -8,6 +8,12 @@
 
 namespace fbs {
 
+// Kernels launched by the calling host thread (every launch site notes itself;
+// a context's per-kind counters add the difference around each launch scope).
+extern thread_local long long tl_kernel_launches;
+inline void note_launch() { ++tl_kernel_launches; }
+inline long long launch_count() { return tl_kernel_launches; }
+
 // Cost volume rows are padded to a multiple of 4 floats so that one pixel's
 // disparity vector starts on a 16-byte boundary (vector loads, TMA, cp.async).
 inline int padded_ld(int D) { return (D + 3) & ~3; }
@@ -70,9 +76,11 @@ cudaError_t launch_aggregate_f32(const float* cost, int ld, const uint8_t* guide
 // aligned.  err: device int set to nonzero if a bounded wait inside the kernel
 // gave up.
 int tc_supported(int D, int radius);
+// max_rows (0 = the kernel's own maximum) caps the window rows per pipeline stage.
 cudaError_t launch_aggregate_tc(const void* cost, const uint2* rgbx, int H, int W, int C, int D,
                                 int radius, float sigma_s, float sigma_r, bool bf16, float* agg_out,
-                                int32_t* disp_int, float* disp_sub, int* err, int num_sms, cudaStream_t stream);
+                                int32_t* disp_int, float* disp_sub, int* err, int num_sms, cudaStream_t stream,
+                                int max_rows = 0);
 // Packed guide plane of an image: (RGBX, squared norm) per pixel, pitch rgbx_pitch(W); the
 // tensor-core path loads its guide tiles from it.
 cudaError_t launch_pack_rgbx(const uint8_t* img, int H, int W, int C, uint2* rgbx, cudaStream_t stream);
@@ -145,7 +153,7 @@ int ctx_cost_mode(const fbs_ctx* ctx);
 int ctx_precision(const fbs_ctx* ctx);
 cudaStream_t ctx_stream(fbs_ctx* ctx, void* cuda_stream);
 fbs_status ctx_error(fbs_ctx* ctx, fbs_status st, const char* msg);
-void ctx_count_launch(fbs_ctx* ctx, int kind);
+void ctx_count_launch(fbs_ctx* ctx, int kind, long long kernels);
 // Release the band form's state (called by fbs_destroy).
 void band_free(fbs_ctx* ctx);
 

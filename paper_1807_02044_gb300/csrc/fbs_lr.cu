@@ -76,6 +76,7 @@ extern "C" fbs_status fbs_compute_disparity_lr(fbs_ctx* ctx, const uint8_t* left
     }
     if (lrc) {
         LaunchScope ls(ctx, FBS_KERNEL_OTHER, st);
+        fbs::note_launch();
         lrc_kernel<<<dim3((W + 255) / 256, H), 256, 0, st>>>(dl, dr, H, W, disp_int, disp_subpix);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(ctx, e, "LRC launch");

@@ -100,15 +100,17 @@ extern "C" fbs_status fbs_compute_disparity_noalloc(fbs_ctx* ctx, const uint8_t*
     // array needs clearing.
     const fbs::CostScratch sc = fbs::carve_cost_scratch(scratch, H, W);
     float* cost = (float*)((uint8_t*)scratch + stats);
+    long long k0 = fbs::launch_count();
     e = fbs::launch_cost_build(sc, left, right, H, W, C, D, ld, fbs::ctx_cost_mode(ctx), tau, cost, st);
-    fbs::ctx_count_launch(ctx, FBS_KERNEL_COST);
+    fbs::ctx_count_launch(ctx, FBS_KERNEL_COST, fbs::launch_count() - k0);
     if (e != cudaSuccess) {
         std::string msg = std::string("cost build launch: ") + cudaGetErrorString(e);
         return fbs::ctx_error(ctx, FBS_ERR_CUDA, msg.c_str());
     }
+    k0 = fbs::launch_count();
     e = fbs::launch_aggregate_f32(cost, ld, left, H, W, C, D, radius, sigma_s, sigma_r, nullptr, disp_int,
                                   disp_subpix, st);
-    fbs::ctx_count_launch(ctx, FBS_KERNEL_AGG_F32);
+    fbs::ctx_count_launch(ctx, FBS_KERNEL_AGG_F32, fbs::launch_count() - k0);
     if (e != cudaSuccess) {
         std::string msg = std::string("aggregation launch: ") + cudaGetErrorString(e);
         return fbs::ctx_error(ctx, FBS_ERR_CUDA, msg.c_str());

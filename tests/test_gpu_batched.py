@@ -1,6 +1,8 @@
-"""Batched form through the C ABI: uneven pairs in one persistent launch per
-stage must reproduce fbs_compute_disparity bit for bit (same tile code, same
-data, same order), and the autotuner's choice must persist."""
+"""Batched form through the C ABI: uneven pairs in one CUDA graph must
+reproduce fbs_compute_disparity bit for bit in the context's precision (FP32:
+one persistent launch per stage, same tile code, same data, same order;
+BF16 / FP16: the single-pair tensor-core launches spread over concurrent graph
+branches), under every plan, and the autotuner's choice must persist."""
 
 import os
 
@@ -53,7 +55,7 @@ def test_batched_equals_per_pair_bit_for_bit(fbs, mode):
             assert torch.equal(q["disp_int"], di)
             assert torch.equal(q["disp_subpix"], ds)
         plan = fbs.fbs_batch_plan(ctx.ctx, pairs)
-        assert 0 <= plan < 4
+        assert 0 <= plan < 7
         # replay with fresh output buffers and new images of the same shapes
         pairs2 = _batch(3 + mode)
         for q in pairs2:
@@ -101,6 +103,93 @@ def test_batched_rejects_bad_pairs(fbs):
         assert ei.value.status == fbs.FBS_ERR_INVALID_ARG and "pair 1" in str(ei.value)
         ctx.set_options(prec=fbs.FBS_PREC_BF16)
         pairs[1]["radius"] = 2
+        pairs[2]["D"] = 300   # beyond the tensor-core form's 256
         with pytest.raises(fbs.FBSError) as ei:
             fbs.fbs_compute_disparity_batched(ctx.ctx, pairs)
-        assert ei.value.status == fbs.FBS_ERR_UNSUPPORTED
+        assert ei.value.status == fbs.FBS_ERR_UNSUPPORTED and "pair 2" in str(ei.value)
+        with pytest.raises(fbs.FBSError) as ei:
+            fbs.fbs_batch_set_plan(ctx.ctx, pairs, 6)
+        assert ei.value.status == fbs.FBS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fp32_batch_equals_per_pair_under_every_plan(fbs, mode):
+    """Persistent plans 0-3 and branched plans 4-6."""
+    pairs = _batch(41 + mode, n=7)
+    with fbs.Context(0, cost=mode) as ctx:
+        ref = _per_pair(ctx, pairs)
+        for plan in range(7):
+            for q in pairs:
+                q["disp_int"].fill_(-7)
+                q["disp_subpix"].fill_(-7.0)
+            fbs.fbs_batch_set_plan(ctx.ctx, pairs, plan)
+            fbs.fbs_compute_disparity_batched(ctx.ctx, pairs, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            fbs.fbs_sync(ctx.ctx)
+            for i, (q, (di, ds)) in enumerate(zip(pairs, ref)):
+                assert torch.equal(q["disp_int"], di), (plan, i)
+                assert torch.equal(q["disp_subpix"], ds), (plan, i)
+        with pytest.raises(fbs.FBSError):
+            fbs.fbs_batch_set_plan(ctx.ctx, pairs, 7)
+
+
+def _per_pair(ctx, pairs):
+    ref = []
+    for q in pairs:
+        ref.append(ctx.compute_disparity(q["left"], q["right"], q["D"], q["radius"], q["sigma_s"], q["sigma_r"],
+                                         q["tau"]))
+    torch.cuda.synchronize()
+    return ref
+
+
+@pytest.mark.parametrize("prec,mode", [("bf16", 0), ("fp16", 0), ("bf16", 1)])
+def test_tensor_core_batch_equals_per_pair_under_every_plan(fbs, prec, mode):
+    p = fbs.FBS_PREC_BF16 if prec == "bf16" else fbs.FBS_PREC_F16
+    pairs = _batch(21 + mode, n=11)
+    pairs[0]["D"], pairs[0]["radius"] = 256, 9    # the largest disparity range, more than one TMEM block
+    with fbs.Context(0, cost=mode, prec=p) as ctx:
+        ref = _per_pair(ctx, pairs)
+        for plan in range(6):
+            for q in pairs:
+                q["disp_int"].fill_(-7)
+                q["disp_subpix"].fill_(-7.0)
+            fbs.fbs_batch_set_plan(ctx.ctx, pairs, plan)
+            assert fbs.fbs_batch_plan(ctx.ctx, pairs) == plan
+            fbs.fbs_compute_disparity_batched(ctx.ctx, pairs, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            fbs.fbs_sync(ctx.ctx)
+            for i, (q, (di, ds)) in enumerate(zip(pairs, ref)):
+                assert torch.equal(q["disp_int"], di), (plan, i)
+                assert torch.equal(q["disp_subpix"], ds), (plan, i)
+
+
+def test_tensor_core_batch_autotunes_and_follows_new_buffers(fbs):
+    pairs = _batch(31, n=6)
+    with fbs.Context(0, prec=fbs.FBS_PREC_BF16) as ctx:
+        assert fbs.fbs_batch_plan(ctx.ctx, pairs) == -1
+        fbs.fbs_profile(ctx.ctx, 1)
+        fbs.fbs_compute_disparity_batched(ctx.ctx, pairs, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        plan = fbs.fbs_batch_plan(ctx.ctx, pairs)
+        assert 0 <= plan < 6
+        ref = _per_pair(ctx, pairs)
+        for q, (di, ds) in zip(pairs, ref):
+            assert torch.equal(q["disp_int"], di) and torch.equal(q["disp_subpix"], ds)
+        # every kernel is counted: per pair pad rows, statistics, cost and aggregation
+        fbs.fbs_profile(ctx.ctx, 1)
+        fbs.fbs_compute_disparity_batched(ctx.ctx, pairs, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert fbs.fbs_profile_read(ctx.ctx, fbs.FBS_KERNEL_AGG_TC)[1] == len(pairs)
+        assert fbs.fbs_profile_read(ctx.ctx, fbs.FBS_KERNEL_COST)[1] == 3 * len(pairs)
+        fbs.fbs_profile(ctx.ctx, 0)
+        # new output buffers and new images of the same shapes: a new graph, the same results as per-pair calls
+        pairs2 = _batch(31, n=6)
+        for q in pairs2:
+            q["left"] = torch.flip(q["left"], dims=[1]).contiguous()
+        fbs.fbs_compute_disparity_batched(ctx.ctx, pairs2, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        got = [(q["disp_int"].clone(), q["disp_subpix"].clone()) for q in pairs2]
+        ref2 = _per_pair(ctx, pairs2)
+        for (gi, gs), (di, ds) in zip(got, ref2):
+            assert torch.equal(gi, di) and torch.equal(gs, ds)
+        fbs.fbs_sync(ctx.ctx)
