@@ -156,6 +156,39 @@ __device__ __forceinline__ void raise_abort(volatile uint32_t* abort_flag, int* 
     atomicCAS(err, 0, code);
 }
 
+// Packed FP32 pairs (f32x2: one instruction, two IEEE round-to-nearest lanes).
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ uint64_t u2_pack(uint32_t lo, uint32_t hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// 2^23 as an FP32 bit pattern: for 0 <= c < 2^23 the pattern kMagic + c is the
+// float 2^23 + c exactly, so subtracting 2^23 gives float(c) exactly.
+constexpr uint32_t kMagic = 0x4B000000u;
+
 template <bool BF16>
 __device__ __forceinline__ uint32_t pack2(float lo, float hi)
 {
@@ -188,7 +221,9 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                     int* __restrict__ err)
 {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // align by an offset from the __shared__ array itself (not an integer round
+    // trip), so the compiler keeps every operand access a 32-bit shared one
+    uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const bool ones_sep = p.ones_sep != 0;
     const TcSmem L = tc_smem_layout(p.KW, p.Nb, p.NH, p.R, p.S, ones_sep);
     uint8_t* a_base = sm + L.a_off;
@@ -258,7 +293,11 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
         // four pixels of a pass start 8 banks apart, so a pass's 4-byte stores
         // need two wavefronts at most.
         // Colour distance: |q - p|^2 = |q|^2 + |p|^2 - 2 q.p, exact in integers
-        // (|q|^2 comes with the guide tile, q.p is one dp4a).
+        // (|q|^2 comes with the guide tile, q.p is one dp4a).  It is below 2^23,
+        // so carrying kMagic in |p|^2 turns the integer into the bits of
+        // 2^23 + c and one packed subtraction gives both columns' c as exact
+        // floats; the exponent argument c*neg_kr + (sx + sy) of a column pair is
+        // one packed add and one packed FMA (the same roundings as scalar code).
         const int ps = lane >> 3, pi = lane & 7;
         const int np = p.rho + 1;
         int pm[kPasses], kcen[kPasses], kk[kPasses][NG];
@@ -278,6 +317,8 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
             }
         }
         const float ninf = __int_as_float(0xff800000);
+        const uint64_t magic2 = f2_pack(-8388608.f, -8388608.f);
+        const uint64_t nkr2 = f2_pack(p.neg_kr, p.neg_kr);
         uint32_t g = 0, t = 0;
         bool stop = false;
         for (int tile = blockIdx.x; tile < p.ntiles && !stop; tile += gridDim.x, ++t) {
@@ -294,13 +335,14 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
             uint32_t pcol[kPasses], pp[kPasses];
             int pty[kPasses];
             float sx0[kPasses][NG], sx1[kPasses][NG];
+            uint64_t sxp[kPasses][NG];
 #pragma unroll
             for (int i = 0; i < kPasses; ++i) {
                 pty[i] = pm[i] >> 4;
                 const bool pval = ty0 + pty[i] < p.H && tx0 + (pm[i] & 15) < p.W;
                 const uint2 pc = gt[(pty[i] + p.rho) * KW + kcen[i]];
                 pcol[i] = pc.x;
-                pp[i] = pc.y;
+                pp[i] = pc.y + kMagic;
 #pragma unroll
                 for (int pg = 0; pg < NG; ++pg) {
                     const int d0 = kk[i][pg] - kcen[i], d1 = d0 + 1;
@@ -309,6 +351,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                                      ? (float)(d0 * d0) * p.neg_ks : ninf;
                     sx1[i][pg] = (pval && d1 >= -p.rho && d1 <= p.rho && (unsigned)(x0 + 1) < (unsigned)p.W)
                                      ? (float)(d1 * d1) * p.neg_ks : ninf;
+                    sxp[i][pg] = f2_pack(sx0[i][pg], sx1[i][pg]);
                 }
             }
             const int hr_lo = max(0, p.rho - ty0);
@@ -337,17 +380,19 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                         const int dy = hr - p.rho - pty[i];
                         const bool act = dy >= -p.rho && dy <= p.rho;   // uniform over the pass
                         const float sy = (float)(dy * dy) * p.neg_ks;
+                        const uint64_t syp = f2_pack(sy, sy);
 #pragma unroll
                         for (int pg = 0; pg < NG; ++pg) {
                             if (!on[i][pg]) continue;
                             uint32_t packed = 0;
                             if (act) {
                                 const uint4 q = *(const uint4*)(grow + kk[i][pg]);
-                                const int c0 = (int)(q.y + pp[i]) - 2 * (int)__dp4a(q.x, pcol[i], 0u);
-                                const int c1 = (int)(q.w + pp[i]) - 2 * (int)__dp4a(q.z, pcol[i], 0u);
-                                const float w0 = ex2_approx(fmaf((float)c0, p.neg_kr, sx0[i][pg] + sy));
-                                const float w1 = ex2_approx(fmaf((float)c1, p.neg_kr, sx1[i][pg] + sy));
-                                packed = pack2<BF16>(w0, w1);
+                                const uint32_t e0 = q.y + pp[i] - 2u * __dp4a(q.x, pcol[i], 0u);
+                                const uint32_t e1 = q.w + pp[i] - 2u * __dp4a(q.z, pcol[i], 0u);
+                                const uint64_t c = f2_add(u2_pack(e0, e1), magic2);
+                                float a0, a1;
+                                f2_unpack(f2_fma(c, nkr2, f2_add(sxp[i][pg], syp)), a0, a1);
+                                packed = pack2<BF16>(ex2_approx(a0), ex2_approx(a1));
                             }
                             *(uint32_t*)(arow + aoff[i][pg]) = packed;
                         }
@@ -709,13 +754,17 @@ cudaError_t launch_aggregate_tc(const void* cost, const uint2* rgbx, int H, int 
     TcSmem L;
     if (!tc_plan(H, W, C, D, radius, sigma_s, sigma_r, bf16, p, L, max_rows)) return cudaErrorInvalidValue;
 
-    // x-blocked volume as a 4-D tensor: (column in block, block row d, block, image row);
-    // a box covers all Nb block rows of the KW/8 blocks of R window rows
+    // x-blocked volume as a 4-D tensor: (16 block rows d x 8 columns = 256
+    // contiguous bytes, group of 16 block rows, block, image row); a box covers
+    // all Nb block rows of the KW/8 blocks of R window rows and lands in shared
+    // memory as [R][KW/8][Nb][8], the B operand's K-major core-matrix order.
+    // The 256-byte inner dimension keeps the copy at a few wide requests per
+    // block instead of one per 16-byte block row.
     CUtensorMap map;
     const int nxb = (W + 7) / 8;
-    cuuint64_t dims[4] = {8, (cuuint64_t)p.Nb, (cuuint64_t)nxb, (cuuint64_t)H};
-    cuuint64_t strides[3] = {16, (cuuint64_t)p.Nb * 16, (cuuint64_t)nxb * p.Nb * 16};
-    cuuint32_t box[4] = {8, (cuuint32_t)p.Nb, (cuuint32_t)(p.KW / 8), (cuuint32_t)p.R};
+    cuuint64_t dims[4] = {128, (cuuint64_t)(p.Nb / 16), (cuuint64_t)nxb, (cuuint64_t)H};
+    cuuint64_t strides[3] = {256, (cuuint64_t)p.Nb * 16, (cuuint64_t)nxb * p.Nb * 16};
+    cuuint32_t box[4] = {128, (cuuint32_t)(p.Nb / 16), (cuuint32_t)(p.KW / 8), (cuuint32_t)p.R};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(&map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4,
                      const_cast<void*>(cost), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
