@@ -454,11 +454,13 @@ def run_ours(args):
     ld = (p.D + 3) // 4 * 4
     vol = 4 * p.H * p.W * ld if args.prec == "f32" else 2 * p.H * p.D * ((p.W + 7) // 8 * 8)
     cost_bytes = 2 * p.H * p.W * p.C + vol
-    roofline_cost = {"kernel": "cost_kernel (+ grey_stats_kernel)", "bound": "hbm",
+    cost_kernel = "cost_kernel" if args.prec == "f32" else "cost_xb_kernel"
+    roofline_cost = {"kernel": "cost_kernel (+ grey_stats_kernel)" if args.prec == "f32" else
+                     "cost_xb_kernel (statistics, costs, pad rows and guide in one launch)", "bound": "hbm",
                      "achieved": cost_bytes / (cost_launch_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "avg_launch_ms": cost_launch_ms, "launches": cost_n,
                      "algorithmic": "read both images once, write the cost volume once",
-                     "traffic": _traffic_for(os.path.join(csrc, "fbs_cost.cu"), "cost_kernel")}
+                     "traffic": _traffic_for(os.path.join(csrc, "fbs_cost.cu"), cost_kernel)}
     roofline_cost["frac"] = roofline_cost["achieved"] / roofline_cost["peak"]
 
     e2e = None

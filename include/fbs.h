@@ -179,7 +179,7 @@ typedef struct {
  *   Every pair needs D <= 256 and radius <= 24 (FBS_ERR_UNSUPPORTED
  *   otherwise).  Scratch: every pair's 16-bit volume at once (sum of
  *   H*ceil(W/8)*8*Dp*2 bytes, Dp = round_up(D,16) (+16 when that stays <= 256),
- *   plus statistics and the packed guide).
+ *   plus the packed guide).
  *   A branched graph holds the pairs' addresses: a new set of buffers
  *   captures a new graph (the context keeps up to 32).
  * The first call of a new shape (the list of H, W, C, D, radius, the cost

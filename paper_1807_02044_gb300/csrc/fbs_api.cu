@@ -26,20 +26,15 @@ fbs_status run_path_tc(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, 
         return fail(ctx, FBS_ERR_UNSUPPORTED, "tensor-core aggregation supports D <= 256 and radius <= 24 (got D=%d, radius=%d)",
                     D, radius);
     const bool bf16 = ctx->opt.prec == FBS_PREC_BF16;
-    const size_t stats = fbs::cost_scratch_bytes(H, W);
+    // scratch: [packed guide | 16-bit x-blocked volume]; the cost kernel writes both
     const size_t rgbx = fbs::rgbx_bytes(H, W);
-    const size_t need = stats + rgbx + fbs::xblock16_bytes(H, W, D);
+    const size_t need = rgbx + fbs::xblock16_bytes(H, W, D);
     fbs_status s = ensure(ctx, &ctx->ws, &ctx->ws_bytes, need, "cost volume");
     if (s != FBS_OK) return s;
-    fbs::CostScratch sc = fbs::carve_cost_scratch(ctx->ws, H, W);
-    sc.rgbx = (uint2*)((uint8_t*)ctx->ws + stats);   // written by the statistics pre-pass (NCC)
-    void* cost = (uint8_t*)ctx->ws + stats + rgbx;
-    cudaError_t e = cudaSuccess;
-    if (ctx->opt.cost != FBS_COST_NCC) {
-        LaunchScope ls(ctx, FBS_KERNEL_OTHER, st);
-        e = fbs::launch_pack_rgbx(left, H, W, C, sc.rgbx, st);
-    }
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "guide packing launch");
+    fbs::CostScratch sc{};
+    sc.rgbx = (uint2*)ctx->ws;
+    void* cost = (uint8_t*)ctx->ws + rgbx;
+    cudaError_t e;
     {
         LaunchScope ls(ctx, FBS_KERNEL_COST, st);
         e = fbs::launch_cost_build_xblock16(sc, left, right, H, W, C, D, ctx->opt.cost, tau, bf16, cost, st);

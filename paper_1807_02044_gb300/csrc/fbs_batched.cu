@@ -13,8 +13,9 @@
 //
 // Branched plans (every precision): each pair runs the launches of the
 // single-pair form over its own slice of one scratch that holds every pair's
-// volume -- FP32: statistics, cost volume, aggregation; BF16 / FP16: pad rows,
-// statistics, 16-bit cost volume, tcgen05 aggregation.  The graph has 1, 2
+// volume -- FP32: statistics, cost volume, aggregation; BF16 / FP16: 16-bit
+// cost volume (statistics, pad rows and packed guide in the same kernel),
+// tcgen05 aggregation.  The graph has 1, 2
 // or 4 independent branches; pairs go, largest first, to the branch with the
 // least work so far, so one pair's memory-bound cost build overlaps another's
 // aggregation and small pairs fill the SMs a large pair's last wave leaves
@@ -262,14 +263,13 @@ fbs_status run_plan(fbs_ctx* ctx, const std::string& sig, int n, const fbs_pair*
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Scratch of one pair.  Tensor cores: [statistics | packed guide | 16-bit
-// x-blocked volume]; FP32: [statistics | FP32 volume, row pitch padded_ld(D)].
+// Scratch of one pair.  Tensor cores: [packed guide | 16-bit x-blocked
+// volume]; FP32: [statistics | FP32 volume, row pitch padded_ld(D)].
 size_t pair_bytes(const fbs_pair& q, bool tc)
 {
     if (!tc) return align256(fbs::cost_scratch_bytes(q.H, q.W)) +
                     align256(sizeof(float) * (size_t)q.H * q.W * fbs::padded_ld(q.D));
-    return align256(fbs::cost_scratch_bytes(q.H, q.W)) + align256(fbs::rgbx_bytes(q.H, q.W)) +
-           align256(fbs::xblock16_bytes(q.H, q.W, q.D));
+    return align256(fbs::rgbx_bytes(q.H, q.W)) + align256(fbs::xblock16_bytes(q.H, q.W, q.D));
 }
 
 fbs_status ensure_branches(fbs_ctx* ctx)
@@ -313,10 +313,10 @@ fbs_status build_branch_graph(fbs_ctx* ctx, int n, const fbs_pair* pairs, int nb
         cudaStream_t s = b == 0 ? cs : ctx->bbranch[b - 1];
         uint8_t* base = (uint8_t*)ctx->ws + off;
         off += pair_bytes(q, tc);
-        const size_t stats = align256(fbs::cost_scratch_bytes(q.H, q.W));
-        fbs::CostScratch sc = fbs::carve_cost_scratch(base, q.H, q.W);
         long long k0 = fbs::launch_count();
         if (!tc) {
+            const size_t stats = align256(fbs::cost_scratch_bytes(q.H, q.W));
+            const fbs::CostScratch sc = fbs::carve_cost_scratch(base, q.H, q.W);
             const int ld = fbs::padded_ld(q.D);
             float* cost = (float*)(base + stats);
             e = fbs::launch_cost_build(sc, q.left, q.right, q.H, q.W, q.C, q.D, ld, mode, q.tau, cost, s);
@@ -328,15 +328,10 @@ fbs_status build_branch_graph(fbs_ctx* ctx, int n, const fbs_pair* pairs, int nb
             g->kernels[FBS_KERNEL_AGG_F32] += fbs::launch_count() - k0;
             continue;
         }
-        sc.rgbx = (uint2*)(base + stats);
-        void* cost = base + stats + align256(fbs::rgbx_bytes(q.H, q.W));
-        if (mode != FBS_COST_NCC) {
-            e = fbs::launch_pack_rgbx(q.left, q.H, q.W, q.C, sc.rgbx, s);
-            g->kernels[FBS_KERNEL_OTHER] += fbs::launch_count() - k0;
-            k0 = fbs::launch_count();
-        }
-        if (e == cudaSuccess)
-            e = fbs::launch_cost_build_xblock16(sc, q.left, q.right, q.H, q.W, q.C, q.D, mode, q.tau, bf16, cost, s);
+        fbs::CostScratch sc{};
+        sc.rgbx = (uint2*)base;
+        void* cost = base + align256(fbs::rgbx_bytes(q.H, q.W));
+        e = fbs::launch_cost_build_xblock16(sc, q.left, q.right, q.H, q.W, q.C, q.D, mode, q.tau, bf16, cost, s);
         g->kernels[FBS_KERNEL_COST] += fbs::launch_count() - k0;
         k0 = fbs::launch_count();
         if (e == cudaSuccess)

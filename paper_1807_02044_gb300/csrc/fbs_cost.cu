@@ -10,22 +10,25 @@
 // zero variance gives c = 0.
 //
 // As in the paper (Sec. II-A, Sec. III) the per-pixel block statistics are
-// computed once per image by a pre-pass (grey_stats_kernel: g, S and
-// 1/sqrt(nQ - S^2)), so the per-(p, d) work is the dot product P.  In the cost
-// kernel a thread owns a run of 4 pixels and 8 consecutive disparities: the
-// left 3x6 grey window stays in registers, the right window slides by one
-// column per disparity (3 new values), the three column products per output
-// column are summed with a sliding 3-column window, and the normaliser of
-// the right block slides the same way -- about 15 instructions per (p, d).
-// Results are staged in shared memory as [d][x] and written out coalesced in
-// either layout:
-//   * [H][W][ld] float32 (D innermost; the FP32 aggregation), padding d in
-//     [D, ld) written as 0;
-//   * 16-bit x-blocked [H][ceil(W/8)][D][8] (the tensor-core aggregation):
-//     for a row y and a block of 8 columns, the D x 8 block is contiguous, so
-//     the tensor-core kernel's TMA reads contiguous 16*D-byte blocks that land
-//     as K-major core matrices (8 columns x 8 disparities, 128 bytes); columns
-//     x >= W of the last block are written as 0.
+// computed once per pixel, so the per-(p, d) work is the dot product P.  Two
+// kernels write the two layouts:
+//   * cost_kernel, [H][W][ld] float32 (D innermost; the FP32 aggregation),
+//     padding d in [D, ld) written as 0.  A pre-pass (grey_stats_kernel: g, S,
+//     1/sqrt(nQ - S^2)) fills statistics planes; a thread owns a run of 4
+//     pixels and 8 consecutive disparities (left 3x6 grey window in
+//     registers, right window sliding one column per disparity, three column
+//     products per output column summed by a sliding 3-column window);
+//     results are staged in shared memory as [d][x] and written out with D
+//     innermost.
+//   * cost_xb_kernel, 16-bit x-blocked [H][ceil(W/8)][Dp][8] (the tensor-core
+//     aggregation): for a row y and a block of 8 columns, the Dp x 8 block is
+//     contiguous, so the tensor-core kernel's TMA reads contiguous blocks that
+//     land as K-major core matrices; columns x >= W of the last block are 0.
+//     One launch computes the statistics of the rows it stages, the costs
+//     (8 pixels x 8 disparities per thread), the pad rows D .. Dp-1 and the
+//     left image's packed guide.
+// Both round the normalisation the same way (ncc_cost), so the 16-bit volume
+// equals the FP32 volume rounded to 16 bits.
 //
 // TAD (not in the paper): C = min(mean_c |I_l(u,v) - I_r(u-d,v)|, tau), tau
 // when u - d < 0.
@@ -53,6 +56,14 @@ __device__ __forceinline__ int rpos(int c) { return (c & 3) * kQR + (c >> 2); }
 __device__ __forceinline__ int spos(int c) { return (c & 3) * kQS + (c >> 2); }
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// C = 1 - c with c = num * (rv_l * rv_r): one rounded product of the two
+// normalisers, then one fused multiply-add (every cost kernel uses this, so the
+// FP32 and the 16-bit volumes hold the same values before the 16-bit rounding).
+__device__ __forceinline__ float ncc_cost(int num, float rv_l, float rv_r)
+{
+    return __fmaf_rn(-__int2float_rn(num), __fmul_rn(rv_l, rv_r), 1.f);
+}
 
 // Per-pixel statistics of one image: g = channel sum, S = 3x3 box sum of g
 // (clamped), rv = 1/sqrt(9 Q - S^2) or 0 for a flat block.
@@ -130,27 +141,23 @@ template <>
 __device__ __forceinline__ __half to_out<__half>(float v) { return __float2half_rn(v); }
 
 template <typename T>
-__device__ __forceinline__ void store8(T* o, const T (&v)[8])
+__device__ __forceinline__ uint4 pack8(const T (&v)[8])
 {
-    if (sizeof(T) == 2) {
-        uint32_t w[4];
+    static_assert(sizeof(T) == 2, "16-bit values");
+    uint32_t w[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-            w[c] = (uint32_t)*reinterpret_cast<const unsigned short*>(&v[2 * c]) |
-                   ((uint32_t)*reinterpret_cast<const unsigned short*>(&v[2 * c + 1]) << 16);
-        *reinterpret_cast<uint4*>(o) = make_uint4(w[0], w[1], w[2], w[3]);
-    } else {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) o[c] = v[c];
-    }
+    for (int c = 0; c < 4; ++c)
+        w[c] = (uint32_t)*reinterpret_cast<const unsigned short*>(&v[2 * c]) |
+               ((uint32_t)*reinterpret_cast<const unsigned short*>(&v[2 * c + 1]) << 16);
+    return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // MODE 0: NCC from the statistics planes; MODE 1: TAD from the raw images.
-// PLANAR false: out is [H][W][ld] (T = float); true: out is x-blocked [H][ld][D][8] with ld = ceil(W/8).
+// out is [H][W][ld] (T = float).
 // One row y and 128 pixels from x0, disparities [d_begin, d_end) (all: 0, D);
 // ends with a __syncthreads.  out_r (nullable, FP32 layout only): the right
 // view's volume, which holds the same costs at (x - d, y, d) (Sec. II-A, Sec. III).
-template <int MODE, typename T, bool PLANAR>
+template <int MODE, typename T>
 __device__ __forceinline__ void cost_tile(const int16_t* __restrict__ gplane, const int* __restrict__ splane,
                                           const float* __restrict__ rvplane, const uint8_t* __restrict__ L,
                                           const uint8_t* __restrict__ R, int H, int W, int C, int D, int ld, float tau,
@@ -283,7 +290,7 @@ __device__ __forceinline__ void cost_tile(const int16_t* __restrict__ gplane, co
                         cst = 2.f;
                     } else {
                         const int num = 9 * P - sli[i] * srw[i];
-                        cst = 1.f - (float)num * (rli[i] * rrw[i]);
+                        cst = ncc_cost(num, rli[i], rrw[i]);
                     }
                     st[32 * i] = cst;
                 }
@@ -311,54 +318,36 @@ __device__ __forceinline__ void cost_tile(const int16_t* __restrict__ gplane, co
         __syncthreads();
 
         const int nd = min(kDC, d_end - dc);
-        if (PLANAR) {
-            // out[((y*ld + xb)*D + d)*8 + xi]: one lane stores the 8 columns of a
-            // block for one disparity (16 bytes), a warp 32 consecutive disparities
-            const int nb = (nxs + 7) >> 3;
-            for (int i = tid; i < nb * nd; i += kThreads) {
-                const int b = i / nd, dd = i - b * nd;
-                const float* sp = stage + dd * kStage;
-                T v[8];
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int x = 8 * b + c;
-                    v[c] = to_out<T>(x < nxs ? sp[stage_pos(x)] : 0.f);
-                }
-                T* o = out + (((size_t)y * ld + (x0 >> 3) + b) * tc_block_rows(D) + dc + dd) * 8;
-                store8(o, v);
-            }
-        } else {
-            // out[(y*W + x)*ld + d]; padding d in [D, ld) of the last pass written as 0
-            const int ndw = (dc + kDC >= d_end) ? (d_end == D ? ld - dc : d_end - dc) : kDC;
-            const int warp = tid >> 5, lane = tid & 31;
-            for (int x = warp; x < nxs; x += kThreads / 32) {
-                T* o = out + ((size_t)y * W + x0 + x) * ld + dc;
-                const int px = stage_pos(x);
-                for (int dd = lane; dd < ndw; dd += 32) o[dd] = to_out<T>(dd < nd ? stage[dd * kStage + px] : 0.f);
-            }
-            if (out_r != nullptr) {
-                // right pixel xr = x - d receives the contiguous disparities
-                // max(dc, x0 - xr) .. min(dc + nd - 1, x0 + nxs - 1 - xr) of this pass
-                const int xr_lo = max(0, x0 - dc - nd + 1), xr_hi = x0 + nxs - 1 - dc;
-                for (int xr = xr_lo + warp; xr <= xr_hi; xr += kThreads / 32) {
-                    const int dlo = max(dc, x0 - xr), dhi = min(dc + nd - 1, x0 + nxs - 1 - xr);
-                    float* o = out_r + ((size_t)y * W + xr) * ld;
-                    for (int d = dlo + lane; d <= dhi; d += 32) o[d] = stage[(d - dc) * kStage + stage_pos(xr + d - x0)];
-                }
+        // out[(y*W + x)*ld + d]; padding d in [D, ld) of the last pass written as 0
+        const int ndw = (dc + kDC >= d_end) ? (d_end == D ? ld - dc : d_end - dc) : kDC;
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int x = warp; x < nxs; x += kThreads / 32) {
+            T* o = out + ((size_t)y * W + x0 + x) * ld + dc;
+            const int px = stage_pos(x);
+            for (int dd = lane; dd < ndw; dd += 32) o[dd] = to_out<T>(dd < nd ? stage[dd * kStage + px] : 0.f);
+        }
+        if (out_r != nullptr) {
+            // right pixel xr = x - d receives the contiguous disparities
+            // max(dc, x0 - xr) .. min(dc + nd - 1, x0 + nxs - 1 - xr) of this pass
+            const int xr_lo = max(0, x0 - dc - nd + 1), xr_hi = x0 + nxs - 1 - dc;
+            for (int xr = xr_lo + warp; xr <= xr_hi; xr += kThreads / 32) {
+                const int dlo = max(dc, x0 - xr), dhi = min(dc + nd - 1, x0 + nxs - 1 - xr);
+                float* o = out_r + ((size_t)y * W + xr) * ld;
+                for (int d = dlo + lane; d <= dhi; d += 32) o[d] = stage[(d - dc) * kStage + stage_pos(xr + d - x0)];
             }
         }
         __syncthreads();
     }
 }
 
-template <int MODE, typename T, bool PLANAR>
+template <int MODE, typename T>
 __global__ void __launch_bounds__(kThreads)
 cost_kernel(const int16_t* __restrict__ gplane, const int* __restrict__ splane, const float* __restrict__ rvplane,
             const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int H, int W, int C, int D, int ld,
             float tau, T* __restrict__ out)
 {
     extern __shared__ int smem_i[];
-    cost_tile<MODE, T, PLANAR>(gplane, splane, rvplane, L, R, H, W, C, D, ld, tau, out, blockIdx.x * kXS, blockIdx.y,
+    cost_tile<MODE, T>(gplane, splane, rvplane, L, R, H, W, C, D, ld, tau, out, blockIdx.x * kXS, blockIdx.y,
                                smem_i, 0, D);
 }
 
@@ -379,10 +368,10 @@ cost_batched_kernel(const BatchPair* __restrict__ pairs, int npairs, int nitems,
         const int nseg = (bp.W + kXS - 1) / kXS;
         const int x0 = (t % nseg) * kXS, y = t / nseg;
         if (bp.mode == 0)
-            cost_tile<0, float, false>(bp.sc.g, bp.sc.s, bp.sc.rv, bp.left, bp.right, bp.H, bp.W, bp.C, bp.D, bp.ld,
+            cost_tile<0, float>(bp.sc.g, bp.sc.s, bp.sc.rv, bp.left, bp.right, bp.H, bp.W, bp.C, bp.D, bp.ld,
                                        bp.tau, bp.cost, x0, y, smem_i, 0, bp.D);
         else
-            cost_tile<1, float, false>(bp.sc.g, bp.sc.s, bp.sc.rv, bp.left, bp.right, bp.H, bp.W, bp.C, bp.D, bp.ld,
+            cost_tile<1, float>(bp.sc.g, bp.sc.s, bp.sc.rv, bp.left, bp.right, bp.H, bp.W, bp.C, bp.D, bp.ld,
                                        bp.tau, bp.cost, x0, y, smem_i, 0, bp.D);
     }
 }
@@ -423,7 +412,7 @@ cost_band_kernel(const int16_t* __restrict__ gplane, const int* __restrict__ spl
     __syncthreads();
     const int d_begin = lo_s, d_end = hi_s;
     if (d_begin >= d_end) return;
-    cost_tile<0, float, false>(gplane, splane, rvplane, nullptr, nullptr, H, W, 1, D, ld, 0.f, out, x0, y, smem_i,
+    cost_tile<0, float>(gplane, splane, rvplane, nullptr, nullptr, H, W, 1, D, ld, 0.f, out, x0, y, smem_i,
                                d_begin, d_end);
 }
 
@@ -436,7 +425,7 @@ cost_lr_kernel(const int16_t* __restrict__ gplane, const int* __restrict__ splan
                float tau, float* __restrict__ out, float* __restrict__ out_r)
 {
     extern __shared__ int smem_i[];
-    cost_tile<MODE, float, false>(gplane, splane, rvplane, L, R, H, W, C, D, ld, tau, out, blockIdx.x * kXS, blockIdx.y,
+    cost_tile<MODE, float>(gplane, splane, rvplane, L, R, H, W, C, D, ld, tau, out, blockIdx.x * kXS, blockIdx.y,
                                   smem_i, 0, D, out_r);
 }
 
@@ -454,23 +443,314 @@ __global__ void right_edge_fill_kernel(int H, int W, int D, int ld, float maxc, 
     }
 }
 
+// ---- 16-bit x-blocked volume: one thread per (block of 8 columns, 8 disparities)
+//
+// The layout [H][ceil(W/8)][Dp][8] keeps the 8 columns of a block contiguous
+// for each d, so a thread that owns one block and 8 consecutive disparities
+// computes the 8 x 8 costs in registers, one 16-byte row per d.  Lanes own
+// consecutive disparity groups of a block; the warp passes its 256 rows
+// through a private shared-memory buffer so that each store instruction
+// writes 32 consecutive rows (512 contiguous bytes within a block).  The left 3x10 grey window and the left
+// statistics stay in registers; the right window (3x10 values and 8 block
+// statistics) slides one column per disparity, 5 new shared-memory values.
+// Per (p, d): three multiply-adds per column product shared by three pixels,
+// the sliding 3-column sum, the numerator and ncc_cost -- about 10
+// instructions.  Staged rows use a skewed index c + c/8, so lanes reading
+// columns 8 apart hit different banks.
+constexpr int kXbThreads = 256;
+
+__device__ __forceinline__ int skew(int c) { return c + (c >> 3); }
+__host__ __device__ inline int skew_len(int n) { return n + (n - 1) / 8; }
+
+__host__ __device__ inline int xb_blocks_per_cta(int D)
+{
+    const int ndg = (D + 7) / 8;
+    const int b = kXbThreads / ndg;
+    return b < 32 ? b : 32;
+}
+
+// Per-warp output buffer: 256 rows of 16 bytes, row r at r + r/8 (conflict-free
+// both when lanes write their 8 rows and when the warp reads 32 consecutive rows).
+constexpr int kXbWarpRows = 256 + 32;
+
+__host__ __device__ inline size_t cost_xb_stage_ints(int mode, int D)
+{
+    const int npx = 8 * xb_blocks_per_cta(D);
+    const int Ll = skew_len(npx + 2), Lr = skew_len(npx + D + 9), Lp = skew_len(npx);
+    const size_t n = mode == 0 ? (size_t)(3 * Ll + 3 * Lr + 2 * Lp + 2 * Lr) : (size_t)(Lp + Lr);
+    return (n + 3) & ~(size_t)3;   // the output buffers that follow are 16-byte aligned
+}
+
+template <int MODE, typename T>
+__global__ void __launch_bounds__(kXbThreads, 2)
+cost_xb_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int H, int W, int C, int D, float tau,
+               T* __restrict__ out, uint2* __restrict__ rgbx)
+{
+    extern __shared__ int sm_xb[];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int ndg = (D + 7) >> 3;
+    const int xbc = xb_blocks_per_cta(D);
+    const int nxb = (W + 7) >> 3;
+    const int xb0 = blockIdx.x * xbc;
+    const int y = blockIdx.y;
+    const int x0 = xb0 * 8;
+    const int npx = xbc * 8;
+    const int nl = npx + 2;            // left grey columns x0-1 .. x0+npx
+    // right columns x0-D-8 .. x0+npx (origin rb): the 8 extra columns keep every
+    // index of a thread's 8 disparities >= 0 also past D (those rows are not stored)
+    const int nr = npx + D + 9;
+    const int rb = x0 - D - 8;
+    const int Ll = skew_len(nl), Lr = skew_len(nr), Lp = skew_len(npx);
+
+    int* gl = sm_xb;                   // [3][Ll]
+    int* gr = gl + 3 * Ll;             // [3][Lr]
+    int* sl = gr + 3 * Lr;             // [Lp]
+    float* rl = (float*)(sl + Lp);     // [Lp]
+    int* sr = (int*)(rl + Lp);         // [Lr]
+    float* rr = (float*)(sr + Lr);     // [Lr]
+    uint32_t* pl = (uint32_t*)sm_xb;   // TAD: left pixels [Lp]
+    uint32_t* pr = pl + Lp;            // TAD: right pixels [Lr], origin rb
+
+    // staging: grey values (channel sums) of rows y-1..y+1 at clamped columns,
+    // then each staged block centre's statistics S, 1/sqrt(9Q - S^2) exactly as
+    // grey_stats_kernel computes them, and the left pixels' packed guide
+    auto grey = [&](const uint8_t* img, int yy, int x) -> int {
+        const uint8_t* q = img + ((size_t)yy * W + x) * C;
+        return C == 3 ? (int)q[0] + (int)q[1] + (int)q[2] : (int)q[0];
+    };
+    auto colour = [&](const uint8_t* img, int x) -> uint32_t {
+        const uint8_t* q = img + ((size_t)y * W + clampi(x, 0, W - 1)) * C;
+        return C == 3 ? (uint32_t)q[0] | ((uint32_t)q[1] << 8) | ((uint32_t)q[2] << 16) : (uint32_t)q[0];
+    };
+    if (MODE == 0) {
+        for (int c = tid; c < nl; c += nthr) {
+            const int x = clampi(x0 - 1 + c, 0, W - 1);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gl[j * Ll + skew(c)] = grey(L, clampi(y - 1 + j, 0, H - 1), x);
+        }
+        for (int c = tid; c < nr; c += nthr) {
+            const int x = clampi(rb + c, 0, W - 1);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gr[j * Lr + skew(c)] = grey(R, clampi(y - 1 + j, 0, H - 1), x);
+        }
+        __syncthreads();
+        auto stats = [&](const int* g, int Lg, int c, int* s_out, float* rv_out) {
+            int sum = 0, sq = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = -1; k <= 1; ++k) {
+                    const int v = g[j * Lg + skew(c + k)];
+                    sum += v;
+                    sq += v * v;
+                }
+            const int var = 9 * sq - sum * sum;
+            s_out[skew(c)] = sum;
+            rv_out[skew(c)] = var > 0 ? rsqrtf((float)var) : 0.f;
+        };
+        for (int i = tid; i < npx; i += nthr) {
+            // left centre x0 + i sits at staged column i + 1
+            int sum = 0, sq = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const int v = gl[j * Ll + skew(i + k)];
+                    sum += v;
+                    sq += v * v;
+                }
+            const int var = 9 * sq - sum * sum;
+            sl[skew(i)] = sum;
+            rl[skew(i)] = var > 0 ? rsqrtf((float)var) : 0.f;
+            if (x0 + i < W) {
+                const uint32_t col = colour(L, x0 + i);
+                rgbx[(size_t)y * rgbx_pitch(W) + x0 + i] = make_uint2(col, (uint32_t)__dp4a(col, col, 0u));
+            }
+        }
+        for (int c = 1 + tid; c < nr - 1; c += nthr) stats(gr, Lr, c, sr, rr);
+    } else {
+        for (int c = tid; c < npx; c += nthr) {
+            const uint32_t col = colour(L, x0 + c);
+            pl[skew(c)] = col;
+            if (x0 + c < W) rgbx[(size_t)y * rgbx_pitch(W) + x0 + c] = make_uint2(col, (uint32_t)__dp4a(col, col, 0u));
+        }
+        for (int c = tid; c < nr; c += nthr) pr[skew(c)] = colour(R, rb + c);
+    }
+    __syncthreads();
+
+    const int dg = tid % ndg, xbl = tid / ndg;
+    const int xb = xb0 + xbl;
+    // threads past xbc * ndg (the block is a whole number of warps) and blocks
+    // beyond the image compute nothing and store nothing
+    const bool active = xbl < xbc && xb < nxb;
+    const int d0 = 8 * dg;
+    const int xl = 8 * xbl;            // the block's first pixel, relative to x0
+    const int xbase = x0 + xl;
+    const int lane = tid & 31;
+    uint4* wbuf = (uint4*)(sm_xb + cost_xb_stage_ints(MODE, D)) + (size_t)(tid >> 5) * kXbWarpRows;
+    uint4* mine = wbuf + 9 * lane;     // rows 8*lane + s at 9*lane + s
+
+    if (!active) {
+    } else if (MODE == 0) {
+        int glw[3][10], grw[3][10], sli[8], srw[8];
+        float rli[8], rrw[8];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int c = 0; c < 10; ++c) glw[j][c] = gl[j * Ll + skew(xl + c)];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            sli[i] = sl[skew(xl + i)];
+            rli[i] = rl[skew(xl + i)];
+        }
+        // right block of (x, d) spans columns x-d-1 .. x-d+1: index (x - d - 1 + k) - rb
+        int base = xl - d0 - 1 + D + 8;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int c = 0; c < 10; ++c) grw[j][c] = gr[j * Lr + skew(base + c)];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            srw[i] = sr[skew(base + 1 + i)];
+            rrw[i] = rr[skew(base + 1 + i)];
+        }
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int d = d0 + s;
+            if (s > 0) {
+                // d grew by one: the window slides one column to the left
+                --base;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+#pragma unroll
+                    for (int c = 9; c > 0; --c) grw[j][c] = grw[j][c - 1];
+                    grw[j][0] = gr[j * Lr + skew(base)];
+                }
+#pragma unroll
+                for (int i = 7; i > 0; --i) {
+                    srw[i] = srw[i - 1];
+                    rrw[i] = rrw[i - 1];
+                }
+                srw[0] = sr[skew(base + 1)];
+                rrw[0] = rr[skew(base + 1)];
+            }
+            int cp[10];
+#pragma unroll
+            for (int c = 0; c < 10; ++c) cp[c] = glw[0][c] * grw[0][c] + glw[1][c] * grw[1][c] + glw[2][c] * grw[2][c];
+            int P = cp[0] + cp[1] + cp[2];
+            T v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (i > 0) P += cp[i + 2] - cp[i - 1];
+                const int x = xbase + i;
+                float cst = ncc_cost(9 * P - sli[i] * srw[i], rli[i], rrw[i]);
+                cst = x - d < 0 ? 2.f : cst;
+                v[i] = to_out<T>(x < W ? cst : 0.f);
+            }
+            mine[s] = pack8(v);
+        }
+    } else {
+        const float inv_c = 1.f / (float)C;
+        uint32_t pli[8], prw[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) pli[i] = pl[skew(xl + i)];
+        // right pixel of (x, d): index (x - d) - rb
+        int base = xl - d0 + D + 8;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) prw[i] = pr[skew(base + i)];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int d = d0 + s;
+            if (s > 0) {
+                --base;
+#pragma unroll
+                for (int i = 7; i > 0; --i) prw[i] = prw[i - 1];
+                prw[0] = pr[skew(base)];
+            }
+            T v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int x = xbase + i;
+                const int sad = (int)__dp4a(__vabsdiffu4(pli[i], prw[i]), 0x01010101u, 0u);
+                const float cst = x - d < 0 ? tau : fminf((float)sad * inv_c, tau);
+                v[i] = to_out<T>(x < W ? cst : 0.f);
+            }
+            mine[s] = pack8(v);
+        }
+    }
+    // write-out: entry e = 32k + lane is row s = e % 8 of lane e / 8 (its block
+    // xbl and group dg come by shuffle); rows d >= D and inactive lanes are skipped
+    __syncwarp();
+    const int Dp = tc_block_rows(D);
+    const int code = active ? (xbl << 8) | dg : -1;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int e = 32 * k + lane;
+        const int src = __shfl_sync(0xffffffffu, code, e >> 3);
+        const int s = e & 7;
+        if (src >= 0 && 8 * (src & 255) + s < D) {
+            const int xbs = xb0 + (src >> 8);
+            const uint4 row = wbuf[e + (e >> 3)];
+            *(uint4*)(out + (((size_t)y * nxb + xbs) * Dp + 8 * (src & 255) + s) * 8) = row;
+        }
+    }
+    // rows D .. Dp-1 of the CTA's blocks: zero, except row round_up(D,16) all
+    // ones when the normaliser rides with the volume
+    const int extra = Dp - D;
+    if (extra > 0) {
+        const int n16 = (D + 15) / 16 * 16;
+        const T one1[2] = {to_out<T>(1.f), to_out<T>(1.f)};
+        const uint32_t ones = *reinterpret_cast<const uint32_t*>(one1);
+        const int nb = min(xbc, nxb - xb0);
+        for (int i = tid; i < nb * extra; i += nthr) {
+            const int b = i / extra, d = D + (i - b * extra);
+            const uint32_t v = (d == n16 && Dp > n16) ? ones : 0u;
+            *(uint4*)(out + (((size_t)y * nxb + xb0 + b) * Dp + d) * 8) = make_uint4(v, v, v, v);
+        }
+    }
+}
+
+size_t cost_xb_smem_bytes(int mode, int D)
+{
+    const int nwarps = (xb_blocks_per_cta(D) * ((D + 7) / 8) + 31) / 32;
+    return sizeof(int) * cost_xb_stage_ints(mode, D) + (size_t)nwarps * kXbWarpRows * 16;
+}
+
+template <int MODE, typename T>
+cudaError_t launch_cost_xb(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H, int W, int C,
+                           int D, float tau, T* out, cudaStream_t stream)
+{
+    const int ndg = (D + 7) / 8;
+    const int xbc = xb_blocks_per_cta(D);
+    const size_t smem = cost_xb_smem_bytes(MODE, D);
+    cudaError_t e = cudaFuncSetAttribute(cost_xb_kernel<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nxb = (W + 7) / 8;
+    dim3 grid((nxb + xbc - 1) / xbc, H);
+    fbs::note_launch();
+    const int nthr = (xbc * ndg + 31) / 32 * 32;   // whole warps (the write-out shuffles need all lanes)
+    cost_xb_kernel<MODE, T><<<grid, nthr, smem, stream>>>(left, right, H, W, C, D, tau, out, sc.rgbx);
+    return cudaGetLastError();
+}
+
 size_t cost_smem_bytes()
 {
     return sizeof(float) * (size_t)kDC * kStage +
            sizeof(int) * (size_t)(3 * (kXS + 2) + 3 * 4 * kQR + 2 * kXS + 2 * (kXS + kDC));
 }
 
-template <int MODE, typename T, bool PLANAR>
+template <int MODE, typename T>
 cudaError_t launch_cost_kernel(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H, int W,
                                int C, int D, int ld, float tau, T* out, cudaStream_t stream)
 {
     const size_t smem = cost_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(cost_kernel<MODE, T, PLANAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(cost_kernel<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((W + kXS - 1) / kXS, H);
     fbs::note_launch();
-    cost_kernel<MODE, T, PLANAR><<<grid, kThreads, smem, stream>>>(sc.g, sc.s, sc.rv, left, right, H, W, C, D, ld,
+    cost_kernel<MODE, T><<<grid, kThreads, smem, stream>>>(sc.g, sc.s, sc.rv, left, right, H, W, C, D, ld,
                                                                    tau, out);
     return cudaGetLastError();
 }
@@ -558,9 +838,9 @@ cudaError_t launch_cost_build(const CostScratch& sc, const uint8_t* left, const 
     if (mode == 0) {
         cudaError_t e = launch_stats(sc, left, right, H, W, C, stream);
         if (e != cudaSuccess) return e;
-        return launch_cost_kernel<0, float, false>(sc, left, right, H, W, C, D, ld, tau, cost, stream);
+        return launch_cost_kernel<0, float>(sc, left, right, H, W, C, D, ld, tau, cost, stream);
     }
-    return launch_cost_kernel<1, float, false>(sc, left, right, H, W, C, D, ld, tau, cost, stream);
+    return launch_cost_kernel<1, float>(sc, left, right, H, W, C, D, ld, tau, cost, stream);
 }
 
 cudaError_t launch_cost_band(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H, int W,
@@ -612,20 +892,13 @@ cudaError_t launch_cost_build_xblock16(const CostScratch& sc, const uint8_t* lef
                                        int W, int C, int D, int mode, float tau, bool bf16, void* cost,
                                        cudaStream_t stream)
 {
-    const int nxb = (W + 7) / 8;
-    cudaError_t pe = launch_xblock16_pad_rows(H, W, D, bf16, cost, stream);
-    if (pe != cudaSuccess) return pe;
-    if (mode == 0) {
-        cudaError_t e = launch_stats(sc, left, right, H, W, C, stream);
-        if (e != cudaSuccess) return e;
-        return bf16 ? launch_cost_kernel<0, __nv_bfloat16, true>(sc, left, right, H, W, C, D, nxb, tau,
-                                                                 (__nv_bfloat16*)cost, stream)
-                    : launch_cost_kernel<0, __half, true>(sc, left, right, H, W, C, D, nxb, tau, (__half*)cost,
-                                                          stream);
-    }
-    return bf16 ? launch_cost_kernel<1, __nv_bfloat16, true>(sc, left, right, H, W, C, D, nxb, tau,
-                                                             (__nv_bfloat16*)cost, stream)
-                : launch_cost_kernel<1, __half, true>(sc, left, right, H, W, C, D, nxb, tau, (__half*)cost, stream);
+    // one launch: statistics, costs, pad rows and the packed guide (sc.rgbx)
+    if (D > 256 || !sc.rgbx) return cudaErrorInvalidValue;   // serves the tensor-core form only
+    if (mode == 0)
+        return bf16 ? launch_cost_xb<0>(sc, left, right, H, W, C, D, tau, (__nv_bfloat16*)cost, stream)
+                    : launch_cost_xb<0>(sc, left, right, H, W, C, D, tau, (__half*)cost, stream);
+    return bf16 ? launch_cost_xb<1>(sc, left, right, H, W, C, D, tau, (__nv_bfloat16*)cost, stream)
+                : launch_cost_xb<1>(sc, left, right, H, W, C, D, tau, (__half*)cost, stream);
 }
 
 }  // namespace fbs

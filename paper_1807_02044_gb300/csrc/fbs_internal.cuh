@@ -50,7 +50,9 @@ cudaError_t launch_cost_build_lr(const CostScratch& sc, const uint8_t* left, con
 // zero, and (when Dp > round_up(D,16)) row round_up(D,16) all ones followed by
 // zero rows -- the ones row lets the tensor-core product also form the sum of
 // the weights.  Columns x >= W of the last block are 0.  bf16 selects
-// __nv_bfloat16, otherwise __half.
+// __nv_bfloat16, otherwise __half.  One kernel, which also writes the left
+// image's packed guide to sc.rgbx (required; the statistics planes of sc are
+// not used).  D <= 256.
 __host__ __device__ inline int tc_block_rows(int D)
 {
     const int n = (D + 15) / 16 * 16;
