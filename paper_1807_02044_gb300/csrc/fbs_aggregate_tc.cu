@@ -50,6 +50,7 @@ constexpr int kTH = 8;          // tile height
 constexpr int kM = kTW * kTH;   // 128 = MMA M = TMEM lanes
 constexpr int kProducerWarps = 16;                 // warps 0-15
 constexpr int kPasses = 32 / kProducerWarps;       // 32 pixel groups of 4 per tile
+static_assert(kPasses == 2, "the producers' passes of a warp share one pixel row (warp >> 1)");
 constexpr int kEpiWarp0 = kProducerWarps;          // 4 epilogue warps: TMEM lane quarters 0-3
 constexpr int kEpilogue = 128;
 constexpr int kTmaWarp = kEpiWarp0 + 4;
@@ -375,27 +376,34 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                     const int hr = h0 + r;
                     uint8_t* arow = a_base + s * a_stage + r * a_row;
                     const uint2* grow = gt + hr * KW;
+                    // both passes of a warp cover pixel row warp >> 1, so the row
+                    // offset, its window test and the spatial y-term are shared
+                    const int dy = hr - p.rho - pty[0];
+                    const bool act = dy >= -p.rho && dy <= p.rho;   // uniform over the warp
+                    const float sy = (float)(dy * dy) * p.neg_ks;
+                    const uint64_t syp = f2_pack(sy, sy);
+                    if (act) {
 #pragma unroll
-                    for (int i = 0; i < kPasses; ++i) {
-                        const int dy = hr - p.rho - pty[i];
-                        const bool act = dy >= -p.rho && dy <= p.rho;   // uniform over the pass
-                        const float sy = (float)(dy * dy) * p.neg_ks;
-                        const uint64_t syp = f2_pack(sy, sy);
+                        for (int i = 0; i < kPasses; ++i) {
 #pragma unroll
-                        for (int pg = 0; pg < NG; ++pg) {
-                            if (!on[i][pg]) continue;
-                            uint32_t packed = 0;
-                            if (act) {
+                            for (int pg = 0; pg < NG; ++pg) {
+                                if (!on[i][pg]) continue;
                                 const uint4 q = *(const uint4*)(grow + kk[i][pg]);
                                 const uint32_t e0 = q.y + pp[i] - 2u * __dp4a(q.x, pcol[i], 0u);
                                 const uint32_t e1 = q.w + pp[i] - 2u * __dp4a(q.z, pcol[i], 0u);
                                 const uint64_t c = f2_add(u2_pack(e0, e1), magic2);
                                 float a0, a1;
                                 f2_unpack(f2_fma(c, nkr2, f2_add(sxp[i][pg], syp)), a0, a1);
-                                packed = pack2<BF16>(ex2_approx(a0), ex2_approx(a1));
+                                *(uint32_t*)(arow + aoff[i][pg]) = pack2<BF16>(ex2_approx(a0), ex2_approx(a1));
                             }
-                            *(uint32_t*)(arow + aoff[i][pg]) = packed;
                         }
+                    } else {
+                        // the window row is outside this pixel row's window: zero weights
+#pragma unroll
+                        for (int i = 0; i < kPasses; ++i)
+#pragma unroll
+                            for (int pg = 0; pg < NG; ++pg)
+                                if (on[i][pg]) *(uint32_t*)(arow + aoff[i][pg]) = 0u;
                     }
                 }
                 fence_proxy_async();
