@@ -38,6 +38,7 @@
 #include <cuda_fp16.h>
 
 #include "fbs_internal.cuh"
+#include "packed_f32.cuh"
 #include "tc_ptx.cuh"
 
 namespace fbs {
@@ -157,49 +158,9 @@ __device__ __forceinline__ void raise_abort(volatile uint32_t* abort_flag, int* 
     atomicCAS(err, 0, code);
 }
 
-// Packed FP32 pairs (f32x2: one instruction, two IEEE round-to-nearest lanes).
-__device__ __forceinline__ uint64_t f2_pack(float lo, float hi)
-{
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ uint64_t u2_pack(uint32_t lo, uint32_t hi)
-{
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b)
-{
-    uint64_t d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
-{
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
 // 2^23 as an FP32 bit pattern: for 0 <= c < 2^23 the pattern kMagic + c is the
 // float 2^23 + c exactly, so subtracting 2^23 gives float(c) exactly.
 constexpr uint32_t kMagic = 0x4B000000u;
-
-template <bool BF16>
-__device__ __forceinline__ uint32_t pack2(float lo, float hi)
-{
-    uint32_t r;
-    if (BF16)
-        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-    else
-        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-    return r;
-}
 
 // Warp roles: 0-15 weight producers, 16-19 epilogue (TMEM lane quarters 0-3),
 // 20 TMA producer (guide tiles and cost rows), 21 MMA issuer.  NG = number of
@@ -394,7 +355,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                                 const uint64_t c = f2_add(u2_pack(e0, e1), magic2);
                                 float a0, a1;
                                 f2_unpack(f2_fma(c, nkr2, f2_add(sxp[i][pg], syp)), a0, a1);
-                                *(uint32_t*)(arow + aoff[i][pg]) = pack2<BF16>(ex2_approx(a0), ex2_approx(a1));
+                                *(uint32_t*)(arow + aoff[i][pg]) = pack_16x2<BF16>(ex2_approx(a0), ex2_approx(a1));
                             }
                         }
                     } else {

@@ -35,7 +35,10 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "fbs_internal.cuh"
+#include "packed_f32.cuh"
 
 namespace fbs {
 namespace {
@@ -279,20 +282,12 @@ __device__ __forceinline__ void cost_tile(const int16_t* __restrict__ gplane, co
                 int cp[6];
 #pragma unroll
                 for (int c = 0; c < 6; ++c) cp[c] = glw[0][c] * grw[0][c] + glw[1][c] * grw[1][c] + glw[2][c] * grw[2][c];
-                int P = cp[0] + cp[1] + cp[2];
                 float* st = stage + (d - dc) * kStage + run;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    if (i > 0) P += cp[i + 2] - cp[i - 1];
                     const int x = x0 + xl0 + i;
-                    float cst;
-                    if (x - d < 0) {
-                        cst = 2.f;
-                    } else {
-                        const int num = 9 * P - sli[i] * srw[i];
-                        cst = ncc_cost(num, rli[i], rrw[i]);
-                    }
-                    st[32 * i] = cst;
+                    const int num = 9 * (cp[i] + cp[i + 1] + cp[i + 2]) - sli[i] * srw[i];
+                    st[32 * i] = x - d < 0 ? 2.f : ncc_cost(num, rli[i], rrw[i]);
                 }
             }
         } else {
@@ -587,6 +582,7 @@ cost_xb_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int
     const int xl = 8 * xbl;            // the block's first pixel, relative to x0
     const int xbase = x0 + xl;
     const int lane = tid & 31;
+    constexpr bool kBf16 = std::is_same<T, __nv_bfloat16>::value;
     uint4* wbuf = (uint4*)(sm_xb + cost_xb_stage_ints(MODE, D)) + (size_t)(tid >> 5) * kXbWarpRows;
     uint4* mine = wbuf + 9 * lane;     // rows 8*lane + s at 9*lane + s
 
@@ -614,41 +610,65 @@ cost_xb_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int
             srw[i] = sr[skew(base + 1 + i)];
             rrw[i] = rr[skew(base + 1 + i)];
         }
+        // the normalisation of a pixel pair is one packed multiply and one packed
+        // FMA (per lane exactly ncc_cost); threads whose 8 pixels are inside the
+        // image and match inside it for all 8 disparities skip the two masks
+        const uint64_t ones2 = f2_pack(1.f, 1.f);
+        auto sweep = [&](auto masked) {
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const int d = d0 + s;
-            if (s > 0) {
-                // d grew by one: the window slides one column to the left
-                --base;
+            for (int s = 0; s < 8; ++s) {
+                const int d = d0 + s;
+                if (s > 0) {
+                    // d grew by one: the window slides one column to the left
+                    --base;
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
+                    for (int j = 0; j < 3; ++j) {
 #pragma unroll
-                    for (int c = 9; c > 0; --c) grw[j][c] = grw[j][c - 1];
-                    grw[j][0] = gr[j * Lr + skew(base)];
+                        for (int c = 9; c > 0; --c) grw[j][c] = grw[j][c - 1];
+                        grw[j][0] = gr[j * Lr + skew(base)];
+                    }
+#pragma unroll
+                    for (int i = 7; i > 0; --i) {
+                        srw[i] = srw[i - 1];
+                        rrw[i] = rrw[i - 1];
+                    }
+                    srw[0] = sr[skew(base + 1)];
+                    rrw[0] = rr[skew(base + 1)];
                 }
+                int cp[10];
 #pragma unroll
-                for (int i = 7; i > 0; --i) {
-                    srw[i] = srw[i - 1];
-                    rrw[i] = rrw[i - 1];
+                for (int c = 0; c < 10; ++c)
+                    cp[c] = glw[0][c] * grw[0][c] + glw[1][c] * grw[1][c] + glw[2][c] * grw[2][c];
+                int P = cp[0] + cp[1] + cp[2];
+                int num[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    if (i > 0) P += cp[i + 2] - cp[i - 1];
+                    num[i] = 9 * P - sli[i] * srw[i];
                 }
-                srw[0] = sr[skew(base + 1)];
-                rrw[0] = rr[skew(base + 1)];
-            }
-            int cp[10];
+                uint32_t w[4];
 #pragma unroll
-            for (int c = 0; c < 10; ++c) cp[c] = glw[0][c] * grw[0][c] + glw[1][c] * grw[1][c] + glw[2][c] * grw[2][c];
-            int P = cp[0] + cp[1] + cp[2];
-            T v[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                if (i > 0) P += cp[i + 2] - cp[i - 1];
-                const int x = xbase + i;
-                float cst = ncc_cost(9 * P - sli[i] * srw[i], rli[i], rrw[i]);
-                cst = x - d < 0 ? 2.f : cst;
-                v[i] = to_out<T>(x < W ? cst : 0.f);
+                for (int q = 0; q < 4; ++q) {
+                    const uint64_t t = f2_mul(f2_pack(rli[2 * q], rli[2 * q + 1]), f2_pack(rrw[2 * q], rrw[2 * q + 1]));
+                    const uint64_t nn = f2_pack(-__int2float_rn(num[2 * q]), -__int2float_rn(num[2 * q + 1]));
+                    float c0, c1;
+                    f2_unpack(f2_fma(nn, t, ones2), c0, c1);
+                    if (decltype(masked)::value) {
+                        const int x = xbase + 2 * q;
+                        c0 = x - d < 0 ? 2.f : c0;
+                        c1 = x + 1 - d < 0 ? 2.f : c1;
+                        c0 = x < W ? c0 : 0.f;
+                        c1 = x + 1 < W ? c1 : 0.f;
+                    }
+                    w[q] = pack_16x2<kBf16>(c0, c1);
+                }
+                mine[s] = make_uint4(w[0], w[1], w[2], w[3]);
             }
-            mine[s] = pack8(v);
-        }
+        };
+        if (xbase + 7 < W && xbase >= d0 + 7)
+            sweep(std::integral_constant<bool, false>{});
+        else
+            sweep(std::integral_constant<bool, true>{});
     } else {
         const float inv_c = 1.f / (float)C;
         uint32_t pli[8], prw[8];
