@@ -58,6 +58,7 @@ constexpr int kTmaWarp = kEpiWarp0 + 4;
 constexpr int kMmaWarp = kTmaWarp + 1;
 constexpr int kThreads = 32 * (kMmaWarp + 1);
 constexpr int kMaxR = 5;          // window rows per stage, at most
+constexpr int kMaxRho2 = 2 * 24 + 1;   // row offsets -rho .. rho of the largest radius
 struct TcParams {
     int H, W, C, D;
     int N;          // round_up(D, 16): disparity rows the TMA box loads
@@ -113,7 +114,7 @@ struct Op16<false> {
 };
 
 struct TcSmem {
-    size_t a_off, b_off, ones_off, g_off, bar_off, misc_off, total;
+    size_t a_off, b_off, ones_off, g_off, bar_off, misc_off, sy_off, total;
 };
 
 // Per stage: R window rows of weights (A, (KW/8) x 2048 bytes each) and R
@@ -136,6 +137,8 @@ __host__ __device__ inline TcSmem tc_smem_layout(int KW, int Nb, int NH, int R, 
     o += (size_t)(3 * S + 9) * 8;
     s.misc_off = o;
     o += 16;
+    s.sy_off = o;         // spatial y-terms, one packed pair per row offset
+    o += (size_t)kMaxRho2 * 8;
     s.total = o + 1024;   // slack for aligning the base to 1024 bytes
     return s;
 }
@@ -225,6 +228,13 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&gmap) : "memory");
     }
     if (warp == 0) tmem_alloc(smem_u32(&misc[0]), p.tmem_cols);
+    // spatial y-term of row offset dy, (ks dy^2, ks dy^2), at index dy + rho
+    uint64_t* sytab = (uint64_t*)(sm + L.sy_off);
+    for (int i = tid; i <= 2 * p.rho; i += kThreads) {
+        const int dy = i - p.rho;
+        const float sy = (float)(dy * dy) * p.neg_ks;
+        sytab[i] = f2_pack(sy, sy);
+    }
     for (int i = tid; i < (int)(S * a_stage / 16); i += kThreads) ((uint4*)a_base)[i] = make_uint4(0, 0, 0, 0);
     {
         // with D + 16 > 256 the normaliser is a separate N=16 MMA against this
@@ -339,11 +349,9 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                     const uint2* grow = gt + hr * KW;
                     // both passes of a warp cover pixel row warp >> 1, so the row
                     // offset, its window test and the spatial y-term are shared
-                    const int dy = hr - p.rho - pty[0];
-                    const bool act = dy >= -p.rho && dy <= p.rho;   // uniform over the warp
-                    const float sy = (float)(dy * dy) * p.neg_ks;
-                    const uint64_t syp = f2_pack(sy, sy);
-                    if (act) {
+                    const int dyr = hr - pty[0];   // row offset + rho
+                    if ((unsigned)dyr <= (unsigned)(2 * p.rho)) {   // uniform over the warp
+                        const uint64_t syp = sytab[dyr];
 #pragma unroll
                         for (int i = 0; i < kPasses; ++i) {
 #pragma unroll
@@ -400,27 +408,38 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
             int bidx = 0;
             bool pending = false;
             float* arow = (agg_out && pvalid) ? agg_out + ((size_t)py * p.W + px) * p.D : nullptr;
+            // WTA (smallest d on ties) keeping the neighbours of the running best
+            auto step = [&](float a, int d) {
+                if (pending) {
+                    a_next = a;
+                    pending = false;
+                }
+                if (a < best) {
+                    best = a;
+                    bidx = d;
+                    a_prev = last;
+                    pending = true;
+                }
+                last = a;
+            };
+            const uint64_t inv2 = f2_pack(inv, inv);
             for (int c0 = 0; c0 < p.N; c0 += 16) {
                 float v[16];
                 tmem_ld16(tbase + (uint32_t)c0, v);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int d = c0 + i;
-                    if (d < p.D) {
-                        const float a = v[i] * inv;
-                        if (arow) arow[d] = a;
-                        if (pending) {
-                            a_next = a;
-                            pending = false;
-                        }
-                        if (a < best) {
-                            best = a;
-                            bidx = d;
-                            a_prev = last;
-                            pending = true;
-                        }
-                        last = a;
-                    }
+                for (int i = 0; i < 16; i += 2) f2_unpack(f2_mul(f2_pack(v[i], v[i + 1]), inv2), v[i], v[i + 1]);
+                if (arow) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (c0 + i < p.D) arow[c0 + i] = v[i];
+                }
+                if (c0 + 16 <= p.D) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) step(v[i], c0 + i);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (c0 + i < p.D) step(v[i], c0 + i);
                 }
             }
             tc_fence_before();
