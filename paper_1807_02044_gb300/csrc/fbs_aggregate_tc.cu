@@ -17,8 +17,8 @@
 //     use the same weights;
 //   * issues KW/16 tcgen05.mma (kind::f16, M=128, N=round_up(D,16), K=16)
 //     accumulating in FP32 in tensor memory.
-// A 3-deep ring of A/B stages lets the threads produce row hr+1 while the
-// tensor core works on row hr; TMA runs two rows ahead.  After the last row,
+// A ring of S stages of R rows each (S >= 2) lets the threads produce the
+// next stage while the tensor core works on the current one; TMA runs ahead.  After the last row,
 // four warps read the accumulator rows (one pixel per TMEM lane), normalise
 // in FP32, and do WTA (smallest d on ties) and Eq. (10) in registers.
 //
@@ -57,7 +57,7 @@ constexpr int kEpilogue = 128;
 constexpr int kTmaWarp = kEpiWarp0 + 4;
 constexpr int kMmaWarp = kTmaWarp + 1;
 constexpr int kThreads = 32 * (kMmaWarp + 1);
-constexpr int kMaxR = 5;          // window rows per stage, at most
+constexpr int kMaxR = 8;          // window rows per stage, at most
 constexpr int kMaxRho2 = 2 * 24 + 1;   // row offsets -rho .. rho of the largest radius
 struct TcParams {
     int H, W, C, D;
@@ -696,9 +696,11 @@ bool tc_plan(int H, int W, int C, int D, int radius, float sigma_s, float sigma_
     p.idesc = base | ((uint32_t)((p.ones_sep ? p.N : p.Nb) >> 3) << 17);
     p.idesc16 = base | (2u << 17);
     // R window rows per stage and S stages: the largest R (<= kMaxR) with at least
-    // 3 stages in 227 KB, then as many stages (<= 6) as fit
+    // 2 stages in 227 KB, then as many stages (<= 6) as fit.  Fewer, larger
+    // stages per tile measured faster than deeper pipelines of small stages:
+    // each stage costs the producers a wait, a proxy fence and an arrival
     for (p.R = max_rows < 1 || max_rows > kMaxR ? kMaxR : max_rows; p.R >= 1; --p.R) {
-        for (p.S = 6; p.S >= 3; --p.S) {
+        for (p.S = 6; p.S >= 2; --p.S) {
             L = tc_smem_layout(p.KW, p.Nb, p.NH, p.R, p.S, p.ones_sep != 0);
             if (L.total <= 227 * 1024) return true;
         }
