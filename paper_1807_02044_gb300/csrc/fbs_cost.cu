@@ -457,11 +457,14 @@ constexpr int kXbThreads = 256;
 __device__ __forceinline__ int skew(int c) { return c + (c >> 3); }
 __host__ __device__ inline int skew_len(int n) { return n + (n - 1) / 8; }
 
+// x-blocks per CTA: 16 up to 8 disparity groups, then 8 (measured best on
+// GB300 for D = 64, 128 and 256; smaller CTAs interleave their staging and
+// compute phases better, and 640 columns split evenly into 16-block CTAs)
 __host__ __device__ inline int xb_blocks_per_cta(int D)
 {
     const int ndg = (D + 7) / 8;
-    const int b = kXbThreads / ndg;
-    return b < 32 ? b : 32;
+    const int b = ndg <= 8 ? 16 : 8;
+    return b * ndg <= kXbThreads ? b : kXbThreads / ndg;
 }
 
 // Per-warp output buffer: 256 rows of 16 bytes, row r at r + r/8 (conflict-free
