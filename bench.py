@@ -616,7 +616,7 @@ def run_batched(args):
            "sequential_bf16": {"ms_per_batch": t_seq16, "gtaps_per_s": taps / (t_seq16 * 1e-3) / 1e9},
            "batched_bf16": {"ms_per_batch": t_b16, "gtaps_per_s": taps / (t_b16 * 1e-3) / 1e9, "plan": plan16,
                             "gpu_launches": launches16, "equals_sequential_bf16_bitwise": identical16,
-                            "graph": f"per pair: pad rows, statistics, 16-bit cost, tcgen05 aggregation; "
+                            "graph": f"per pair: one-kernel 16-bit cost build, tcgen05 aggregation; "
                                      f"{[1, 2, 4][plan16 >> 1]} concurrent branches, stage rows "
                                      f"{'max' if plan16 % 2 == 0 else '<= 3'}"},
            "roofline": None, "cpu_baseline": None, "e2e": None}

@@ -161,6 +161,25 @@ __device__ __forceinline__ void raise_abort(volatile uint32_t* abort_flag, int* 
     atomicCAS(err, 0, code);
 }
 
+// The persistent tile walk of a CTA (tiles blockIdx.x, + gridDim.x, ...) with
+// the tile's column and row carried incrementally (no division per tile).
+struct TileWalk {
+    int tile, tx, ty, dx, dy, ntx;
+    __device__ __forceinline__ TileWalk(int ntx_)
+        : tile((int)blockIdx.x), tx((int)blockIdx.x % ntx_), ty((int)blockIdx.x / ntx_),
+          dx((int)gridDim.x % ntx_), dy((int)gridDim.x / ntx_), ntx(ntx_) {}
+    __device__ __forceinline__ void next()
+    {
+        tile += (int)gridDim.x;
+        tx += dx;
+        ty += dy;
+        if (tx >= ntx) {
+            tx -= ntx;
+            ++ty;
+        }
+    }
+};
+
 // 2^23 as an FP32 bit pattern: for 0 <= c < 2^23 the pattern kMagic + c is the
 // float 2^23 + c exactly, so subtracting 2^23 gives float(c) exactly.
 constexpr uint32_t kMagic = 0x4B000000u;
@@ -291,10 +310,10 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
         const float ninf = __int_as_float(0xff800000);
         const uint64_t magic2 = f2_pack(-8388608.f, -8388608.f);
         const uint64_t nkr2 = f2_pack(p.neg_kr, p.neg_kr);
-        uint32_t g = 0, t = 0;
+        uint32_t gs = 0, gu = 0, t = 0;   // stage slot and use count of the next stage
         bool stop = false;
-        for (int tile = blockIdx.x; tile < p.ntiles && !stop; tile += gridDim.x, ++t) {
-            const int tx0 = (tile % p.ntx) * kTW, ty0 = (tile / p.ntx) * kTH;
+        for (TileWalk tw(p.ntx); tw.tile < p.ntiles && !stop; tw.next(), ++t) {
+            const int tx0 = tw.tx * kTW, ty0 = tw.ty * kTH;
             const int xlo = tx0 - p.rho8;
             const uint32_t tb = t & 1;
             if (!mbar_wait_or_abort(g_full0 + 8 * tb, (t >> 1) & 1, abort_flag)) {
@@ -330,7 +349,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
             const int hr_hi = min(p.NH, p.H - ty0 + p.rho);
             for (int h0 = hr_lo; h0 < hr_hi; h0 += R) {
                 const int nr = min(R, hr_hi - h0);
-                const uint32_t s = g % S, use = g / S;
+                const uint32_t s = gs, use = gu;   // g % S, g / S, carried below
                 // one lane waits for the MMAs that last read stage s; the warp follows
                 bool ok = true;
                 if (lane == 0 && use > 0) ok = mbar_wait_or_abort(empty0 + 8 * s, (use - 1) & 1, abort_flag);
@@ -378,7 +397,10 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                 fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(full_a0 + 8 * s);
-                ++g;
+                if (++gs == (uint32_t)S) {
+                    gs = 0;
+                    ++gu;
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(g_empty0 + 8 * tb);   // this tile's guide is no longer read
@@ -388,8 +410,8 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
         const int q4 = warp - kEpiWarp0;    // TMEM lane quarter
         const int m = 32 * q4 + lane;       // pixel of the tile == TMEM lane
         uint32_t t = 0;
-        for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++t) {
-            const uint32_t ab = t % p.nacc, u = t / p.nacc;
+        for (TileWalk tw(p.ntx); tw.tile < p.ntiles; tw.next(), ++t) {
+            const uint32_t ab = p.nacc == 2 ? (t & 1) : 0, u = p.nacc == 2 ? (t >> 1) : t;
             // tcgen05.ld is warp-collective: the whole warp continues or stops
             const bool ok = __all_sync(0xffffffffu, mbar_wait_or_abort(acc_full0 + 8 * ab, u & 1, abort_flag));
             if (!ok) {
@@ -398,7 +420,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
             }
             tc_fence_after();
             const uint32_t tbase = tmem + ((uint32_t)(32 * q4) << 16) + ab * p.acc_stride;
-            const int tx0 = (tile % p.ntx) * kTW, ty0 = (tile / p.ntx) * kTH;
+            const int tx0 = tw.tx * kTW, ty0 = tw.ty * kTH;
             const int py = ty0 + (m >> 4), px = tx0 + (m & 15);
             const bool pvalid = py < p.H && px < p.W;
             float dv[16];
@@ -459,11 +481,11 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
     } else if (warp == kTmaWarp) {
         // ================= TMA producer of guide tiles and cost rows ==========
         if (lane == 0) {
-            uint32_t g = 0, t = 0, gpend = 0;
+            uint32_t g = 0, gs = 0, gu = 0, t = 0, gpend = 0;
             const uint32_t guide_bytes = (uint32_t)p.NH * KW * 8;
             bool stop = false;
-            for (int tile = blockIdx.x; tile < p.ntiles && !stop; tile += gridDim.x, ++t) {
-                const int tx0 = (tile % p.ntx) * kTW, ty0 = (tile / p.ntx) * kTH;
+            for (TileWalk tw(p.ntx); tw.tile < p.ntiles && !stop; tw.next(), ++t) {
+                const int tx0 = tw.tx * kTW, ty0 = tw.ty * kTH;
                 const int xlo = tx0 - p.rho8;
                 {
                     const uint32_t tb = t & 1, u = t >> 1;
@@ -479,7 +501,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                 const int hr_hi = min(p.NH, p.H - ty0 + p.rho);
                 for (int h0 = hr_lo; h0 < hr_hi; h0 += R) {
                     const int nr = min(R, hr_hi - h0);
-                    const uint32_t s = g % S, use = g / S;
+                    const uint32_t s = gs, use = gu;   // g % S, g / S
                     if (use > 0 && !mbar_wait_or_abort(empty0 + 8 * s, (use - 1) & 1, abort_flag)) {
                         raise_abort(abort_flag, err, 2);
                         stop = true;
@@ -489,6 +511,10 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                     mbar_expect_tx(full_b0 + 8 * s, b_stage);
                     tma_load_4d(smem_u32(b_base + s * b_stage), &tmap, 0, 0, xlo >> 3, ty0 - p.rho + h0, full_b0 + 8 * s);
                     ++g;
+                    if (++gs == (uint32_t)S) {
+                        gs = 0;
+                        ++gu;
+                    }
                 }
             }
             if (*abort_flag) {
@@ -502,28 +528,28 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
     } else {
         // ================= MMA issuer =========================================
         if (lane == 0) {
-            uint32_t g = 0, t = 0;
+            uint32_t gs = 0, gu = 0, t = 0;   // stage slot and use count
             // descriptors of stage 0, row 0, K-step 0; other positions add their
             // byte offset >> 4 to the 14-bit start-address field
             const uint64_t a_desc0 = sdesc(smem_u32(a_base), 2048, 128);
             const uint64_t b_desc0 = sdesc(smem_u32(b_base), lbo_b, 128);
             const uint64_t o_desc0 = sdesc(smem_u32(sm + L.ones_off), 256, 128);
             bool stop = false;
-            for (int tile = blockIdx.x; tile < p.ntiles && !stop; tile += gridDim.x, ++t) {
-                const uint32_t ab = t % p.nacc, u = t / p.nacc;
+            for (TileWalk tw(p.ntx); tw.tile < p.ntiles && !stop; tw.next(), ++t) {
+                const uint32_t ab = p.nacc == 2 ? (t & 1) : 0, u = p.nacc == 2 ? (t >> 1) : t;
                 if (u > 0 && !mbar_wait_or_abort(acc_empty0 + 8 * ab, (u - 1) & 1, abort_flag)) {
                     raise_abort(abort_flag, err, 5);
                     break;
                 }
                 tc_fence_after();
                 const uint32_t dacc = tmem + ab * p.acc_stride;
-                const int ty0 = (tile / p.ntx) * kTH;
+                const int ty0 = tw.ty * kTH;
                 const int hr_lo = max(0, p.rho - ty0);
                 const int hr_hi = min(p.NH, p.H - ty0 + p.rho);
                 uint32_t accumulate = 0;
                 for (int h0 = hr_lo; h0 < hr_hi; h0 += R) {
                     const int nr = min(R, hr_hi - h0);
-                    const uint32_t s = g % S, par = (g / S) & 1;
+                    const uint32_t s = gs, par = gu & 1;   // g % S, (g / S) & 1
                     if (!mbar_wait_or_abort(full_a0 + 8 * s, par, abort_flag) ||
                         !mbar_wait_or_abort(full_b0 + 8 * s, par, abort_flag)) {
                         raise_abort(abort_flag, err, 3);
@@ -553,7 +579,10 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                         }
                     }
                     umma_commit(empty0 + 8 * s);
-                    ++g;
+                    if (++gs == (uint32_t)S) {
+                        gs = 0;
+                        ++gu;
+                    }
                 }
                 if (stop) break;
                 umma_commit(acc_full0 + 8 * ab);

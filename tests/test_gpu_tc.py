@@ -135,3 +135,29 @@ def test_tc_f16_1280x960_d128_r15(fbs, oracle_mod):
     bad = float(np.mean(np.abs(ds16.cpu().numpy() - ds32.cpu().numpy()) > 1.0))
     print(f"extra bad pixels over FP32: {100 * bad:.4f}%")
     assert bad <= 0.005
+
+
+@pytest.mark.parametrize("prec,expect", [("f32", {"COST": 2, "AGG_F32": 1, "AGG_TC": 0}),
+                                         ("bf16", {"COST": 1, "AGG_F32": 0, "AGG_TC": 1})])
+def test_kernel_accounting_counts_every_launch(fbs, prec, expect):
+    """fbs_profile_read reports kernels, not calls: the FP32 form launches the
+    statistics pre-pass, the cost kernel and the aggregation; the 16-bit form
+    one cost kernel (statistics, pad rows and guide included) and the
+    tensor-core aggregation."""
+    rng = np.random.default_rng(3)
+    L = rng.integers(0, 256, size=(40, 72, 3)).astype(np.uint8)
+    R = np.roll(L, -2, axis=1)
+    p = fbs.FBS_PREC_F32 if prec == "f32" else _prec(fbs, prec)
+    with fbs.Context(0, prec=p) as ctx:
+        dl, dr = _dev(L), _dev(R)
+        ctx.compute_disparity(dl, dr, 24, 3, 3.0, 12.0)
+        torch.cuda.synchronize()
+        fbs.fbs_profile(ctx.ctx, 1)
+        for _ in range(3):
+            ctx.compute_disparity(dl, dr, 24, 3, 3.0, 12.0)
+        torch.cuda.synchronize()
+        got = {k: fbs.fbs_profile_read(ctx.ctx, getattr(fbs, "FBS_KERNEL_" + k))[1] for k in expect}
+        fbs.fbs_profile(ctx.ctx, 0)
+        fbs.fbs_sync(ctx.ctx)
+    assert got == {k: 3 * v for k, v in expect.items()}
+
