@@ -824,7 +824,8 @@ def run_band(args):
 def run_lr(args):
     """One step = both disparity maps and the LRC check (Eq. (9)) through
     fbs_compute_disparity_lr (FP32): one cost pass storing both volumes, two
-    aggregations, the check.  Gtaps/s counts the taps of both views."""
+    aggregations, the check.  Gtaps/s counts the taps of both views.  Beside it
+    the same call in a BF16 context (both views on the tensor cores)."""
     import numpy as np
     import torch
 
@@ -857,6 +858,22 @@ def run_lr(args):
     occ_rejected = float(((li == -1) & ~gt_ok).float().sum().item() / max(1.0, float((~gt_ok).sum().item())))
     taps = 2 * _taps(p)
     kt = res["kt"]
+    ctx.close()
+    # the same step in a BF16 context: both views on the tensor cores
+    ctx16 = fbs.Context(0, prec=fbs.FBS_PREC_BF16)
+    li16 = torch.empty_like(li)
+    ls16 = torch.empty_like(ls)
+    res16 = _time_call(fbs, torch, ctx16, lambda: fbs.fbs_compute_disparity_lr(
+        ctx16.ctx, dl, dr, H, W, p.C, D, p.radius, p.sigma_s, p.sigma_r, p.tau, li16, ls16, ri, rs, True, stream),
+        stream, flush, steps, warmup)
+    torch.cuda.synchronize()
+    valid = (li != -1) & (li16 != -1)
+    bf16 = {"ms_per_step": res16["step_ms"], "gtaps_per_s": taps / (res16["step_ms"] * 1e-3) / 1e9,
+            "fps": 1e3 / res16["step_ms"], "lrc_rejected_pct": 100.0 * float((li16 == -1).float().mean().item()),
+            "bad_px_vs_f32_pct": 100.0 * float(((ls16 - ls).abs() > 1.0)[valid].float().mean().item()),
+            "kernel_ms_per_step": {k: v[0] / steps for k, v in res16["kt"].items() if v[1]},
+            "gpu_launches": sum(n for _, n in res16["kt"].values())}
+    ctx16.close()
     out = {"metric": METRIC, "value": taps / (res["step_ms"] * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1,
            "steps": steps, "warmup": warmup, "ms_per_step": res["step_ms"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -865,9 +882,9 @@ def run_lr(args):
            "fps": 1e3 / res["step_ms"], "left_only_ms": one["step_ms"],
            "kernel_ms_per_step": {k: v[0] / steps for k, v in kt.items() if v[1]},
            "lrc_rejected_pct": 100.0 * rejected, "occluded_px_rejected_pct": 100.0 * occ_rejected,
-           "gpu_launches": sum(n for _, n in kt.values()), "roofline": None, "cpu_baseline": None, "e2e": None}
+           "gpu_launches": sum(n for _, n in kt.values()), "bf16_both_views": bf16,
+           "roofline": None, "cpu_baseline": None, "e2e": None}
     print(json.dumps(out))
-    ctx.close()
     return 0
 
 

@@ -111,16 +111,23 @@ fbs_status fbs_compute_disparity_host(fbs_ctx *ctx, const uint8_t *left, const u
 
 /*
  * Both views and the left-right consistency (LRC) check (Sec. II-A, Sec. III,
- * Eq. (9)).  Each matching cost is computed once and stored twice: in the left
- * volume at (u, v, d) and in the right volume at (u - d, v, d); where u + d >= W
- * the right volume holds the maximum cost.  Each volume is aggregated with its
- * own image as guide (Eq. (6)-(8)), WTA and Eq. (10) give both maps.
+ * Eq. (9)).  The right map at (u, v) matches R(u) against L(u + d); where
+ * u + d >= W the cost is the maximum.  Each view is aggregated with its own
+ * image as guide (Eq. (6)-(8)), WTA and Eq. (10) give both maps.
  *   disp_int / disp_subpix: the LEFT map (either may be NULL, not both); with
  *     lrc != 0 every left pixel whose disparity d fails Eq. (9) -- u - d < 0 or
  *     the right disparity at (u - d, v) differs from d -- is set to -1 in both.
  *   disp_int_right / disp_subpix_right (each nullable): the right map.
- * FP32 arithmetic whatever the context's precision.  Scratch: two cost volumes
- * (2 * H*W*round_up(D,4)*4 bytes) and two integer maps.
+ * FP32 context: each matching cost is computed once and stored in the left
+ * volume at (u, v, d) and in the right volume at (u - d, v, d); scratch: two
+ * cost volumes (2 * H*W*round_up(D,4)*4 bytes) and two integer maps.
+ * BF16 / FP16 context: the tensor-core path of fbs_compute_disparity for the
+ * left view, and for the right view the same path on the horizontally
+ * mirrored pair with the images swapped (its left view is the mirrored right
+ * view), mirrored back; the left map is bit-identical to
+ * fbs_compute_disparity's.  D <= 256 and radius <= 24 (FBS_ERR_UNSUPPORTED
+ * otherwise); scratch: one 16-bit volume at a time plus two mirrored images
+ * and four maps.
  */
 fbs_status fbs_compute_disparity_lr(fbs_ctx *ctx, const uint8_t *left, const uint8_t *right,
                                     int H, int W, int C, int D, int radius,

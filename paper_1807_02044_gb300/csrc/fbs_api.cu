@@ -15,9 +15,9 @@
 
 using namespace fbs_detail;
 
-namespace {
+namespace fbs {
 
-// Tensor-core form: 16-bit planar cost volume, tcgen05 aggregation.
+// Tensor-core form: 16-bit x-blocked cost volume, tcgen05 aggregation.
 fbs_status run_path_tc(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C, int D,
                        int radius, float sigma_s, float sigma_r, float tau, int32_t* disp_int, float* disp_subpix,
                        cudaStream_t st)
@@ -49,12 +49,17 @@ fbs_status run_path_tc(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, 
     return FBS_OK;
 }
 
+}  // namespace fbs
+
+namespace {
+
 fbs_status run_path(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C, int D,
                     int radius, float sigma_s, float sigma_r, float tau, int32_t* disp_int,
                     float* disp_subpix, cudaStream_t st)
 {
     if (ctx->opt.prec != FBS_PREC_F32)
-        return run_path_tc(ctx, left, right, H, W, C, D, radius, sigma_s, sigma_r, tau, disp_int, disp_subpix, st);
+        return fbs::run_path_tc(ctx, left, right, H, W, C, D, radius, sigma_s, sigma_r, tau, disp_int, disp_subpix,
+                                st);
     const int ld = fbs::padded_ld(D);
     const size_t stats = fbs::cost_scratch_bytes(H, W);
     const size_t need = stats + sizeof(float) * (size_t)H * W * ld;
@@ -178,6 +183,7 @@ fbs_status fbs_destroy(fbs_ctx* ctx)
         if (ctx->bjoin[k]) cudaEventDestroy(ctx->bjoin[k]);
     }
     if (ctx->bfork) cudaEventDestroy(ctx->bfork);
+    if (ctx->aux) cudaFree(ctx->aux);
     if (ctx->bpairs) cudaFree(ctx->bpairs);
     if (ctx->bcounters) cudaFree(ctx->bcounters);
     for (int k = 0; k < 2; ++k) {

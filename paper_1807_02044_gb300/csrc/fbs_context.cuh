@@ -60,6 +60,9 @@ struct fbs_ctx {
     struct fbs_band_state* band = nullptr;
     void* band_ws = nullptr;
     size_t band_ws_bytes = 0;
+    // both-view tensor-core form: mirrored images and right-view maps
+    void* aux = nullptr;
+    size_t aux_bytes = 0;
 };
 
 namespace fbs_detail {
@@ -186,7 +189,7 @@ inline fbs_status ensure(fbs_ctx* ctx, void** buf, size_t* have, size_t need, co
 {
     if (need <= *have) return FBS_OK;
     const size_t cap = ctx->opt.workspace_cap;
-    if (cap && ctx->ws_bytes + ctx->io_bytes + ctx->band_ws_bytes - *have + need > cap)
+    if (cap && ctx->ws_bytes + ctx->io_bytes + ctx->band_ws_bytes + ctx->aux_bytes - *have + need > cap)
         return fail(ctx, FBS_ERR_OOM, "%s needs %zu bytes; workspace cap is %zu", what, need, cap);
     if (*buf) {
         cudaError_t e = cudaDeviceSynchronize();   // the old buffer may still be in use

@@ -158,5 +158,10 @@ fbs_status ctx_error(fbs_ctx* ctx, fbs_status st, const char* msg);
 void ctx_count_launch(fbs_ctx* ctx, int kind, long long kernels);
 // Release the band form's state (called by fbs_destroy).
 void band_free(fbs_ctx* ctx);
+// The single-view tensor-core path of fbs_compute_disparity (context scratch
+// ctx->ws; arguments already checked).
+fbs_status run_path_tc(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C, int D,
+                       int radius, float sigma_s, float sigma_r, float tau, int32_t* disp_int, float* disp_subpix,
+                       cudaStream_t st);
 
 }  // namespace fbs

@@ -111,3 +111,56 @@ def test_full_size_bench_workload_row_band(fbs, oracle_mod):
     ri, rs, ragg = oracle_mod.fbs_right(p.left, p.right, p.D, p.radius, p.sigma_s, p.sigma_r, rows=(y0, y1),
                                         want_agg=True)
     check_disparities(dr[y0:y1], sr_[y0:y1], ragg, ri, rs, 2.0)
+
+
+U16 = {"bf16": 2.0 ** -9, "f16": 2.0 ** -11}
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+@pytest.mark.parametrize("H,W,C,D,r,mode", [(17, 45, 3, 20, 3, 0), (24, 70, 1, 33, 4, 0), (13, 37, 3, 12, 2, 1)])
+def test_tensor_core_both_views_match_the_oracle(fbs, oracle_mod, prec, H, W, C, D, r, mode):
+    """16-bit operands: both integer maps agree with the FP64 oracle except at
+    near ties of the rounding bound 3uR + 1e-5 (u the 16-bit unit roundoff,
+    R the cost range), every winner is within that margin of the oracle's
+    best, and the LRC decision agrees wherever both winners it reads are clear."""
+    L, R = _pair(H * W + D + 7, H, W, C, shift=4)
+    tau = 30.0
+    p = fbs.FBS_PREC_BF16 if prec == "bf16" else fbs.FBS_PREC_F16
+    with fbs.Context(0, cost=mode, prec=p) as ctx:
+        dl, sl, dr, sr_ = _run_lr(fbs, ctx, L, R, D, r, float(r), 12.0, tau, lrc=False)
+        cl, _, _, _ = _run_lr(fbs, ctx, L, R, D, r, float(r), 12.0, tau, lrc=True)
+    rng_ = tau if mode == 1 else 2.0
+    tol = 3 * U16[prec] * rng_ + 1e-5
+    ref_l, _, agg_l = oracle_mod.fbs(L, R, D, r, float(r), 12.0, tau=tau, mode=mode, want_agg=True)
+    ref_r, _, agg_r = oracle_mod.fbs_right(L, R, D, r, float(r), 12.0, tau=tau, mode=mode, want_agg=True)
+    for di, ref, agg in ((dl, ref_l, agg_l), (dr, ref_r, agg_r)):
+        ties = near_tie_mask(agg, 2 * tol)
+        assert np.all((di == ref) | ties)
+        chosen = np.take_along_axis(agg, di[..., None].astype(np.int64), -1)[..., 0]
+        assert np.all(chosen - agg.min(-1) <= 2 * tol + 1e-12)
+    clear = ~near_tie_mask(agg_l, 2 * tol)
+    u = np.arange(W)[None, :].repeat(H, 0)
+    ur = u - ref_l
+    inside = ur >= 0
+    tie_r = near_tie_mask(agg_r, 2 * tol)
+    tie_at = np.zeros_like(clear)
+    tie_at[inside] = tie_r[np.nonzero(inside)[0], ur[inside]]
+    clear &= ~tie_at
+    ok_ref = oracle_mod.lrc(ref_l, ref_r) == 1
+    assert np.array_equal((cl != -1)[clear], ok_ref[clear])
+
+
+def test_tensor_core_views_equal_the_single_view_path(fbs):
+    """The left map is fbs_compute_disparity's; the right map is the single-view
+    path on the mirrored, swapped pair, mirrored back -- both bit for bit."""
+    L, R = _pair(5, 40, 120, 3, shift=7)
+    with fbs.Context(0, prec=fbs.FBS_PREC_BF16) as ctx:
+        dl, sl, dr, sr_ = _run_lr(fbs, ctx, L, R, 32, 5, 5.0, 12.0, 0.0, lrc=False)
+        di, ds = ctx.compute_disparity(_dev(L), _dev(R), 32, 5, 5.0, 12.0)
+        mi, ms = ctx.compute_disparity(_dev(R[:, ::-1]), _dev(L[:, ::-1]), 32, 5, 5.0, 12.0)
+        torch.cuda.synchronize()
+    assert np.array_equal(dl, di.cpu().numpy())
+    assert np.array_equal(sl.view(np.uint32), ds.cpu().numpy().view(np.uint32))
+    assert np.array_equal(dr, mi.cpu().numpy()[:, ::-1])
+    assert np.array_equal(sr_.view(np.uint32), ms.cpu().numpy()[:, ::-1].view(np.uint32))
+
