@@ -158,6 +158,55 @@ def test_host_entry_point_matches_device_path(fbs, ctx):
     assert np.array_equal(hs, ds.cpu().numpy())
 
 
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+@pytest.mark.parametrize("H,W,D,r,mode", [(33, 57, 20, 3, 0), (480, 640, 64, 7, 0), (61, 90, 40, 15, 0),
+                                          (7, 30, 12, 2, 0), (100, 77, 24, 4, 1)])
+def test_host_entry_point_tensor_cores(fbs, prec, H, W, D, r, mode):
+    """The tensor-core form of the host-buffer call (upload, the path,
+    download) returns exactly what the device-buffer call returns, with
+    pageable and with pinned host buffers, also with one output omitted and on
+    new contents of the same buffers."""
+    rng = np.random.default_rng(H * W + D)
+    L = _rand(rng, H, W, 3)
+    R = np.roll(L, -5, axis=1)
+    p = fbs.FBS_PREC_BF16 if prec == "bf16" else fbs.FBS_PREC_F16
+    with fbs.Context(0, cost=mode, prec=p) as c16:
+        di, ds = c16.compute_disparity(_dev(L), _dev(R), D, r, float(r), 12.0, 20.0)
+        torch.cuda.synchronize()
+        di, ds = di.cpu().numpy(), ds.cpu().numpy()
+        # pageable numpy buffers
+        hi = np.full((H, W), -9, np.int32)
+        hs = np.full((H, W), -9, np.float32)
+        fbs.fbs_compute_disparity_host(c16.ctx, L, R, H, W, 3, D, r, float(r), 12.0, 20.0, hi, hs)
+        assert np.array_equal(hi, di)
+        assert np.array_equal(hs.view(np.uint32), ds.view(np.uint32))
+        # pinned buffers, twice
+        pl = torch.from_numpy(L).pin_memory()
+        pr = torch.from_numpy(R).pin_memory()
+        pi = torch.full((H, W), -9, dtype=torch.int32).pin_memory()
+        ps = torch.full((H, W), -9.0).pin_memory()
+        for _ in range(2):
+            pi.fill_(-9)
+            ps.fill_(-9.0)
+            fbs.fbs_compute_disparity_host(c16.ctx, pl, pr, H, W, 3, D, r, float(r), 12.0, 20.0, pi, ps)
+            assert np.array_equal(pi.numpy(), di)
+            assert np.array_equal(ps.numpy().view(np.uint32), ds.view(np.uint32))
+        ps2 = torch.full((H, W), -9.0).pin_memory()
+        fbs.fbs_compute_disparity_host(c16.ctx, pl, pr, H, W, 3, D, r, float(r), 12.0, 20.0, None, ps2)
+        assert np.array_equal(ps2.numpy().view(np.uint32), ds.view(np.uint32))
+        # new contents of the same pinned buffers
+        L2 = L[::-1].copy()
+        R2 = R[::-1].copy()
+        pl.copy_(torch.from_numpy(L2))
+        pr.copy_(torch.from_numpy(R2))
+        fbs.fbs_compute_disparity_host(c16.ctx, pl, pr, H, W, 3, D, r, float(r), 12.0, 20.0, pi, ps)
+        d2i, d2s = c16.compute_disparity(_dev(L2), _dev(R2), D, r, float(r), 12.0, 20.0)
+        torch.cuda.synchronize()
+        assert np.array_equal(pi.numpy(), d2i.cpu().numpy())
+        assert np.array_equal(ps.numpy().view(np.uint32), d2s.cpu().numpy().view(np.uint32))
+        fbs.fbs_sync(c16.ctx)
+
+
 def test_invalid_arguments_are_rejected_before_launch(fbs, ctx):
     L = _dev(np.zeros((4, 4, 3), np.uint8))
     out = torch.empty((4, 4), dtype=torch.int32, device="cuda")
