@@ -487,7 +487,9 @@ def run_ours(args):
         assert np.array_equal(hi.numpy(), chosen["di"].cpu().numpy())
         e2e = {"value": job_rate(taps, world, e2e_s) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * p.H * p.W * p.C,
                "d2h_bytes_per_step": 8 * p.H * p.W, "steps": n_e2e,
-               "call": "fbs_compute_disparity_host (pinned host buffers, copies and sync inside the timed call)"}
+               "call": "fbs_compute_disparity_host (pinned host buffers, transfers and sync inside the timed call; "
+                       "the 16-bit forms read the images from and write the maps to the pinned host buffers "
+                       "directly, without staging copies)"}
 
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

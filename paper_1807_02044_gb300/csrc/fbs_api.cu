@@ -53,6 +53,18 @@ fbs_status run_path_tc(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, 
 
 namespace {
 
+// The device address of a page-locked host buffer, or nullptr when the GPU
+// cannot address it (pageable memory).
+const void* device_view(const void* p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 fbs_status run_path(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C, int D,
                     int radius, float sigma_s, float sigma_r, float tau, int32_t* disp_int,
                     float* disp_subpix, cudaStream_t st)
@@ -293,6 +305,22 @@ fbs_status fbs_compute_disparity_host(fbs_ctx* ctx, const uint8_t* left, const u
     if (s != FBS_OK) return s;
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(ctx, FBS_ERR_CUDA, "cannot select device %d", ctx->device);
+    // Tensor-core form with page-locked host buffers the GPU can address: no
+    // staging copies -- the cost kernel reads the images from host memory and
+    // the aggregation epilogue writes the maps there (over the host link; only
+    // these two kernels touch the caller's buffers, each byte once).
+    if (ctx->opt.prec != FBS_PREC_F32) {
+        const uint8_t *hl = (const uint8_t*)device_view(left), *hr = (const uint8_t*)device_view(right);
+        int32_t* hi = disp_int ? (int32_t*)device_view(disp_int) : nullptr;
+        float* hs = disp_subpix ? (float*)device_view(disp_subpix) : nullptr;
+        if (hl && hr && (hi || !disp_int) && (hs || !disp_subpix)) {
+            s = fbs::run_path_tc(ctx, hl, hr, H, W, C, D, radius, sigma_s, sigma_r, tau, hi, hs, ctx->stream);
+            if (s != FBS_OK) return s;
+            cudaError_t e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "host-buffer call");
+            return FBS_OK;
+        }
+    }
     const size_t npx = (size_t)H * W;
     const size_t img = npx * C;
     const size_t img_al = (img + 255) & ~(size_t)255;
