@@ -272,6 +272,11 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = misc[0];
+    // With a programmatic launch the set-up above overlaps the end of the
+    // kernel that writes the cost volume and the guide; everything below reads
+    // them, so every thread waits here until that kernel has completed and its
+    // writes are visible (a no-op for an ordinary launch).
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     if (warp < kProducerWarps) {
         // ================= weight producers =================================
@@ -685,8 +690,21 @@ cudaError_t run_tc(const CUtensorMap& map, const CUtensorMap& gmap, const TcPara
     cudaError_t e = cudaFuncSetAttribute(aggregate_tc_kernel<BF16, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)L.total);
     if (e != cudaSuccess) return e;
+    // programmatic stream serialization: the kernel may start while the
+    // previous kernel of the stream (the cost build, which signals early) ends
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = L.total;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     fbs::note_launch();
-    aggregate_tc_kernel<BF16, NG><<<grid, kThreads, L.total, stream>>>(map, gmap, p, agg_out, disp_int, disp_sub, err);
+    e = cudaLaunchKernelEx(&cfg, aggregate_tc_kernel<BF16, NG>, map, gmap, p, agg_out, disp_int, disp_sub, err);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -485,6 +485,10 @@ cost_xb_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int
                T* __restrict__ out, uint2* __restrict__ rgbx)
 {
     extern __shared__ int sm_xb[];
+    // let a programmatically launched successor (the tensor-core aggregation)
+    // start its set-up once every CTA of this grid has started; it waits for
+    // this grid's completion before it reads anything this kernel writes
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int ndg = (D + 7) >> 3;
     const int xbc = xb_blocks_per_cta(D);
