@@ -20,8 +20,9 @@ inline int padded_ld(int D) { return (D + 3) & ~3; }
 
 // ---- step 1: matching cost, Eq. (1)-(3) or TAD -------------------------------
 // Per-pixel statistics of both images (grey value, 3x3 block sum, 1/sqrt of
-// the block variance times n^2), computed by a pre-pass and read by the cost
-// kernels.  Both images: 2*H*W entries each.
+// the block variance times n^2), computed by a pre-pass and read by the FP32
+// layout's cost kernels (the 16-bit x-blocked cost kernel computes them in
+// shared memory and uses only rgbx).  Both images: 2*H*W entries each.
 struct CostScratch {
     int16_t* g;
     int* s;
