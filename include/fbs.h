@@ -62,10 +62,11 @@ typedef struct {
     int prec;                   /* fbs_precision */
     int fused;                  /* reserved, 0 */
     size_t workspace_cap;       /* bytes of scratch the context may hold; 0 = unlimited */
-    const char *autotune_cache_path; /* reserved, may be NULL */
+    const char *autotune_cache_path; /* batched form: file of "shape plan" lines the
+                                        autotuner appends to and reads back; may be NULL */
 } fbs_options;
 
-/* Fill *opt with the defaults: NCC, F32, unfused, no cap. */
+/* Fill *opt with the defaults: NCC, F32, unfused, no cap, no autotune cache file. */
 void fbs_default_options(fbs_options *opt);
 
 /* Create a context on CUDA device `device`.  opt may be NULL (defaults).
@@ -91,7 +92,13 @@ const char *fbs_last_error(const fbs_ctx *ctx);
  * Eq. (10).  left, right: device images.  disp_int, disp_subpix: device
  * outputs of H*W elements; either may be NULL but not both.  sigma_s is
  * gamma_d of Eq. (7), sigma_r is gamma_r of Eq. (8); tau is used only by the
- * TAD cost mode.  Scratch: one cost volume (H*W*D*4 bytes) held by ctx.
+ * TAD cost mode.  Scratch held by ctx: FP32 -- the block statistics and one
+ * cost volume (H*W*round_up(D,4)*4 bytes); BF16 / F16 -- one 16-bit x-blocked
+ * cost volume (H*ceil(W/8)*8*Dp*2 bytes, Dp as for the batched form) and the
+ * packed guide.  The 16-bit forms need D <= 256 and radius <= 24
+ * (FBS_ERR_UNSUPPORTED otherwise).  Two kernels per call in the 16-bit forms
+ * (cost build, tensor-core aggregation launched programmatically so its
+ * set-up overlaps the end of the cost build), three in FP32.
  */
 fbs_status fbs_compute_disparity(fbs_ctx *ctx, const uint8_t *left, const uint8_t *right,
                                  int H, int W, int C, int D, int radius,
