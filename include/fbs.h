@@ -44,7 +44,7 @@ typedef enum {
     FBS_ERR_OOM = 2,           /* device allocation failed or workspace cap reached */
     FBS_ERR_CUDA = 3,          /* a CUDA call or kernel failed; see fbs_last_error */
     FBS_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
-    FBS_ERR_UNSUPPORTED = 5    /* valid request this build cannot serve */
+    FBS_ERR_UNSUPPORTED = 5    /* valid request outside a form's limits (e.g. D > 256 on the tensor cores) */
 } fbs_status;
 
 /* Matching cost.  NCC is the paper's, Eq. (1)-(3) with varrho = 1.  TAD is a
