@@ -23,11 +23,13 @@
 // in FP32, and do WTA (smallest d on ties) and Eq. (10) in registers.
 //
 // Shared-memory operand layout (no swizzle, canonical K-major core matrices
-// of 8 rows x 16 bytes): element (row r, k) of an operand with R rows sits at
-//     (k / 8) * (R * 16) + r * 16 + (k % 8) * 2,
-// i.e. the stride between core matrices along K (LBO) is R*16 bytes and along
-// the rows (SBO) 128 bytes.  TMA writes a box of 8 columns x N disparities in
-// exactly that order, so B needs no rearrangement.  All operands live in
+// of 8 rows x 16 bytes): element (row r, k) of an operand sits at
+//     (k / 8) * LBO + r * 16 + (k % 8) * 2,
+// i.e. the stride between core matrices along the rows (SBO) is 128 bytes and
+// along K (LBO) 16 bytes per row plus padding: 128 * 16 + 64 for the weights
+// (the padding spreads the producers' stores over the banks), Nb * 16 for the
+// costs.  TMA writes a box of 8 columns x Nb disparities in exactly that order,
+// so B needs no rearrangement.  All operands live in
 // shared memory; warp roles and mbarrier pipelines are described at the kernel.
 //
 // Every wait on an mbarrier is bounded (iteration and clock limits); on a
@@ -50,14 +52,19 @@ constexpr int kTW = 16;         // tile width
 constexpr int kTH = 8;          // tile height
 constexpr int kM = kTW * kTH;   // 128 = MMA M = TMEM lanes
 constexpr int kProducerWarps = 16;                 // warps 0-15
-constexpr int kPasses = 32 / kProducerWarps;       // 32 pixel groups of 4 per tile
-static_assert(kPasses == 2, "the producers' passes of a warp share one pixel row (warp >> 1)");
+static_assert(kProducerWarps == 16 && kTH == 8 && kTW == 16,
+              "producer warp w covers pixel rows 2 (w >> 2), +1 and the stage rows r % 4 == w % 4");
 constexpr int kEpiWarp0 = kProducerWarps;          // 4 epilogue warps: TMEM lane quarters 0-3
 constexpr int kEpilogue = 128;
 constexpr int kTmaWarp = kEpiWarp0 + 4;
 constexpr int kMmaWarp = kTmaWarp + 1;
 constexpr int kThreads = 32 * (kMmaWarp + 1);
 constexpr int kMaxR = 8;          // window rows per stage, at most
+// Byte distance between the A operand's core matrices adjacent along K: the
+// 2048 bytes of 128 rows x 16 bytes, plus 64 bytes of padding, so that the
+// producers' 4-byte stores to the same row of two K-blocks fall in different
+// shared-memory banks.
+constexpr uint32_t kALbo = 2048 + 64;
 constexpr int kMaxRho2 = 2 * 24 + 1;   // row offsets -rho .. rho of the largest radius
 struct TcParams {
     int H, W, C, D;
@@ -117,14 +124,14 @@ struct TcSmem {
     size_t a_off, b_off, ones_off, g_off, bar_off, misc_off, sy_off, total;
 };
 
-// Per stage: R window rows of weights (A, (KW/8) x 2048 bytes each) and R
+// Per stage: R window rows of weights (A, (KW/8) x kALbo bytes each) and R
 // rows of costs (B, (KW/8) x Nb x 16 bytes each).
 __host__ __device__ inline TcSmem tc_smem_layout(int KW, int Nb, int NH, int R, int S, bool ones_sep)
 {
     TcSmem s;
     size_t o = 0;
     s.a_off = o;
-    o += (size_t)S * R * (KW / 8) * 2048;
+    o += (size_t)S * R * (KW / 8) * kALbo;
     s.b_off = o;
     o += (size_t)S * R * (KW / 8) * Nb * 16;
     s.ones_off = o;
@@ -185,8 +192,9 @@ struct TileWalk {
 constexpr uint32_t kMagic = 0x4B000000u;
 
 // Warp roles: 0-15 weight producers, 16-19 epilogue (TMEM lane quarters 0-3),
-// 20 TMA producer (guide tiles and cost rows), 21 MMA issuer.  NG = number of
-// groups of 8 column pairs a pixel's window row needs (ceil((rho + 1) / 8)).
+// 20 TMA producer (guide tiles and cost rows), 21 MMA issuer.  NPT = column
+// pairs per pixel and window row of one producer thread (ceil((rho + 1) / 2),
+// rounded up to an instantiated count).
 //
 // Pipeline: a stage holds R consecutive window rows of one tile (the last
 // stage of a tile may hold fewer).  For stage g in slot s = g % S:
@@ -198,7 +206,7 @@ constexpr uint32_t kMagic = 0x4B000000u;
 //   epilogue   waits acc_full[ab], reads the accumulator, arrives acc_empty[ab].
 // One wait/commit pair per R rows keeps the single-thread control path
 // (which shares its scheduler with busy warps) off the critical path.
-template <bool BF16, int NG>
+template <bool BF16, int NPT, int PM>
 __global__ void __launch_bounds__(kThreads, 1)
 aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap gmap, TcParams p,
                     float* __restrict__ agg_out, int32_t* __restrict__ disp_int, float* __restrict__ disp_sub,
@@ -222,7 +230,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int KW = p.KW, R = p.R, S = p.S;
-    const uint32_t a_row = (uint32_t)(KW / 8) * 2048;       // bytes of one window row of weights
+    const uint32_t a_row = (uint32_t)(KW / 8) * kALbo;      // bytes of one window row of weights
     const uint32_t lbo_b = (uint32_t)p.Nb * 16;
     const uint32_t b_row = (uint32_t)(KW / 8) * lbo_b;      // bytes of one window row of costs
     const uint32_t a_stage = a_row * R, b_stage = b_row * R;
@@ -280,41 +288,56 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
 
     if (warp < kProducerWarps) {
         // ================= weight producers =================================
-        // Pass i of warp w covers pixels m = 8b + par + 2*ps (ps = lane >> 3) with
-        // j = kPasses*w + i, b = j >> 1, par = j & 1 (the 4 pixels of a pass share
-        // a tile row).  Pixel m needs window columns kc-rho .. kc+rho (kc = tx +
-        // rho8); they are covered by rho+1 pairs of adjacent columns (k, k+1)
-        // starting at the even column <= kc-rho, 8 pairs per group (lane & 7).
-        // Columns a pixel never reaches are never written and stay zero.  The
-        // four pixels of a pass start 8 banks apart, so a pass's 4-byte stores
-        // need two wavefronts at most.
+        // Warp w covers the pixel rows ty = 2 (w >> 2) and ty + 1 of the tile
+        // and, within every stage, the window rows r with r % 4 == w % 4; lane
+        // -> pixel column xm = lane & 15 and pair phase h = lane >> 4.  Pixel
+        // (xm, y) needs window columns kcen - rho .. kcen + rho (kcen = xm +
+        // rho8), covered by rho + 1 pairs of adjacent columns (k, k + 1)
+        // starting at the even column c0 <= kcen - rho; the thread computes the
+        // pairs 2 j + h (j < NPT) of both pixels of its column, which share
+        // every guide load (the same window position q).  Columns a pixel never
+        // reaches are never written and stay zero.  Whether a window row lies
+        // inside a pixel row's window is uniform over the warp, and the row is
+        // computed only for the pixel rows whose window it lies in (zeros for
+        // the other).  PM says which pairs exist: all NPT (odd radius), all
+        // but the last one of phase 1 (even radius), or per-pair flags.
         // Colour distance: |q - p|^2 = |q|^2 + |p|^2 - 2 q.p, exact in integers
         // (|q|^2 comes with the guide tile, q.p is one dp4a).  It is below 2^23,
         // so carrying kMagic in |p|^2 turns the integer into the bits of
         // 2^23 + c and one packed subtraction gives both columns' c as exact
         // floats; the exponent argument c*neg_kr + (sx + sy) of a column pair is
         // one packed add and one packed FMA (the same roundings as scalar code).
-        const int ps = lane >> 3, pi = lane & 7;
+        const int ty = 2 * (warp >> 2), rq = warp & 3;
+        const int xm = lane & 15, h = lane >> 4;
+        const int m0 = 16 * ty + xm;   // A row of the upper pixel; the lower one is m0 + 16
+        const int kcen = xm + p.rho8;
+        const int c0 = (kcen - p.rho) & ~1;
         const int np = p.rho + 1;
-        int pm[kPasses], kcen[kPasses], kk[kPasses][NG];
-        uint32_t aoff[kPasses][NG];
-        bool on[kPasses][NG];
+        // pair j of the thread: columns k, k + 1 with k = c0 + 2 h + 4 j, guide
+        // entries at byte 8 (c0 + 2 h) + 32 j of a guide row
+        uint32_t aoff[NPT];
+        bool on[NPT];
 #pragma unroll
-        for (int i = 0; i < kPasses; ++i) {
-            const int j = kPasses * warp + i;
-            pm[i] = 8 * (j >> 1) + (j & 1) + 2 * ps;
-            kcen[i] = (pm[i] & 15) + p.rho8;
-#pragma unroll
-            for (int pg = 0; pg < NG; ++pg) {
-                const int k = ((kcen[i] - p.rho) & ~1) + 2 * pi + 16 * pg;
-                kk[i][pg] = k;
-                on[i][pg] = pg * 8 + pi < np;
-                aoff[i][pg] = (uint32_t)((k >> 3) * 2048 + pm[i] * 16 + (k & 7) * 2);
-            }
+        for (int j = 0; j < NPT; ++j) {
+            const int k = c0 + 2 * h + 4 * j;
+            on[j] = PM == 0 ? true : PM == 1 ? (j < NPT - 1 || h == 0) : 2 * j + h < np;
+            aoff[j] = (uint32_t)((k >> 3) * kALbo + m0 * 16 + (k & 7) * 2);
         }
+        const uint32_t gcol = (uint32_t)(c0 + 2 * h) * 8;   // byte offset of pair 0 in a guide row
+        const uint32_t g_row = (uint32_t)KW * 8;            // bytes of one guide row
         const float ninf = __int_as_float(0xff800000);
         const uint64_t magic2 = f2_pack(-8388608.f, -8388608.f);
         const uint64_t nkr2 = f2_pack(p.neg_kr, p.neg_kr);
+        const unsigned two_rho = (unsigned)(2 * p.rho);
+        // the two 16-bit weights of one column pair of one pixel
+        auto weights = [&](const uint4 q, uint32_t pcol, uint32_t pp, uint64_t sxy) -> uint32_t {
+            const uint32_t e0 = q.y + pp - 2u * __dp4a(q.x, pcol, 0u);
+            const uint32_t e1 = q.w + pp - 2u * __dp4a(q.z, pcol, 0u);
+            const uint64_t c = f2_add(u2_pack(e0, e1), magic2);
+            float a0, a1;
+            f2_unpack(f2_fma(c, nkr2, sxy), a0, a1);
+            return pack_16x2<BF16>(ex2_approx(a0), ex2_approx(a1));
+        };
         uint32_t gs = 0, gu = 0, t = 0;   // stage slot and use count of the next stage
         bool stop = false;
         for (TileWalk tw(p.ntx); tw.tile < p.ntiles && !stop; tw.next(), ++t) {
@@ -325,31 +348,48 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                 raise_abort(abort_flag, err, 6);
                 break;
             }
-            const uint2* gt = gtile + tb * (p.NH * KW);
-            // per pass and pair: spatial x-term, or -inf when the column is outside
-            // the window or the image or the pixel is outside the image
-            uint32_t pcol[kPasses], pp[kPasses];
-            int pty[kPasses];
-            float sx0[kPasses][NG], sx1[kPasses][NG];
-            uint64_t sxp[kPasses][NG];
+            const uint8_t* gt = (const uint8_t*)(gtile + tb * (p.NH * KW));
+            // the two pixels' colours and, per pair, the spatial x-terms, or -inf
+            // when the column is outside the window or the image (pixels outside
+            // the image only feed their own accumulator rows, never stored)
+            const uint2 pc0 = *(const uint2*)(gt + (ty + p.rho) * g_row + kcen * 8);
+            const uint2 pc1 = *(const uint2*)(gt + (ty + 1 + p.rho) * g_row + kcen * 8);
+            const uint32_t pcol0 = pc0.x, pp0 = pc0.y + kMagic, pcol1 = pc1.x, pp1 = pc1.y + kMagic;
+            uint64_t sxp[NPT];
 #pragma unroll
-            for (int i = 0; i < kPasses; ++i) {
-                pty[i] = pm[i] >> 4;
-                const bool pval = ty0 + pty[i] < p.H && tx0 + (pm[i] & 15) < p.W;
-                const uint2 pc = gt[(pty[i] + p.rho) * KW + kcen[i]];
-                pcol[i] = pc.x;
-                pp[i] = pc.y + kMagic;
-#pragma unroll
-                for (int pg = 0; pg < NG; ++pg) {
-                    const int d0 = kk[i][pg] - kcen[i], d1 = d0 + 1;
-                    const int x0 = xlo + kk[i][pg];
-                    sx0[i][pg] = (pval && d0 >= -p.rho && d0 <= p.rho && (unsigned)x0 < (unsigned)p.W)
+            for (int j = 0; j < NPT; ++j) {
+                const int k = c0 + 2 * h + 4 * j;
+                const int d0 = k - kcen, d1 = d0 + 1;
+                const int x0 = xlo + k;
+                const float s0 = (d0 >= -p.rho && d0 <= p.rho && (unsigned)x0 < (unsigned)p.W)
                                      ? (float)(d0 * d0) * p.neg_ks : ninf;
-                    sx1[i][pg] = (pval && d1 >= -p.rho && d1 <= p.rho && (unsigned)(x0 + 1) < (unsigned)p.W)
+                const float s1 = (d1 >= -p.rho && d1 <= p.rho && (unsigned)(x0 + 1) < (unsigned)p.W)
                                      ? (float)(d1 * d1) * p.neg_ks : ninf;
-                    sxp[i][pg] = f2_pack(sx0[i][pg], sx1[i][pg]);
-                }
+                sxp[j] = f2_pack(s0, s1);
             }
+            const uint8_t* gth = gt + gcol;
+            // one window row of the thread's pairs: which & 1 computes the upper
+            // pixel, which & 2 the lower one; a pixel not computed gets zeros
+            auto row_pairs = [&](uint8_t* arow, const uint8_t* grow, uint64_t sy0, uint64_t sy1, int which)
+                                 __attribute__((always_inline)) {
+                // at most 5 pairs at a time: their loads first
+#pragma unroll
+                for (int j0 = 0; j0 < NPT; j0 += 5) {
+                    uint4 q[5];
+                    if (which != 0) {
+#pragma unroll
+                        for (int i = 0; i < 5 && j0 + i < NPT; ++i)
+                            if (on[j0 + i]) q[i] = *(const uint4*)(grow + 32 * (j0 + i));
+                    }
+#pragma unroll
+                    for (int i = 0; i < 5 && j0 + i < NPT; ++i) {
+                        const int j = j0 + i;
+                        if (!on[j]) continue;
+                        *(uint32_t*)(arow + aoff[j]) = (which & 1) ? weights(q[i], pcol0, pp0, f2_add(sxp[j], sy0)) : 0u;
+                        *(uint32_t*)(arow + aoff[j] + 256) = (which & 2) ? weights(q[i], pcol1, pp1, f2_add(sxp[j], sy1)) : 0u;
+                    }
+                }
+            };
             const int hr_lo = max(0, p.rho - ty0);
             const int hr_hi = min(p.NH, p.H - ty0 + p.rho);
             for (int h0 = hr_lo; h0 < hr_hi; h0 += R) {
@@ -363,41 +403,24 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                     stop = true;
                     break;
                 }
-                // rows unrolled: a thread keeps up to kMaxR * kPasses independent
-                // weight chains in flight
+                uint8_t* ast = a_base + s * a_stage;
 #pragma unroll
-                for (int r = 0; r < kMaxR; ++r) {
+                for (int r = rq; r < kMaxR; r += 4) {
                     if (r >= nr) break;
                     const int hr = h0 + r;
-                    uint8_t* arow = a_base + s * a_stage + r * a_row;
-                    const uint2* grow = gt + hr * KW;
-                    // both passes of a warp cover pixel row warp >> 1, so the row
-                    // offset, its window test and the spatial y-term are shared
-                    const int dyr = hr - pty[0];   // row offset + rho
-                    if ((unsigned)dyr <= (unsigned)(2 * p.rho)) {   // uniform over the warp
-                        const uint64_t syp = sytab[dyr];
-#pragma unroll
-                        for (int i = 0; i < kPasses; ++i) {
-#pragma unroll
-                            for (int pg = 0; pg < NG; ++pg) {
-                                if (!on[i][pg]) continue;
-                                const uint4 q = *(const uint4*)(grow + kk[i][pg]);
-                                const uint32_t e0 = q.y + pp[i] - 2u * __dp4a(q.x, pcol[i], 0u);
-                                const uint32_t e1 = q.w + pp[i] - 2u * __dp4a(q.z, pcol[i], 0u);
-                                const uint64_t c = f2_add(u2_pack(e0, e1), magic2);
-                                float a0, a1;
-                                f2_unpack(f2_fma(c, nkr2, f2_add(sxp[i][pg], syp)), a0, a1);
-                                *(uint32_t*)(arow + aoff[i][pg]) = pack_16x2<BF16>(ex2_approx(a0), ex2_approx(a1));
-                            }
-                        }
-                    } else {
-                        // the window row is outside this pixel row's window: zero weights
-#pragma unroll
-                        for (int i = 0; i < kPasses; ++i)
-#pragma unroll
-                            for (int pg = 0; pg < NG; ++pg)
-                                if (on[i][pg]) *(uint32_t*)(arow + aoff[i][pg]) = 0u;
-                    }
+                    const int dy = hr - ty;   // row offset + rho of the upper pixel
+                    const bool in0 = (unsigned)dy <= two_rho, in1 = (unsigned)(dy - 1) <= two_rho;
+                    uint8_t* arow = ast + r * a_row;
+                    const uint8_t* grow = gth + hr * g_row;
+                    // uniform over the warp: both pixel rows, one of them, or neither
+                    if (in0 && in1)
+                        row_pairs(arow, grow, sytab[dy], sytab[dy - 1], 3);
+                    else if (in0)
+                        row_pairs(arow, grow, sytab[dy], 0ull, 1);
+                    else if (in1)
+                        row_pairs(arow, grow, 0ull, sytab[dy - 1], 2);
+                    else
+                        row_pairs(arow, grow, 0ull, 0ull, 0);
                 }
                 fence_proxy_async();
                 __syncwarp();
@@ -431,42 +454,51 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
             float dv[16];
             tmem_ld16(tbase + p.den_col, dv);
             const float inv = 1.f / dv[0];
-            float best = __int_as_float(0x7f800000), a_prev = 0.f, a_next = 0.f, last = 0.f;
+            const float finf = __int_as_float(0x7f800000);
+            float best = finf, a_prev = 0.f, a_next = 0.f, last = 0.f;
             int bidx = 0;
-            bool pending = false;
+            bool pend = false;   // the best is the previous chunk's last value: its successor comes next
             float* arow = (agg_out && pvalid) ? agg_out + ((size_t)py * p.W + px) * p.D : nullptr;
-            // WTA (smallest d on ties) keeping the neighbours of the running best
-            auto step = [&](float a, int d) {
-                if (pending) {
-                    a_next = a;
-                    pending = false;
-                }
-                if (a < best) {
-                    best = a;
-                    bidx = d;
-                    a_prev = last;
-                    pending = true;
-                }
-                last = a;
-            };
             const uint64_t inv2 = f2_pack(inv, inv);
-            for (int c0 = 0; c0 < p.N; c0 += 16) {
-                float v[16];
-                tmem_ld16(tbase + (uint32_t)c0, v);
+            // WTA (smallest d on ties) over chunks of 16 values, keeping the
+            // neighbours of the running best; two chunks per accumulator read
+            for (int c0 = 0; c0 < p.N; c0 += 32) {
+                float v[2][16];
+                if (c0 + 16 < p.N)
+                    tmem_ld16x2(tbase + (uint32_t)c0, tbase + (uint32_t)c0 + 16, v);
+                else
+                    tmem_ld16(tbase + (uint32_t)c0, v[0]);
 #pragma unroll
-                for (int i = 0; i < 16; i += 2) f2_unpack(f2_mul(f2_pack(v[i], v[i + 1]), inv2), v[i], v[i + 1]);
-                if (arow) {
+                for (int hc = 0; hc < 2; ++hc) {
+                    const int cb = c0 + 16 * hc;
+                    if (cb >= p.N) break;
+                    float* w = v[hc];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (c0 + i < p.D) arow[c0 + i] = v[i];
-                }
-                if (c0 + 16 <= p.D) {
+                    for (int i = 0; i < 16; i += 2) f2_unpack(f2_mul(f2_pack(w[i], w[i + 1]), inv2), w[i], w[i + 1]);
+                    if (arow) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) step(v[i], c0 + i);
-                } else {
+                        for (int i = 0; i < 16; ++i)
+                            if (cb + i < p.D) arow[cb + i] = w[i];
+                    }
+                    if (cb + 16 > p.D) {
+                        // disparities past D (zero cost rows) never win
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (c0 + i < p.D) step(v[i], c0 + i);
+                        for (int i = 0; i < 16; ++i)
+                            if (cb + i >= p.D) w[i] = finf;
+                    }
+                    a_next = pend ? w[0] : a_next;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const bool lt = w[i] < best;
+                        best = lt ? w[i] : best;
+                        bidx = lt ? cb + i : bidx;
+                        a_prev = lt ? (i > 0 ? w[i - 1] : last) : a_prev;
+                        if (i < 15)
+                            a_next = lt ? w[i + 1] : a_next;
+                        else
+                            pend = lt;
+                    }
+                    last = w[15];
                 }
             }
             tc_fence_before();
@@ -536,7 +568,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
             uint32_t gs = 0, gu = 0, t = 0;   // stage slot and use count
             // descriptors of stage 0, row 0, K-step 0; other positions add their
             // byte offset >> 4 to the 14-bit start-address field
-            const uint64_t a_desc0 = sdesc(smem_u32(a_base), 2048, 128);
+            const uint64_t a_desc0 = sdesc(smem_u32(a_base), kALbo, 128);
             const uint64_t b_desc0 = sdesc(smem_u32(b_base), lbo_b, 128);
             const uint64_t o_desc0 = sdesc(smem_u32(sm + L.ones_off), 256, 128);
             bool stop = false;
@@ -570,7 +602,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                         for (int k = 0; k < nk; ++k) {
                             umma_f16(dacc, ad, bd, p.idesc, accumulate);
                             accumulate = 1;
-                            ad += (2 * 2048) >> 4;
+                            ad += (2 * kALbo) >> 4;
                             bd += (2 * lbo_b) >> 4;
                         }
                     } else {
@@ -579,7 +611,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                             umma_f16(dacc, ad, bd, p.idesc, accumulate);
                             umma_f16(dacc + p.den_col, ad, o_desc0 + ((j * 2 * 256) >> 4), p.idesc16, accumulate);
                             accumulate = 1;
-                            ad += (2 * 2048) >> 4;
+                            ad += (2 * kALbo) >> 4;
                             bd += (2 * lbo_b) >> 4;
                         }
                     }
@@ -683,11 +715,11 @@ cudaError_t launch_hwd_to_xblock16(const float* in, int H, int W, int D, bool bf
 
 namespace {
 
-template <bool BF16, int NG>
+template <bool BF16, int NPT, int PM>
 cudaError_t run_tc(const CUtensorMap& map, const CUtensorMap& gmap, const TcParams& p, const TcSmem& L, int grid,
                    float* agg_out, int32_t* disp_int, float* disp_sub, int* err, cudaStream_t stream)
 {
-    cudaError_t e = cudaFuncSetAttribute(aggregate_tc_kernel<BF16, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(aggregate_tc_kernel<BF16, NPT, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)L.total);
     if (e != cudaSuccess) return e;
     // programmatic stream serialization: the kernel may start while the
@@ -703,7 +735,7 @@ cudaError_t run_tc(const CUtensorMap& map, const CUtensorMap& gmap, const TcPara
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     fbs::note_launch();
-    e = cudaLaunchKernelEx(&cfg, aggregate_tc_kernel<BF16, NG>, map, gmap, p, agg_out, disp_int, disp_sub, err);
+    e = cudaLaunchKernelEx(&cfg, aggregate_tc_kernel<BF16, NPT, PM>, map, gmap, p, agg_out, disp_int, disp_sub, err);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -819,18 +851,35 @@ cudaError_t launch_aggregate_tc(const void* cost, const uint2* rgbx, int H, int 
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
 
     const int grid = p.ntiles < num_sms ? p.ntiles : num_sms;
-    const int ng = (radius + 1 + 7) / 8;
-    switch ((bf16 ? 10 : 0) + ng) {
-    case 1: return run_tc<false, 1>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
-    case 2: return run_tc<false, 2>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
-    case 3: return run_tc<false, 3>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
-    case 4: return run_tc<false, 4>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
-    case 11: return run_tc<true, 1>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
-    case 12: return run_tc<true, 2>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
-    case 13: return run_tc<true, 3>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
-    case 14: return run_tc<true, 4>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
-    default: return cudaErrorInvalidValue;
-    }
+    // pairs of window columns per pixel and thread: ceil((radius + 1) / 2).
+    // Up to 8 the count is instantiated exactly (an odd radius uses every
+    // pair, an even one all but the last pair of phase 1); above, it is
+    // rounded up and the surplus pairs are switched off per pair.
+    const int npt = (radius + 2) / 2;
+    const int pm = (radius & 1) ? 0 : 1;
+#define FBS_TC_CASE(n)                                                                                         \
+    if (npt == n)                                                                                             \
+        return pm == 0 ? (bf16 ? run_tc<true, n, 0>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream)  \
+                               : run_tc<false, n, 0>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream)) \
+                       : (bf16 ? run_tc<true, n, 1>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream)  \
+                               : run_tc<false, n, 1>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream));
+    FBS_TC_CASE(1)
+    FBS_TC_CASE(2)
+    FBS_TC_CASE(3)
+    FBS_TC_CASE(4)
+    FBS_TC_CASE(5)
+    FBS_TC_CASE(6)
+    FBS_TC_CASE(7)
+    FBS_TC_CASE(8)
+#undef FBS_TC_CASE
+#define FBS_TC_CASE(n)                                                                                     \
+    if (npt <= n)                                                                                         \
+        return bf16 ? run_tc<true, n, 2>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream) \
+                    : run_tc<false, n, 2>(map, gmap, p, L, grid, agg_out, disp_int, disp_sub, err, stream);
+    FBS_TC_CASE(10)
+    FBS_TC_CASE(13)
+#undef FBS_TC_CASE
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace fbs
