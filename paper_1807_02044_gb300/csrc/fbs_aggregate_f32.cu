@@ -416,8 +416,7 @@ cudaError_t launch_kd(const float* cost, int ld, const uint8_t* guide, int H, in
                       float* disp_sub, cudaStream_t stream)
 {
     const size_t smem = smem_bytes<8 * KD>(rho);
-    cudaError_t e = cudaFuncSetAttribute(aggregate_f32_kernel<KD, VEC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = fbs::raise_smem_limit(aggregate_f32_kernel<KD, VEC>, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY);
     fbs::note_launch();
@@ -434,7 +433,7 @@ cudaError_t prepare_aggregate_f32_batched(int max_radius, size_t* smem_out)
 {
     const size_t smem = smem_bytes<64>(max_radius);
     *smem_out = smem;
-    return cudaFuncSetAttribute(aggregate_f32_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return fbs::raise_smem_limit(aggregate_f32_batched_kernel, (int)smem);
 }
 
 cudaError_t launch_aggregate_f32_batched(const BatchPair* pairs, int npairs, int nitems, int* counter, int grid,
@@ -453,7 +452,7 @@ cudaError_t launch_aggregate_band(const float* cost, int ld, const uint8_t* guid
     const float neg_ks = (float)(-log2e / ((double)sigma_s * sigma_s));
     const float neg_kr = (float)(-log2e / ((double)sigma_r * sigma_r));
     const size_t smem = smem_bytes<64>(radius);
-    cudaError_t e = cudaFuncSetAttribute(aggregate_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = fbs::raise_smem_limit(aggregate_band_kernel, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY);
     fbs::note_launch();

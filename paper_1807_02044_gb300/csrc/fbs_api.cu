@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -116,6 +117,31 @@ fbs_status ctx_error(fbs_ctx* ctx, fbs_status st, const char* msg) { return fail
 void ctx_count_launch(fbs_ctx* ctx, int kind, long long kernels) { ctx->launches[kind] += kernels; }
 
 thread_local long long tl_kernel_launches = 0;
+
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes)
+{
+    struct Entry {
+        const void* kernel;
+        int device;
+        size_t bytes;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> table;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (Entry& x : table)
+        if (x.kernel == kernel && x.device == dev) {
+            if (x.bytes >= bytes) return cudaSuccess;
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            if (e == cudaSuccess) x.bytes = bytes;
+            return e;
+        }
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) table.push_back({kernel, dev, bytes});
+    return e;
+}
 
 }  // namespace fbs
 

@@ -183,8 +183,7 @@ cudaError_t launch_conv_t(const __nv_bfloat16* in, const __nv_bfloat16* image, c
 {
     constexpr int KC = k_cores(CIN);
     const size_t smem = (size_t)KC * kM * 16 + (size_t)KC * N * 16 + 16;
-    cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<CIN, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = fbs::raise_smem_limit(conv3x3_tc_kernel<CIN, N>, (int)smem);
     if (e != cudaSuccess) return e;
     const int ntiles = (Hq * Wq + kM - 1) / kM;
     const int grid = ntiles < 2 * num_sms ? ntiles : 2 * num_sms;

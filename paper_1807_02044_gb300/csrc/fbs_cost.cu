@@ -773,8 +773,7 @@ cudaError_t launch_cost_xb(const CostScratch& sc, const uint8_t* left, const uin
     const int ndg = (D + 7) / 8;
     const int xbc = xb_blocks_per_cta(D);
     const size_t smem = cost_xb_smem_bytes(MODE, D);
-    cudaError_t e = cudaFuncSetAttribute(cost_xb_kernel<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = fbs::raise_smem_limit(cost_xb_kernel<MODE, T>, (int)smem);
     if (e != cudaSuccess) return e;
     if (MODE == 0) {
         // statistics planes and the packed guide first
@@ -816,8 +815,7 @@ cudaError_t launch_cost_kernel(const CostScratch& sc, const uint8_t* left, const
                                int C, int D, int ld, float tau, T* out, cudaStream_t stream)
 {
     const size_t smem = cost_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(cost_kernel<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = fbs::raise_smem_limit(cost_kernel<MODE, T>, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((W + kXS - 1) / kXS, H);
     fbs::note_launch();
@@ -843,8 +841,7 @@ size_t cost_kernel_smem() { return cost_smem_bytes(); }
 
 cudaError_t prepare_cost_batched()
 {
-    return cudaFuncSetAttribute(cost_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)cost_smem_bytes());
+    return fbs::raise_smem_limit(cost_batched_kernel, (int)cost_smem_bytes());
 }
 
 cudaError_t launch_stats_batched(const BatchPair* pairs, int npairs, int nitems, int* counter, int grid,
@@ -934,7 +931,7 @@ cudaError_t launch_cost_band(const CostScratch& sc, const uint8_t* left, const u
     cudaError_t e = launch_stats(sc, left, right, H, W, C, stream);
     if (e != cudaSuccess) return e;
     const size_t smem = cost_smem_bytes();
-    e = cudaFuncSetAttribute(cost_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = fbs::raise_smem_limit(cost_band_kernel, (int)smem);
     if (e != cudaSuccess) return e;
     const int ntx = (W + kAggTileX - 1) / kAggTileX, nty = (H + kAggTileY - 1) / kAggTileY;
     dim3 grid((W + kXS - 1) / kXS, H);
@@ -954,13 +951,13 @@ cudaError_t launch_cost_build_lr(const CostScratch& sc, const uint8_t* left, con
     const size_t smem = cost_smem_bytes();
     dim3 grid((W + kXS - 1) / kXS, H);
     if (mode == 0) {
-        e = cudaFuncSetAttribute(cost_lr_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = fbs::raise_smem_limit(cost_lr_kernel<0>, (int)smem);
         fbs::note_launch();
         if (e == cudaSuccess)
             cost_lr_kernel<0><<<grid, kThreads, smem, stream>>>(sc.g, sc.s, sc.rv, left, right, H, W, C, D, ld, tau,
                                                                 cost, cost_r);
     } else {
-        e = cudaFuncSetAttribute(cost_lr_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = fbs::raise_smem_limit(cost_lr_kernel<1>, (int)smem);
         fbs::note_launch();
         if (e == cudaSuccess)
             cost_lr_kernel<1><<<grid, kThreads, smem, stream>>>(sc.g, sc.s, sc.rv, left, right, H, W, C, D, ld, tau,

@@ -14,6 +14,16 @@ extern thread_local long long tl_kernel_launches;
 inline void note_launch() { ++tl_kernel_launches; }
 inline long long launch_count() { return tl_kernel_launches; }
 
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) costs a driver call per
+// launch; this raises a kernel's limit on the current device only when a
+// launch needs more than has been set there before (thread-safe).
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes);
+template <typename K>
+inline cudaError_t raise_smem_limit(K* kernel, size_t bytes)
+{
+    return raise_smem_limit((const void*)kernel, bytes);
+}
+
 // Cost volume rows are padded to a multiple of 4 floats so that one pixel's
 // disparity vector starts on a 16-byte boundary (vector loads, TMA, cp.async).
 inline int padded_ld(int D) { return (D + 3) & ~3; }
