@@ -105,6 +105,25 @@ fbs_status fbs_band_net_train_step(fbs_ctx *ctx, const uint8_t *left, const uint
                                    float *loss, float *grad, void *cuda_stream);
 
 /*
+ * Parity / debug entry point (not a method step; the paper has no
+ * counterpart): the intermediate tensors of the context's last
+ * fbs_band_net_forward or fbs_band_net_train_step call, as FP32 copies, so a
+ * test can check every layer on its own inputs.  P = ceil(H/4) * ceil(W/4)
+ * quarter pixels of that call; both buffers are device memory owned by the
+ * caller, channels innermost:
+ *   acts (nullable): P * (8 + 5 * 32 + 2) floats -- the network input [P][8]
+ *     (the six features rounded to BF16, two zero channels), the hidden
+ *     activations Y_1 .. Y_5 [P][32] each (BF16 values), the outputs [P][2];
+ *   grads (nullable; only after a training step, else FBS_ERR_INVALID_ARG):
+ *     P * (5 * 32 + 8) floats -- for layers 1..5 the BF16 gradient of the loss
+ *     with respect to the layer's pre-activation [P][32] each (the gradient
+ *     with respect to Y_l masked by its ReLU), then the BF16 gradient with
+ *     respect to the outputs [P][8] (two channels used).
+ * Returns FBS_ERR_INVALID_ARG (launching nothing) before any such call.
+ */
+fbs_status fbs_band_net_trace(fbs_ctx *ctx, float *acts, float *grads, void *cuda_stream);
+
+/*
  * The non-learned band source the paper names as future work (Sec. V):
  * reliable feature points suggest the search range of their neighbours.  A
  * quarter pixel is a feature point when its coarse cost margin (feature f3 of

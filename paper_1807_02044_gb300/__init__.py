@@ -94,6 +94,7 @@ SIGNATURES = {
     "fbs_band_net_forward": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P, _P, _P]),
     "fbs_band_net_train_step": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P, _I, _F, _P, _P, _P]),
     "fbs_band_limits": (_I, [_P, _P, _P, _I, _I, _I, _F, _P, _P, _P]),
+    "fbs_band_net_trace": (_I, [_P, _P, _P, _P]),
     "fbs_band_feature_points": (_I, [_P, _P, _P, _I, _I, _I, _I, _F, _P, _P, _P]),
     "fbs_compute_disparity_banded": (_I, [_P, _P, _P, _P, _I, _F, _P]),
     "fbs_compute_disparity_learned": (_I, [_P, _P, _I, _F, _P]),
@@ -342,6 +343,12 @@ def fbs_band_net_train_step(ctx, left, right, H, W, C, D, label_int, label_sub, 
     _check(ctx, lib().fbs_band_net_train_step(ctx, _addr(left), _addr(right), H, W, C, D, _addr(label_int),
                                              _addr(label_sub), half_band, lr, _addr(loss), _addr(grad),
                                              _stream(stream)))
+
+
+def fbs_band_net_trace(ctx, acts=None, grads=None, stream=None):
+    """Intermediate tensors of the last network call (see fbs_band.h): acts and
+    grads are float32 CUDA tensors of P*(8+5*32+2) and P*(5*32+8) elements."""
+    _check(ctx, lib().fbs_band_net_trace(ctx, _addr(acts), _addr(grads), _stream(stream)))
 
 
 def fbs_band_feature_points(ctx, left, right, H, W, C, D, margin_threshold, centre, conf, stream=None):

@@ -23,6 +23,13 @@ namespace {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+// BF16 tensor -> FP32 copy (fbs_band_net_trace)
+__global__ void bf16_to_f32_kernel(const __nv_bfloat16* __restrict__ src, float* __restrict__ dst, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = __bfloat162float(src[i]);
+}
+
 // ---- features (readings B1-B3) ---------------------------------------------------
 // Quarter-resolution intensity of both images: integer sum of the channel
 // sums over the 4x4 block, pixels clamped to the image.
@@ -318,6 +325,9 @@ struct fbs_band_state {
     __nv_bfloat16* images = nullptr;
     long long step = 0;
     bool ready = false;
+    // shape of the last forward or training call, for fbs_band_net_trace
+    int last_H = 0, last_W = 0, last_D = 0;
+    bool last_training = false;
 };
 
 namespace {
@@ -726,6 +736,10 @@ fbs_status fbs_band_net_forward(fbs_ctx* ctx, const uint8_t* left, const uint8_t
     const int Hq = (H + 3) / 4, Wq = (W + 3) / 4;
     if ((s = run_features(ctx, sc, left, right, H, W, C, D, nullptr, st)) != FBS_OK) return s;
     if ((s = run_forward(ctx, sc, Hq, Wq, st)) != FBS_OK) return s;
+    ctx->band->last_H = H;
+    ctx->band->last_W = W;
+    ctx->band->last_D = D;
+    ctx->band->last_training = false;
     cudaError_t e = cudaSuccess;
     if (centre || conf) {
         LaunchScope ls(ctx, FBS_KERNEL_NET, st);
@@ -759,6 +773,10 @@ fbs_status fbs_band_net_train_step(fbs_ctx* ctx, const uint8_t* left, const uint
     if ((s = run_features(ctx, sc, left, right, H, W, C, D, nullptr, st)) != FBS_OK) return s;
     if ((s = run_forward(ctx, sc, Hq, Wq, st)) != FBS_OK) return s;
     if ((s = run_backward(ctx, sc, H, W, D, label_int, label_sub, half_band, st)) != FBS_OK) return s;
+    b->last_H = H;
+    b->last_W = W;
+    b->last_D = D;
+    b->last_training = true;
     cudaError_t e = cudaSuccess;
     if (grad) e = cudaMemcpyAsync(grad, b->grad, (size_t)kParams * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, b->loss, 4, cudaMemcpyDeviceToHost, st);
@@ -777,6 +795,44 @@ fbs_status fbs_band_net_train_step(fbs_ctx* ctx, const uint8_t* left, const uint
     }
     if (e == cudaSuccess && (grad || loss)) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? FBS_OK : cuda_fail(ctx, e, "band training step");
+}
+
+fbs_status fbs_band_net_trace(fbs_ctx* ctx, float* acts, float* grads, void* cuda_stream)
+{
+    if (!ctx) return FBS_ERR_INVALID_ARG;
+    if (!acts && !grads) return fail(ctx, FBS_ERR_INVALID_ARG, "both outputs are NULL");
+    if (!ctx->band || ctx->band->last_H == 0)
+        return fail(ctx, FBS_ERR_INVALID_ARG, "no band-network forward or training call to trace");
+    fbs_band_state* b = ctx->band;
+    if (grads && !b->last_training)
+        return fail(ctx, FBS_ERR_INVALID_ARG, "gradients exist only after fbs_band_net_train_step");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = pick_stream(ctx, cuda_stream);
+    const int H = b->last_H, W = b->last_W, D = b->last_D;
+    const NetScratch sc = carve_net(ctx->band_ws, H, W, D, b->last_training, false);
+    const size_t P = (size_t)((H + 3) / 4) * ((W + 3) / 4);
+    cudaError_t e = cudaSuccess;
+    LaunchScope ls(ctx, FBS_KERNEL_OTHER, st);
+    auto convert = [&](const __nv_bfloat16* src, float* dst, size_t n) {
+        if (e != cudaSuccess) return;
+        fbs::note_launch();
+        const int blocks = (int)std::min<size_t>((n + 255) / 256, 1024);
+        fbs::bf16_to_f32_kernel<<<blocks, 256, 0, st>>>(src, dst, n);
+        e = cudaGetLastError();
+    };
+    if (acts) {
+        float* o = acts;
+        convert(sc.x0, o, P * 8);
+        o += P * 8;
+        for (int l = 0; l < 5; ++l, o += P * 32) convert(sc.y[l], o, P * 32);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(o, sc.out, P * 8, cudaMemcpyDeviceToDevice, st);
+    }
+    if (grads) {
+        float* o = grads;
+        for (int l = 0; l < 5; ++l, o += P * 32) convert(sc.g[l], o, P * 32);
+        convert(sc.g[5], o, P * 8);
+    }
+    return e == cudaSuccess ? FBS_OK : cuda_fail(ctx, e, "band network trace");
 }
 
 fbs_status fbs_band_feature_points(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C,

@@ -4,9 +4,10 @@ Features and band limits are decided in the kernels' precision with the same
 correctly rounded operations as the oracle, so they must match bit for bit.
 The band-restricted path must match the oracle's band definition with the
 tolerances of the plain path (integer winners identical except near ties,
-subpixel within 1e-3).  The network runs on BF16 operands: its outputs and
-gradients are compared with the FP64 network in relative L2 norm, with the
-bound derived in the test below.
+subpixel within 1e-3).  The network runs on BF16 operands: every layer's
+activations, outputs and gradients are compared element by element with the
+FP64 network on the same BF16 operands, on the kernels' own inputs to the
+layer, with the bounds derived below.
 """
 
 import numpy as np
@@ -160,24 +161,24 @@ def test_banded_full_size_sampled(fbs, oracle_mod):
 
 
 # ---------------------------------------------------------------------------
-# Network: forward outputs and gradients against the FP64 network
+# Network: every layer element by element, on the kernels' own inputs
 # ---------------------------------------------------------------------------
-# Two references.  (1) The FP64 network with every operand the kernels hold
-# in 16 bits rounded to BF16 at the same place (input, weights, activations,
-# backward gradients) and all sums in FP64: the kernels differ from it by the
-# FP32 accumulation (relative ~1e-6 over K = 288 products and the pixel sums)
-# and by the activations whose FP32 value falls on the other side of a BF16
-# rounding midpoint than the FP64 value (probability ~ 1e-6 / 2^-8 per
-# activation): each such flip moves one activation by one BF16 ulp and every
-# output in its 13 x 13 receptive field by a little.  So the bulk of the
-# outputs (the median error) must agree to 1e-4 of the output scale and the
-# whole map to EMU_TOL in relative L2 norm.  (2) The unrounded FP64 network:
-# the difference is the effect of BF16 operands, reported and bounded loosely
-# (unit roundoff u = 2^-9; six forward layers compound to ~6-12u in norm for
-# the outputs; a weight gradient passes through up to eleven roundings and
-# the ReLU masks of the forward pass).
-EMU_TOL = 1e-3
-EMU_OUT_TOL = 5e-3
+# fbs_band_net_trace reads back the kernels' input, hidden activations,
+# outputs and backward gradients.  Each layer is checked on the GPU's own
+# inputs to it against the FP64 network with the same BF16 operands
+# (tests/_band_ref.py): a hidden activation or a backward gradient must equal
+# the BF16 rounding of the FP64 value, except at "ambiguous" elements whose
+# FP64 value lies within the FP32 accumulation bound gamma(n) * sum|terms| of a
+# rounding boundary (n = 9 Cin + 1 terms of a convolution, 9 Cout of a data
+# gradient); there only the other rounding is allowed (a "flip", counted).
+# The outputs and the weight gradients (FP32 results) must lie within
+# gamma(n) * sum|terms| of the FP64 sum (n = 9 Cin + 1, or the number of
+# quarter pixels for a weight gradient) plus one FP32 rounding.
+#
+# End to end, against the unrounded FP64 network, the effect of the BF16
+# operands is reported and bounded loosely (unit roundoff u = 2^-9; six forward
+# layers compound to ~6-12u in norm for the outputs; a weight gradient passes
+# through up to eleven roundings and the ReLU masks of the forward pass).
 OUT_TOL = 0.03
 GRAD_TOL = 0.15
 
@@ -198,34 +199,56 @@ def test_param_layout_matches_the_oracle(fbs):
     assert fbs.fbs_band_net_param_count() == bn.param_count()
 
 
+def _trace_sizes(Hq, Wq):
+    P = Hq * Wq
+    return P * (8 + 5 * 32 + 2), P * (5 * 32 + 8)
+
+
 @pytest.mark.parametrize("H,W,D", [(96, 160, 64), (53, 77, 40)])
-def test_forward_matches_fp64_network(fbs, oracle_mod, H, W, D):
+def test_forward_layers_match_elementwise(fbs, oracle_mod, H, W, D):
+    from tests import _band_ref as br
     L, R = _rand_pair(H + W, H, W, 3, shift=12)
     theta = _params(1)
     Hq, Wq, _ = oracle_mod.quarter_shape(H, W, D)
     out = torch.empty((Hq, Wq, 2), dtype=torch.float32, device="cuda")
     centre = torch.empty((H, W), dtype=torch.float32, device="cuda")
     conf = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    acts = torch.empty(_trace_sizes(Hq, Wq)[0], dtype=torch.float32, device="cuda")
     with fbs.Context(0) as ctx:
         fbs.fbs_band_net_set_params(ctx.ctx, theta)
         fbs.fbs_band_net_forward(ctx.ctx, _dev(L), _dev(R), H, W, 3, D, out, centre, conf)
+        fbs.fbs_band_net_trace(ctx.ctx, acts, None)
         torch.cuda.synchronize()
         fbs.fbs_sync(ctx.ctx)
+    (x0, ys, O), _ = br.split_trace(acts.cpu().numpy(), None, Hq, Wq)
     feat, est = oracle_mod.band_features(L, R, D)
-    O, _ = bn.forward(theta.astype(np.float64), feat.astype(np.float64))
-    Oe, _ = bn.forward(theta.astype(np.float64), feat.astype(np.float64), bf16=True)
-    g = out.cpu().numpy()
+    # the network input: the six features rounded to BF16, two zero channels
+    assert np.array_equal(x0[..., :6], bn.round_bf16(feat)) and not x0[..., 6:].any()
+    assert np.array_equal(O, out.cpu().numpy().astype(np.float64))
+    th64 = theta.astype(np.float64)
+    X = x0[..., :6]
+    for l, (Wt, b) in enumerate(bn.unpack(th64)):
+        Z, S = br.conv_with_scale(X, bn.round_bf16(Wt), b)
+        eps = br.gamma(9 * bn.CIN[l] + 1) * S
+        if l < bn.N_LAYERS - 1:
+            defects, flips, amb = br.rounding_check(ys[l], Z, eps, relu=True)
+            print(f"layer {l + 1}: {ys[l].size} activations, {amb} ambiguous, {flips} flips, {defects} defects")
+            assert defects == 0, (l + 1, defects)
+            X = ys[l]
+        else:
+            err = np.abs(O - Z)
+            bound = eps + 2.0 ** -24 * np.abs(Z)
+            print(f"outputs: max |err| / bound {float((err / bound).max()):.3f}")
+            assert np.all(err <= bound)
+    # end to end against the unrounded FP64 network (loose, reported)
+    Of, _ = bn.forward(th64, feat.astype(np.float64))
     for c in range(2):
-        scale = np.sqrt(np.mean(Oe[..., c] ** 2))
-        med = np.median(np.abs(g[..., c] - Oe[..., c])) / scale
-        emu = np.linalg.norm(g[..., c] - Oe[..., c]) / np.linalg.norm(Oe[..., c])
-        err = np.linalg.norm(g[..., c] - O[..., c]) / np.linalg.norm(O[..., c])
-        print(f"output {c}: vs BF16-operand FP64 net median {med:.2e} rel. L2 {emu:.2e}; vs FP64 net {err:.2e}")
-        assert med <= 1e-4, (c, med)
-        assert emu <= EMU_OUT_TOL, (c, emu)
-        assert err <= OUT_TOL, (c, err)
+        e2e = np.linalg.norm(O[..., c] - Of[..., c]) / np.linalg.norm(Of[..., c])
+        print(f"output {c}: rel. L2 vs the unrounded FP64 network {e2e:.2e}")
+        assert e2e <= OUT_TOL, (c, e2e)
     # the head: centre = 4 (e* + o0) in FP32 and conf = sigmoid(z) of the
     # quarter pixel (x / 4, y / 4), from the kernel's own outputs
+    g = out.cpu().numpy()
     up = bn.upsample(np.arange(Hq * Wq).reshape(Hq, Wq), H, W)
     o0 = g[..., 0].ravel()[up]
     z = g[..., 1].ravel()[up]
@@ -234,7 +257,8 @@ def test_forward_matches_fp64_network(fbs, oracle_mod, H, W, D):
     np.testing.assert_allclose(conf.cpu().numpy(), 1.0 / (1.0 + np.exp(-z.astype(np.float64))), rtol=0, atol=1e-6)
 
 
-def test_gradients_match_fp64_network(fbs, oracle_mod):
+def test_backward_layers_match_elementwise(fbs, oracle_mod):
+    from tests import _band_ref as br
     H, W, D, h = 120, 176, 64, 8
     L, R = _rand_pair(5, H, W, 3, shift=20)
     theta = _params(2)
@@ -244,33 +268,66 @@ def test_gradients_match_fp64_network(fbs, oracle_mod):
     ls = (li + rng.uniform(-0.5, 0.5, (H, W))).astype(np.float32)
     grad = np.zeros(bn.param_count(), np.float32)
     loss = np.zeros(1, np.float32)
+    Hq, Wq, _ = oracle_mod.quarter_shape(H, W, D)
+    na, ng = _trace_sizes(Hq, Wq)
+    acts = torch.empty(na, dtype=torch.float32, device="cuda")
+    grads = torch.empty(ng, dtype=torch.float32, device="cuda")
     with fbs.Context(0) as ctx:
         fbs.fbs_band_net_set_params(ctx.ctx, theta)
         fbs.fbs_band_net_train_step(ctx.ctx, _dev(L), _dev(R), H, W, 3, D, _dev(li), _dev(ls), h, 0.0, loss, grad)
+        fbs.fbs_band_net_trace(ctx.ctx, acts, grads)
+        torch.cuda.synchronize()
         fbs.fbs_sync(ctx.ctx)
+    (x0, ys, O), (gs, go) = br.split_trace(acts.cpu().numpy(), grads.cpu().numpy(), Hq, Wq)
     feat, est = oracle_mod.band_features(L, R, D)
     th64 = theta.astype(np.float64)
-    res = {}
-    for mode in (True, False):
-        O, acts = bn.forward(th64, feat.astype(np.float64), bf16=mode)
-        cq, _ = bn.centre_conf(O, est)
-        t, y = oracle_mod.band_targets(li, ls.astype(np.float64), D, h, cq)
-        Lref, dO = bn.loss_and_output_grad(O, est, t, y)
-        res[mode] = (Lref, bn.backward(th64, acts, dO, bf16=mode))
-    Le, ge = res[True]
-    Lf, gf = res[False]
-    assert abs(loss[0] - Le) <= EMU_TOL * abs(Le)
+    layers = bn.unpack(th64)
+    N = Hq * Wq
+    # loss and its gradient from the GPU's own outputs (targets from its centre)
+    cq = 4.0 * (est + O[..., 0])
+    t, y = oracle_mod.band_targets(li, ls, D, h, cq)
+    Lref, dO = bn.loss_and_output_grad(O, est, t, y)
+    assert abs(loss[0] - Lref) <= 1e-5 * abs(Lref) + 1e-7, (loss[0], Lref)
+    eps_o = np.stack([2.0 ** -20 * 4.0 * np.abs(y) * (np.abs(cq) + np.abs(t) + 1.0),
+                      2.0 ** -20 * (1.0 + np.abs(y))], axis=-1) / N
+    defects, flips, amb = br.rounding_check(go[..., :2], dO, eps_o, relu=False)
+    print(f"output gradient: {go[..., :2].size} values, {amb} ambiguous, {flips} flips, {defects} defects")
+    assert defects == 0 and not go[..., 2:].any()
+    inputs = [x0[..., :6]] + ys          # inputs[l] is the input of layer l + 1
+    offs = np.cumsum([0] + [9 * ci * co + co for ci, co in zip(bn.CIN, bn.COUT)])
+    G = go[..., :2]
+    for l in range(bn.N_LAYERS - 1, -1, -1):
+        ci, co = bn.CIN[l], bn.COUT[l]
+        dW, db, dWa, dba = br.weight_grad_with_scale(inputs[l], G)
+        gW = grad[offs[l]: offs[l] + 9 * ci * co].reshape(3, 3, ci, co).astype(np.float64)
+        gb = grad[offs[l] + 9 * ci * co: offs[l + 1]].astype(np.float64)
+        bW = br.gamma(N) * dWa + 2.0 ** -24 * np.abs(dW)
+        bb = br.gamma(N) * dba + 2.0 ** -24 * np.abs(db)
+        rW = float((np.abs(gW - dW) / np.maximum(bW, 1e-300)).max())
+        print(f"layer {l + 1}: weight gradient max |err| / bound {rW:.3f}")
+        assert np.all(np.abs(gW - dW) <= bW), l + 1
+        assert np.all(np.abs(gb - db) <= bb), l + 1
+        if l == 0:
+            break
+        dX, dXa = br.conv_transpose_with_scale(G, bn.round_bf16(layers[l][0]))
+        mask = inputs[l] > 0
+        eps = br.gamma(9 * co) * dXa
+        defects, flips, amb = br.rounding_check(gs[l - 1], dX * mask, eps * mask, relu=False)
+        print(f"layer {l}: {gs[l - 1].size} backward gradients, {amb} ambiguous, {flips} flips, {defects} defects")
+        assert defects == 0, (l, defects)
+        G = gs[l - 1]
+    # end to end against the unrounded FP64 network (loose, reported)
+    Of, actsf = bn.forward(th64, feat.astype(np.float64))
+    cqf, _ = bn.centre_conf(Of, est)
+    tf, yf = oracle_mod.band_targets(li, ls.astype(np.float64), D, h, cqf)
+    Lf, dOf = bn.loss_and_output_grad(Of, est, tf, yf)
+    gf = bn.backward(th64, actsf, dOf)
     assert abs(loss[0] - Lf) <= OUT_TOL * abs(Lf)
-    o = 0
     for l, (ci, co) in enumerate(zip(bn.CIN, bn.COUT)):
-        n = 9 * ci * co + co
-        g = grad[o:o + n]
-        emu = np.linalg.norm(g - ge[o:o + n]) / np.linalg.norm(ge[o:o + n])
-        err = np.linalg.norm(g - gf[o:o + n]) / np.linalg.norm(gf[o:o + n])
-        print(f"layer {l + 1}: rel. L2 vs BF16-operand FP64 net {emu:.2e}, vs FP64 net {err:.2e}")
-        assert emu <= EMU_TOL, (l, emu)
+        g = grad[offs[l]: offs[l + 1]]
+        err = np.linalg.norm(g - gf[offs[l]: offs[l + 1]]) / np.linalg.norm(gf[offs[l]: offs[l + 1]])
+        print(f"layer {l + 1}: rel. L2 vs the unrounded FP64 network {err:.2e}")
         assert err <= GRAD_TOL, (l, err)
-        o += n
 
 
 def test_training_steps_reduce_the_loss(fbs, oracle_mod):

@@ -295,3 +295,43 @@ def test_feature_points_on_a_shift_by_four_k(oracle_mod):
     c, conf = oracle_mod.band_feature_points(L, R, D, 0.05)
     inner = (slice(20, -20), slice(4 * k + 24, -20))
     assert np.all(conf[inner] == 1.0) and np.all(c[inner] == 4.0 * k)
+
+
+def test_layer_check_helper_separates_flips_from_defects():
+    """The element-wise rule of tests/_band_ref.py: the BF16 rounding of the
+    FP64 value passes; the other rounding passes only where the value lies
+    within the accumulation bound of a rounding midpoint (a flip); any other
+    value is a defect."""
+    from tests import _band_ref as br
+    one_ulp = 2.0 ** -7                        # BF16 spacing in [1, 2)
+    mid = 1.0 + 0.5 * one_ulp                  # midpoint between 1 and 1 + ulp
+    z = np.array([1.3, mid - 1e-6, mid + 1e-6, mid - 1e-3, 2.0 ** -30, -1e-12])
+    eps = np.full(z.shape, 1e-5)
+    exact = bn.round_bf16(np.maximum(z, 0.0))
+    assert br.rounding_check(exact, z, eps, relu=True)[0] == 0
+    # the other rounding next to the midpoint: a flip, not a defect
+    got = exact.copy()
+    got[1] = 1.0 + one_ulp
+    got[2] = 1.0
+    d, f, a = br.rounding_check(got, z, eps, relu=True)
+    assert (d, f) == (0, 2) and a >= 2
+    # the other rounding far from the midpoint: a defect
+    got = exact.copy()
+    got[3] = 1.0 + one_ulp
+    assert br.rounding_check(got, z, eps, relu=True)[0] == 1
+    # a wrong value (a mis-indexed tap would give one): a defect
+    got = exact.copy()
+    got[0] = bn.round_bf16(np.array([1.5]))[0]
+    assert br.rounding_check(got, z, eps, relu=True)[0] == 1
+    # at the ReLU boundary both 0 and a small positive value pass
+    got = exact.copy()
+    got[4] = 0.0
+    got[5] = bn.round_bf16(np.array([1e-12]))[0]
+    assert br.rounding_check(got, z, np.full(z.shape, 1e-9), relu=True)[0] == 0
+    # signed values without ReLU
+    s = np.array([-1.3, -(mid - 1e-6)])
+    e2 = np.full(2, 1e-5)
+    assert br.rounding_check(bn.round_bf16(s), s, e2, relu=False)[0] == 0
+    assert br.rounding_check(np.array([bn.round_bf16(np.array([-1.3]))[0], -(1.0 + one_ulp)]), s, e2,
+                             relu=False)[:2] == (0, 1)
+    assert br.rounding_check(np.array([1.3, -1.0]), s, e2, relu=False)[0] == 1
