@@ -111,7 +111,7 @@ fbs_status fbs_compute_disparity(fbs_ctx *ctx, const uint8_t *left, const uint8_
  * the results have arrived.  FP32 contexts, or pageable buffers: the images
  * are copied to device staging and the maps back, on the context's stream.
  * BF16 / FP16 contexts with page-locked buffers the GPU can address (all four,
- * or the ones given): no staging copies -- the cost build reads the images
+ * or the ones given): no staging copies -- the cost kernel reads the images
  * from host memory and the aggregation writes the maps there directly.
  */
 fbs_status fbs_compute_disparity_host(fbs_ctx *ctx, const uint8_t *left, const uint8_t *right,

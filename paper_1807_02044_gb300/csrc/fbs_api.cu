@@ -27,12 +27,14 @@ fbs_status run_path_tc(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, 
         return fail(ctx, FBS_ERR_UNSUPPORTED, "tensor-core aggregation supports D <= 256 and radius <= 24 (got D=%d, radius=%d)",
                     D, radius);
     const bool bf16 = ctx->opt.prec == FBS_PREC_BF16;
-    // scratch: [packed guide | statistics planes | 16-bit x-blocked volume]; the
-    // cost build writes all three
-    fbs_status s = ensure(ctx, &ctx->ws, &ctx->ws_bytes, fbs::tc_cost_scratch_bytes(H, W, D), "cost volume");
+    // scratch: [packed guide | 16-bit x-blocked volume]; the cost kernel writes both
+    const size_t rgbx = fbs::rgbx_bytes(H, W);
+    const size_t need = rgbx + fbs::xblock16_bytes(H, W, D);
+    fbs_status s = ensure(ctx, &ctx->ws, &ctx->ws_bytes, need, "cost volume");
     if (s != FBS_OK) return s;
-    void* cost = nullptr;
-    const fbs::CostScratch sc = fbs::carve_tc_cost_scratch(ctx->ws, H, W, &cost);
+    fbs::CostScratch sc{};
+    sc.rgbx = (uint2*)ctx->ws;
+    void* cost = (uint8_t*)ctx->ws + rgbx;
     cudaError_t e;
     {
         LaunchScope ls(ctx, FBS_KERNEL_COST, st);

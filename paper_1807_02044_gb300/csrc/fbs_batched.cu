@@ -263,13 +263,13 @@ fbs_status run_plan(fbs_ctx* ctx, const std::string& sig, int n, const fbs_pair*
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Scratch of one pair.  Tensor cores: [packed guide | statistics | 16-bit
-// x-blocked volume]; FP32: [statistics | FP32 volume, row pitch padded_ld(D)].
+// Scratch of one pair.  Tensor cores: [packed guide | 16-bit x-blocked
+// volume]; FP32: [statistics | FP32 volume, row pitch padded_ld(D)].
 size_t pair_bytes(const fbs_pair& q, bool tc)
 {
     if (!tc) return align256(fbs::cost_scratch_bytes(q.H, q.W)) +
                     align256(sizeof(float) * (size_t)q.H * q.W * fbs::padded_ld(q.D));
-    return align256(fbs::tc_cost_scratch_bytes(q.H, q.W, q.D));
+    return align256(fbs::rgbx_bytes(q.H, q.W)) + align256(fbs::xblock16_bytes(q.H, q.W, q.D));
 }
 
 fbs_status ensure_branches(fbs_ctx* ctx)
@@ -328,8 +328,9 @@ fbs_status build_branch_graph(fbs_ctx* ctx, int n, const fbs_pair* pairs, int nb
             g->kernels[FBS_KERNEL_AGG_F32] += fbs::launch_count() - k0;
             continue;
         }
-        void* cost = nullptr;
-        const fbs::CostScratch sc = fbs::carve_tc_cost_scratch(base, q.H, q.W, &cost);
+        fbs::CostScratch sc{};
+        sc.rgbx = (uint2*)base;
+        void* cost = base + align256(fbs::rgbx_bytes(q.H, q.W));
         e = fbs::launch_cost_build_xblock16(sc, q.left, q.right, q.H, q.W, q.C, q.D, mode, q.tau, bf16, cost, s);
         g->kernels[FBS_KERNEL_COST] += fbs::launch_count() - k0;
         k0 = fbs::launch_count();

@@ -482,17 +482,13 @@ __host__ __device__ inline size_t cost_xb_stage_ints(int mode, int D)
 template <int MODE, typename T>
 __global__ void __launch_bounds__(kXbThreads, 2)
 cost_xb_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int H, int W, int C, int D, float tau,
-               T* __restrict__ out, uint2* __restrict__ rgbx, const int16_t* __restrict__ gplane,
-               const int* __restrict__ splane, const float* __restrict__ rvplane)
+               T* __restrict__ out, uint2* __restrict__ rgbx)
 {
     extern __shared__ int sm_xb[];
     // let a programmatically launched successor (the tensor-core aggregation)
     // start its set-up once every CTA of this grid has started; it waits for
     // this grid's completion before it reads anything this kernel writes
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    // NCC reads the statistics planes of the pre-pass that precedes this
-    // kernel (possibly still running when this one was launched)
-    if (MODE == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int ndg = (D + 7) >> 3;
     const int xbc = xb_blocks_per_cta(D);
@@ -517,36 +513,63 @@ cost_xb_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int
     uint32_t* pl = (uint32_t*)sm_xb;   // TAD: left pixels [Lp]
     uint32_t* pr = pl + Lp;            // TAD: right pixels [Lr], origin rb
 
-    // staging.  NCC: grey values (channel sums) of rows y-1..y+1 at clamped
-    // columns and the block statistics S, 1/sqrt(9Q - S^2) of row y, read from
-    // the pre-pass planes (the left image's packed guide comes from there too).
-    // TAD: the packed colours of row y and the left image's guide.
+    // staging: grey values (channel sums) of rows y-1..y+1 at clamped columns,
+    // then each staged block centre's statistics S, 1/sqrt(9Q - S^2) exactly as
+    // grey_stats_kernel computes them, and the left pixels' packed guide
+    auto grey = [&](const uint8_t* img, int yy, int x) -> int {
+        const uint8_t* q = img + ((size_t)yy * W + x) * C;
+        return C == 3 ? (int)q[0] + (int)q[1] + (int)q[2] : (int)q[0];
+    };
     auto colour = [&](const uint8_t* img, int x) -> uint32_t {
         const uint8_t* q = img + ((size_t)y * W + clampi(x, 0, W - 1)) * C;
         return C == 3 ? (uint32_t)q[0] | ((uint32_t)q[1] << 8) | ((uint32_t)q[2] << 16) : (uint32_t)q[0];
     };
     if (MODE == 0) {
-        const size_t plane = (size_t)H * W;
-        const int y0 = clampi(y - 1, 0, H - 1), y2 = clampi(y + 1, 0, H - 1);
-        const size_t rows[3] = {(size_t)y0 * W, (size_t)y * W, (size_t)y2 * W};
         for (int c = tid; c < nl; c += nthr) {
             const int x = clampi(x0 - 1 + c, 0, W - 1);
 #pragma unroll
-            for (int j = 0; j < 3; ++j) gl[j * Ll + skew(c)] = gplane[rows[j] + x];
+            for (int j = 0; j < 3; ++j) gl[j * Ll + skew(c)] = grey(L, clampi(y - 1 + j, 0, H - 1), x);
         }
         for (int c = tid; c < nr; c += nthr) {
             const int x = clampi(rb + c, 0, W - 1);
 #pragma unroll
-            for (int j = 0; j < 3; ++j) gr[j * Lr + skew(c)] = gplane[plane + rows[j] + x];
-            // right centre rb + c (only centres inside the image feed stored costs)
-            sr[skew(c)] = splane[plane + rows[1] + x];
-            rr[skew(c)] = rvplane[plane + rows[1] + x];
+            for (int j = 0; j < 3; ++j) gr[j * Lr + skew(c)] = grey(R, clampi(y - 1 + j, 0, H - 1), x);
         }
+        __syncthreads();
+        auto stats = [&](const int* g, int Lg, int c, int* s_out, float* rv_out) {
+            int sum = 0, sq = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = -1; k <= 1; ++k) {
+                    const int v = g[j * Lg + skew(c + k)];
+                    sum += v;
+                    sq += v * v;
+                }
+            const int var = 9 * sq - sum * sum;
+            s_out[skew(c)] = sum;
+            rv_out[skew(c)] = var > 0 ? rsqrtf((float)var) : 0.f;
+        };
         for (int i = tid; i < npx; i += nthr) {
-            const int x = min(x0 + i, W - 1);
-            sl[skew(i)] = splane[rows[1] + x];
-            rl[skew(i)] = rvplane[rows[1] + x];
+            // left centre x0 + i sits at staged column i + 1
+            int sum = 0, sq = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const int v = gl[j * Ll + skew(i + k)];
+                    sum += v;
+                    sq += v * v;
+                }
+            const int var = 9 * sq - sum * sum;
+            sl[skew(i)] = sum;
+            rl[skew(i)] = var > 0 ? rsqrtf((float)var) : 0.f;
+            if (x0 + i < W) {
+                const uint32_t col = colour(L, x0 + i);
+                rgbx[(size_t)y * rgbx_pitch(W) + x0 + i] = make_uint2(col, (uint32_t)__dp4a(col, col, 0u));
+            }
         }
+        for (int c = 1 + tid; c < nr - 1; c += nthr) stats(gr, Lr, c, sr, rr);
     } else {
         for (int c = tid; c < npx; c += nthr) {
             const uint32_t col = colour(L, x0 + c);
@@ -720,52 +743,6 @@ size_t cost_xb_smem_bytes(int mode, int D)
     return sizeof(int) * cost_xb_stage_ints(mode, D) + (size_t)nwarps * kXbWarpRows * 16;
 }
 
-// Statistics pre-pass of the 16-bit cost build: per pixel of both images the
-// grey value g, its 3x3 block sum S and 1/sqrt(9 Q - S^2) (0 for a flat
-// block), with the same clamping and rounding as grey_stats_kernel, and the
-// left image's packed guide.  One CTA per 256 pixels of one row of one image:
-// the grey values of rows y-1 .. y+1 are staged once in shared memory (each
-// image byte is loaded once per CTA), then every pixel sums its block there.
-constexpr int kStatX = 256;
-__global__ void __launch_bounds__(kStatX)
-grey_stats_rows_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int H, int W, int C,
-                       int16_t* __restrict__ g_out, int* __restrict__ s_out, float* __restrict__ rv_out,
-                       uint2* __restrict__ rgbx)
-{
-    __shared__ int gs[3][kStatX + 2];
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int img = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * kStatX;
-    const uint8_t* src = img == 0 ? L : R;
-    for (int i = threadIdx.x; i < 3 * (kStatX + 2); i += kStatX) {
-        const int j = i / (kStatX + 2), c = i - j * (kStatX + 2);
-        const int yy = clampi(y - 1 + j, 0, H - 1), xx = clampi(x0 - 1 + c, 0, W - 1);
-        const uint8_t* p = src + ((size_t)yy * W + xx) * C;
-        gs[j][c] = C == 3 ? (int)p[0] + (int)p[1] + (int)p[2] : (int)p[0];
-    }
-    __syncthreads();
-    const int x = x0 + threadIdx.x;
-    if (x >= W) return;
-    int sum = 0, sq = 0;
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int v = gs[j][threadIdx.x + k];
-            sum += v;
-            sq += v * v;
-        }
-    const int var = 9 * sq - sum * sum;
-    const size_t o = (size_t)img * H * W + (size_t)y * W + x;
-    g_out[o] = (int16_t)gs[1][threadIdx.x + 1];
-    s_out[o] = sum;
-    rv_out[o] = var > 0 ? rsqrtf((float)var) : 0.f;
-    if (img == 0 && rgbx != nullptr) {
-        const uint8_t* p = src + ((size_t)y * W + x) * C;
-        const uint32_t c = C == 3 ? (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) : (uint32_t)p[0];
-        rgbx[(size_t)y * rgbx_pitch(W) + x] = make_uint2(c, (uint32_t)__dp4a(c, c, 0u));
-    }
-}
-
 template <int MODE, typename T>
 cudaError_t launch_cost_xb(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H, int W, int C,
                            int D, float tau, T* out, cudaStream_t stream)
@@ -775,32 +752,11 @@ cudaError_t launch_cost_xb(const CostScratch& sc, const uint8_t* left, const uin
     const size_t smem = cost_xb_smem_bytes(MODE, D);
     cudaError_t e = fbs::raise_smem_limit(cost_xb_kernel<MODE, T>, (int)smem);
     if (e != cudaSuccess) return e;
-    if (MODE == 0) {
-        // statistics planes and the packed guide first
-        fbs::note_launch();
-        grey_stats_rows_kernel<<<dim3((W + kStatX - 1) / kStatX, H, 2), kStatX, 0, stream>>>(
-            left, right, H, W, C, sc.g, sc.s, sc.rv, sc.rgbx);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
     const int nxb = (W + 7) / 8;
-    const int nthr = (xbc * ndg + 31) / 32 * 32;   // whole warps (the write-out shuffles need all lanes)
-    // programmatic stream serialization: the cost kernel may start while the
-    // statistics pre-pass ends (it waits for the pre-pass before reading)
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((nxb + xbc - 1) / xbc, H);
-    cfg.blockDim = dim3(nthr);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = MODE == 0 ? 1 : 0;
+    dim3 grid((nxb + xbc - 1) / xbc, H);
     fbs::note_launch();
-    e = cudaLaunchKernelEx(&cfg, cost_xb_kernel<MODE, T>, left, right, H, W, C, D, tau, out, sc.rgbx,
-                           (const int16_t*)sc.g, (const int*)sc.s, (const float*)sc.rv);
-    if (e != cudaSuccess) return e;
+    const int nthr = (xbc * ndg + 31) / 32 * 32;   // whole warps (the write-out shuffles need all lanes)
+    cost_xb_kernel<MODE, T><<<grid, nthr, smem, stream>>>(left, right, H, W, C, D, tau, out, sc.rgbx);
     return cudaGetLastError();
 }
 
@@ -868,20 +824,6 @@ size_t cost_scratch_bytes(int H, int W)
 }
 
 size_t rgbx_bytes(int H, int W) { return ((size_t)H * rgbx_pitch(W) * 8 + 255) & ~(size_t)255; }
-
-size_t tc_cost_scratch_bytes(int H, int W, int D)
-{
-    return rgbx_bytes(H, W) + cost_scratch_bytes(H, W) + ((xblock16_bytes(H, W, D) + 255) & ~(size_t)255);
-}
-
-CostScratch carve_tc_cost_scratch(void* base, int H, int W, void** cost)
-{
-    uint8_t* p = (uint8_t*)base;
-    CostScratch sc = carve_cost_scratch(p + rgbx_bytes(H, W), H, W);
-    sc.rgbx = (uint2*)p;
-    *cost = p + rgbx_bytes(H, W) + cost_scratch_bytes(H, W);
-    return sc;
-}
 
 __global__ void pack_rgbx_kernel(const uint8_t* __restrict__ img, int H, int W, int C, uint2* __restrict__ out)
 {
@@ -974,10 +916,8 @@ cudaError_t launch_cost_build_xblock16(const CostScratch& sc, const uint8_t* lef
                                        int W, int C, int D, int mode, float tau, bool bf16, void* cost,
                                        cudaStream_t stream)
 {
-    // NCC: the statistics pre-pass (planes of sc and the packed guide sc.rgbx),
-    // then the costs and pad rows; TAD: one launch (costs, pad rows, guide)
+    // one launch: statistics, costs, pad rows and the packed guide (sc.rgbx)
     if (D > 256 || !sc.rgbx) return cudaErrorInvalidValue;   // serves the tensor-core form only
-    if (mode == 0 && (!sc.g || !sc.s || !sc.rv)) return cudaErrorInvalidValue;
     if (mode == 0)
         return bf16 ? launch_cost_xb<0>(sc, left, right, H, W, C, D, tau, (__nv_bfloat16*)cost, stream)
                     : launch_cost_xb<0>(sc, left, right, H, W, C, D, tau, (__half*)cost, stream);

@@ -61,20 +61,15 @@ cudaError_t launch_cost_build_lr(const CostScratch& sc, const uint8_t* left, con
 // zero, and (when Dp > round_up(D,16)) row round_up(D,16) all ones followed by
 // zero rows -- the ones row lets the tensor-core product also form the sum of
 // the weights.  Columns x >= W of the last block are 0.  bf16 selects
-// __nv_bfloat16, otherwise __half.  NCC: a statistics pre-pass fills the
-// planes of sc and the left image's packed guide sc.rgbx, then the cost
-// kernel reads them; TAD: one kernel, which also writes sc.rgbx.  sc.rgbx is
-// required (and the planes for NCC).  D <= 256.
+// __nv_bfloat16, otherwise __half.  One kernel, which also writes the left
+// image's packed guide to sc.rgbx (required; the statistics planes of sc are
+// not used).  D <= 256.
 __host__ __device__ inline int tc_block_rows(int D)
 {
     const int n = (D + 15) / 16 * 16;
     return n + 16 <= 256 ? n + 16 : n;
 }
 inline size_t xblock16_bytes(int H, int W, int D) { return (size_t)H * ((W + 7) / 8) * tc_block_rows(D) * 8 * 2; }
-// Scratch of the 16-bit cost build: [packed guide | statistics planes |
-// x-blocked volume], each part 256-byte aligned; carve sets *cost to the volume.
-size_t tc_cost_scratch_bytes(int H, int W, int D);
-CostScratch carve_tc_cost_scratch(void* base, int H, int W, void** cost);
 cudaError_t launch_cost_build_xblock16(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H,
                                        int W, int C, int D, int mode, float tau, bool bf16, void* cost,
                                        cudaStream_t stream);

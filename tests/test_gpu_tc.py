@@ -161,11 +161,11 @@ def test_tc_f16_1280x960_d128_r15(fbs, oracle_mod):
 
 
 @pytest.mark.parametrize("prec,expect", [("f32", {"COST": 2, "AGG_F32": 1, "AGG_TC": 0}),
-                                         ("bf16", {"COST": 2, "AGG_F32": 0, "AGG_TC": 1})])
+                                         ("bf16", {"COST": 1, "AGG_F32": 0, "AGG_TC": 1})])
 def test_kernel_accounting_counts_every_launch(fbs, prec, expect):
-    """fbs_profile_read reports kernels, not calls: both forms launch the
-    statistics pre-pass and the cost kernel (the 16-bit one also writes the
-    pad rows, the pre-pass the packed guide), then the FP32 or the
+    """fbs_profile_read reports kernels, not calls: the FP32 form launches the
+    statistics pre-pass, the cost kernel and the aggregation; the 16-bit form
+    one cost kernel (statistics, pad rows and guide included) and the
     tensor-core aggregation."""
     rng = np.random.default_rng(3)
     L = rng.integers(0, 256, size=(40, 72, 3)).astype(np.uint8)
