@@ -13,4 +13,6 @@ from .scenes import (  # noqa: F401
     shifted_texture_pair,
     constant_image,
     random_batch_specs,
+    render_layers,
+    regions,
 )

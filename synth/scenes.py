@@ -327,6 +327,43 @@ def make_pair(name: str, seed: int, H=None, W=None, D=None, radius=None, sigma_s
                 name=name, seed=seed, meta=dict(layers=nlayers))
 
 
+def render_layers(specs, H, W, C=3, noise=0.0, seed=0, texture="uniform"):
+    """Render an explicit scene: specs is a list of (kind, params, footprint)
+    as for the layers of make_pair (kind "const" {c}, "plane" {a, b, c} or
+    "quad" {c, alpha, beta, x0, y0}; footprint "all", ("rect", x0, x1, y0, y1)
+    or ("ellipse", cx, cy, rx, ry)), each layer with its own texture of the
+    given kind.  Returns (left, right, gt, occ) as make_pair's Pair holds them;
+    with known surfaces the ground truth and the occlusion masks have closed
+    forms (the tests check them)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    layers = [_Layer(kind, dict(params), fp, _Texture(rng, texture, C, -2.0, W + 300.0, -2.0, H + 2.0))
+              for kind, params, fp in specs]
+    return _render(layers, H, W, C, noise, rng)
+
+
+def regions(pair, textured_std=4.0, jump=1.0, margin=3):
+    """Evaluation regions of a synthetic pair, the counterparts of the paper's
+    region names: "non_occ" = pixels visible in the right view; "non_occ_textl"
+    = visible and textured (grey standard deviation over the 9x9 window >=
+    textured_std levels); "non_occ_discont" = visible and farther than margin
+    pixels (Chebyshev) from a ground-truth depth discontinuity (|gt| jumping by
+    more than jump between 4-neighbours)."""
+    grey = pair.left.astype(np.float64).mean(axis=2)
+    m1 = ndimage.uniform_filter(grey, 9)
+    m2 = ndimage.uniform_filter(grey * grey, 9)
+    textured = np.sqrt(np.maximum(m2 - m1 * m1, 0.0)) >= textured_std
+    j = np.zeros(pair.gt.shape, bool)
+    dx = np.abs(np.diff(pair.gt, axis=1)) > jump
+    dy = np.abs(np.diff(pair.gt, axis=0)) > jump
+    j[:, 1:] |= dx
+    j[:, :-1] |= dx
+    j[1:, :] |= dy
+    j[:-1, :] |= dy
+    discont = ndimage.maximum_filter(j, size=2 * margin + 1)
+    vis = ~pair.occ
+    return {"non_occ": vis, "non_occ_textl": vis & textured, "non_occ_discont": vis & ~discont}
+
+
 def make_workload(name: str, seed: int = 0) -> Pair:
     """The full-size pair of a workload."""
     return make_pair(name, seed)
