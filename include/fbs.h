@@ -83,6 +83,28 @@ fbs_status fbs_set_options(fbs_ctx *ctx, const fbs_options *opt);
  * report any kernel error. */
 fbs_status fbs_sync(fbs_ctx *ctx);
 
+/* Failure detection (not a step of the method).  Every wait of the
+ * tensor-core aggregation on another part of the same kernel (its pipeline of
+ * weight producers, copies, MMAs and epilogue) is bounded: after `seconds` of
+ * SM clock time the kernel stops issuing work, lets its own copies and MMAs
+ * land (a fixed ~2 s bound), frees its tensor memory and records an error
+ * that the next fbs_sync returns as FBS_ERR_TIMEOUT; the outputs of that call
+ * are invalid and the context stays usable.  0 <= seconds <= 60, 0 = the
+ * default (about 2 s).  Applies to kernels launched after the call (batch
+ * graphs built earlier keep the limit they were built with). */
+fbs_status fbs_set_wait_limit(fbs_ctx *ctx, double seconds);
+
+/* Failure injection (a test hook; not a step of the method): the next
+ * `count` steps of fbs_compute_disparity or fbs_compute_disparity_host (and
+ * of fbs_compute_disparity_lr in BF16 / FP16 contexts) on ctx launch nothing
+ * and fail as if their first
+ * kernel launch had returned `cuda_error` (a cudaError_t value): FBS_ERR_OOM
+ * for cudaErrorMemoryAllocation, FBS_ERR_CUDA otherwise, with the error's
+ * text in fbs_last_error.  Lets a caller exercise its error handling without a
+ * device fault; the context stays usable.  count 0 disarms; count < 0, or a
+ * zero error with count > 0, is FBS_ERR_INVALID_ARG. */
+fbs_status fbs_debug_fail_launches(fbs_ctx *ctx, int cuda_error, int count);
+
 /* Message for the last non-OK status of this context ("" if none). */
 const char *fbs_last_error(const fbs_ctx *ctx);
 

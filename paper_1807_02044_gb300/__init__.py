@@ -71,6 +71,8 @@ SIGNATURES = {
     "fbs_destroy": (_I, [_P]),
     "fbs_set_options": (_I, [_P, ctypes.POINTER(fbs_options)]),
     "fbs_sync": (_I, [_P]),
+    "fbs_set_wait_limit": (_I, [_P, ctypes.c_double]),
+    "fbs_debug_fail_launches": (_I, [_P, _I, _I]),
     "fbs_last_error": (ctypes.c_char_p, [_P]),
     "fbs_compute_disparity": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _F, _P, _P, _P]),
     "fbs_compute_disparity_host": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _F, _F, _F, _P, _P]),
@@ -192,6 +194,14 @@ def fbs_set_options(ctx, options):
 
 def fbs_sync(ctx):
     _check(ctx, lib().fbs_sync(ctx))
+
+
+def fbs_set_wait_limit(ctx, seconds):
+    _check(ctx, lib().fbs_set_wait_limit(ctx, float(seconds)))
+
+
+def fbs_debug_fail_launches(ctx, cuda_error, count):
+    _check(ctx, lib().fbs_debug_fail_launches(ctx, int(cuda_error), int(count)))
 
 
 def fbs_last_error(ctx):

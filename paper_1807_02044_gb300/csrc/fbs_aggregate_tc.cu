@@ -78,6 +78,7 @@ struct TcParams {
     uint32_t acc_stride, den_col, tmem_cols;
     float neg_ks, neg_kr;
     uint32_t idesc, idesc16;
+    long long wait_cycles;   // limit of one pipeline wait (on another role's progress)
 };
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
@@ -150,15 +151,18 @@ __host__ __device__ inline TcSmem tc_smem_layout(int KW, int Nb, int NH, int R, 
     return s;
 }
 
-// Bounded wait that also gives up as soon as another role has aborted.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag)
+// Bounded wait (limit in SM clock cycles) that also gives up as soon as
+// another role has aborted.  The waits that only let the CTA's own copies and
+// MMAs land before it frees its tensor memory use mbar_wait's fixed ~2 s bound.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
+                                                   long long limit)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (unsigned i = 0; i < kWaitIters; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) break;
+        if (clock64() - t0 > limit) break;
     }
     return false;
 }
@@ -344,7 +348,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
             const int tx0 = tw.tx * kTW, ty0 = tw.ty * kTH;
             const int xlo = tx0 - p.rho8;
             const uint32_t tb = t & 1;
-            if (!mbar_wait_or_abort(g_full0 + 8 * tb, (t >> 1) & 1, abort_flag)) {
+            if (!mbar_wait_or_abort(g_full0 + 8 * tb, (t >> 1) & 1, abort_flag, p.wait_cycles)) {
                 raise_abort(abort_flag, err, 6);
                 break;
             }
@@ -397,7 +401,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                 const uint32_t s = gs, use = gu;   // g % S, g / S, carried below
                 // one lane waits for the MMAs that last read stage s; the warp follows
                 bool ok = true;
-                if (lane == 0 && use > 0) ok = mbar_wait_or_abort(empty0 + 8 * s, (use - 1) & 1, abort_flag);
+                if (lane == 0 && use > 0) ok = mbar_wait_or_abort(empty0 + 8 * s, (use - 1) & 1, abort_flag, p.wait_cycles);
                 if (!__shfl_sync(0xffffffffu, ok, 0)) {
                     raise_abort(abort_flag, err, 1);
                     stop = true;
@@ -441,7 +445,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
         for (TileWalk tw(p.ntx); tw.tile < p.ntiles; tw.next(), ++t) {
             const uint32_t ab = p.nacc == 2 ? (t & 1) : 0, u = p.nacc == 2 ? (t >> 1) : t;
             // tcgen05.ld is warp-collective: the whole warp continues or stops
-            const bool ok = __all_sync(0xffffffffu, mbar_wait_or_abort(acc_full0 + 8 * ab, u & 1, abort_flag));
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_or_abort(acc_full0 + 8 * ab, u & 1, abort_flag, p.wait_cycles));
             if (!ok) {
                 raise_abort(abort_flag, err, 4);
                 break;
@@ -526,7 +530,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                 const int xlo = tx0 - p.rho8;
                 {
                     const uint32_t tb = t & 1, u = t >> 1;
-                    if (u > 0 && !mbar_wait_or_abort(g_empty0 + 8 * tb, (u - 1) & 1, abort_flag)) {
+                    if (u > 0 && !mbar_wait_or_abort(g_empty0 + 8 * tb, (u - 1) & 1, abort_flag, p.wait_cycles)) {
                         raise_abort(abort_flag, err, 7);
                         break;
                     }
@@ -539,7 +543,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                 for (int h0 = hr_lo; h0 < hr_hi; h0 += R) {
                     const int nr = min(R, hr_hi - h0);
                     const uint32_t s = gs, use = gu;   // g % S, g / S
-                    if (use > 0 && !mbar_wait_or_abort(empty0 + 8 * s, (use - 1) & 1, abort_flag)) {
+                    if (use > 0 && !mbar_wait_or_abort(empty0 + 8 * s, (use - 1) & 1, abort_flag, p.wait_cycles)) {
                         raise_abort(abort_flag, err, 2);
                         stop = true;
                         break;
@@ -574,7 +578,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
             bool stop = false;
             for (TileWalk tw(p.ntx); tw.tile < p.ntiles && !stop; tw.next(), ++t) {
                 const uint32_t ab = p.nacc == 2 ? (t & 1) : 0, u = p.nacc == 2 ? (t >> 1) : t;
-                if (u > 0 && !mbar_wait_or_abort(acc_empty0 + 8 * ab, (u - 1) & 1, abort_flag)) {
+                if (u > 0 && !mbar_wait_or_abort(acc_empty0 + 8 * ab, (u - 1) & 1, abort_flag, p.wait_cycles)) {
                     raise_abort(abort_flag, err, 5);
                     break;
                 }
@@ -587,8 +591,8 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                 for (int h0 = hr_lo; h0 < hr_hi; h0 += R) {
                     const int nr = min(R, hr_hi - h0);
                     const uint32_t s = gs, par = gu & 1;   // g % S, (g / S) & 1
-                    if (!mbar_wait_or_abort(full_a0 + 8 * s, par, abort_flag) ||
-                        !mbar_wait_or_abort(full_b0 + 8 * s, par, abort_flag)) {
+                    if (!mbar_wait_or_abort(full_a0 + 8 * s, par, abort_flag, p.wait_cycles) ||
+                        !mbar_wait_or_abort(full_b0 + 8 * s, par, abort_flag, p.wait_cycles)) {
                         raise_abort(abort_flag, err, 3);
                         stop = true;
                         break;
@@ -814,13 +818,14 @@ cudaError_t launch_xblock16_pad_rows(int H, int W, int D, bool bf16, void* out, 
 cudaError_t launch_aggregate_tc(const void* cost, const uint2* rgbx, int H, int W, int C, int D,
                                 int radius, float sigma_s, float sigma_r, bool bf16, float* agg_out,
                                 int32_t* disp_int, float* disp_sub, int* err, int num_sms, cudaStream_t stream,
-                                int max_rows)
+                                int max_rows, long long wait_cycles)
 {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     TcParams p;
     TcSmem L;
     if (!tc_plan(H, W, C, D, radius, sigma_s, sigma_r, bf16, p, L, max_rows)) return cudaErrorInvalidValue;
+    p.wait_cycles = wait_cycles > 0 ? wait_cycles : kWaitCycles;
 
     // The two tensor maps depend only on the buffers and the shape: a few
     // recent encodings are kept per host thread (a repeated call with the same

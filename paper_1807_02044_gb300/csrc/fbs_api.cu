@@ -2,6 +2,7 @@
 // dispatch of the fast-bilateral-stereo kernels.  See include/fbs.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -26,6 +27,8 @@ fbs_status run_path_tc(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, 
     if (!fbs::tc_supported(D, radius))
         return fail(ctx, FBS_ERR_UNSUPPORTED, "tensor-core aggregation supports D <= 256 and radius <= 24 (got D=%d, radius=%d)",
                     D, radius);
+    fbs_status inj = take_injected_failure(ctx);
+    if (inj != FBS_OK) return inj;
     const bool bf16 = ctx->opt.prec == FBS_PREC_BF16;
     // scratch: [packed guide | 16-bit x-blocked volume]; the cost kernel writes both
     const size_t rgbx = fbs::rgbx_bytes(H, W);
@@ -44,7 +47,7 @@ fbs_status run_path_tc(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, 
     {
         LaunchScope ls(ctx, FBS_KERNEL_AGG_TC, st);
         e = fbs::launch_aggregate_tc(cost, sc.rgbx, H, W, C, D, radius, sigma_s, sigma_r, bf16, nullptr, disp_int,
-                                     disp_subpix, ctx->derr, ctx->num_sms, st);
+                                     disp_subpix, ctx->derr, ctx->num_sms, st, 0, ctx->wait_cycles);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core aggregation launch");
     return FBS_OK;
@@ -73,6 +76,8 @@ fbs_status run_path(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int
     if (ctx->opt.prec != FBS_PREC_F32)
         return fbs::run_path_tc(ctx, left, right, H, W, C, D, radius, sigma_s, sigma_r, tau, disp_int, disp_subpix,
                                 st);
+    fbs_status inj = take_injected_failure(ctx);
+    if (inj != FBS_OK) return inj;
     const int ld = fbs::padded_ld(D);
     const size_t stats = fbs::cost_scratch_bytes(H, W);
     const size_t need = stats + sizeof(float) * (size_t)H * W * ld;
@@ -190,6 +195,7 @@ fbs_status fbs_create(fbs_ctx** out, const fbs_options* opt, int device)
         return FBS_ERR_CUDA;
     }
     if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->sm_khz, cudaDevAttrClockRate, device) != cudaSuccess ||
         cudaMalloc(&ctx->derr, sizeof(int)) != cudaSuccess || cudaMemset(ctx->derr, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         if (ctx->derr) cudaFree(ctx->derr);
@@ -258,6 +264,25 @@ fbs_status fbs_sync(fbs_ctx* ctx)
         cudaMemset(ctx->derr, 0, sizeof(int));
         return fail(ctx, FBS_ERR_TIMEOUT, "a bounded wait inside a kernel gave up (code %d); its outputs are invalid", word);
     }
+    return FBS_OK;
+}
+
+fbs_status fbs_debug_fail_launches(fbs_ctx* ctx, int cuda_error, int count)
+{
+    if (!ctx) return FBS_ERR_INVALID_ARG;
+    if (count < 0 || (count > 0 && cuda_error == (int)cudaSuccess))
+        return fail(ctx, FBS_ERR_INVALID_ARG, "count %d must be >= 0 and the error non-zero", count);
+    ctx->inject_error = cuda_error;
+    ctx->inject_count = count;
+    return FBS_OK;
+}
+
+fbs_status fbs_set_wait_limit(fbs_ctx* ctx, double seconds)
+{
+    if (!ctx) return FBS_ERR_INVALID_ARG;
+    if (!(seconds >= 0.0 && seconds <= 60.0))
+        return fail(ctx, FBS_ERR_INVALID_ARG, "wait limit %g s outside 0 .. 60", seconds);
+    ctx->wait_cycles = seconds == 0.0 ? 0 : std::max(1LL, (long long)(seconds * ctx->sm_khz * 1e3));
     return FBS_OK;
 }
 
@@ -429,7 +454,7 @@ fbs_status fbs_aggregate(fbs_ctx* ctx, const float* cost, const uint8_t* guide, 
         {
             LaunchScope ls(ctx, FBS_KERNEL_AGG_TC, st);
             e = fbs::launch_aggregate_tc(cost16, packed, H, W, C, D, radius, sigma_s, sigma_r, bf16, agg_out,
-                                         disp_int, disp_subpix, ctx->derr, ctx->num_sms, st);
+                                         disp_int, disp_subpix, ctx->derr, ctx->num_sms, st, 0, ctx->wait_cycles);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core aggregation launch");
         return FBS_OK;

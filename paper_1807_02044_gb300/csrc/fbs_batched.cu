@@ -84,8 +84,10 @@ void load_tuned(fbs_ctx* ctx)
 void store_tuned(fbs_ctx* ctx, const std::string& sig, int plan)
 {
     if (!ctx->opt.autotune_cache_path) return;
+    // a leading newline keeps the entry on a line of its own even after a
+    // truncated last line (blank lines are skipped by load_tuned)
     std::ofstream f(ctx->opt.autotune_cache_path, std::ios::app);
-    if (f) f << sig << " " << plan << "\n";
+    if (f) f << "\n" << sig << " " << plan << "\n";
 }
 
 // Device buffers that graphs capture by address: grown only here, and every
@@ -336,7 +338,8 @@ fbs_status build_branch_graph(fbs_ctx* ctx, int n, const fbs_pair* pairs, int nb
         k0 = fbs::launch_count();
         if (e == cudaSuccess)
             e = fbs::launch_aggregate_tc(cost, sc.rgbx, q.H, q.W, q.C, q.D, q.radius, q.sigma_s, q.sigma_r, bf16,
-                                         nullptr, q.disp_int, q.disp_subpix, ctx->derr, ctx->num_sms, s, rows);
+                                         nullptr, q.disp_int, q.disp_subpix, ctx->derr, ctx->num_sms, s, rows,
+                                         ctx->wait_cycles);
         g->kernels[FBS_KERNEL_AGG_TC] += fbs::launch_count() - k0;
     }
     // join every branch back, also after a failed launch, so the capture ends cleanly

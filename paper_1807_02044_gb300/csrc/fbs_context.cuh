@@ -34,6 +34,10 @@ struct fbs_ctx {
     std::string err;
     int num_sms = 0;
     int* derr = nullptr;         // device error word written by kernels with bounded waits
+    int sm_khz = 0;              // peak SM clock (kHz): converts the wait limit to clock cycles
+    long long wait_cycles = 0;   // limit of one pipeline wait in the kernels (0 = their default, ~2 s)
+    int inject_error = 0;        // failure injection: the cudaError_t the next steps report ...
+    int inject_count = 0;        // ... for this many steps, instead of launching
     // kernel accounting
     long long launches[FBS_KERNEL_KINDS] = {};
     bool profiling = false;
@@ -100,6 +104,15 @@ inline fbs_status cuda_fail(fbs_ctx* ctx, cudaError_t e, const char* where)
 {
     if (e == cudaErrorMemoryAllocation) return fail(ctx, FBS_ERR_OOM, "%s: %s", where, cudaGetErrorString(e));
     return fail(ctx, FBS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// A step armed by fbs_debug_fail_launches reports the injected error instead
+// of launching anything.
+inline fbs_status take_injected_failure(fbs_ctx* ctx)
+{
+    if (ctx->inject_count <= 0) return FBS_OK;
+    --ctx->inject_count;
+    return cuda_fail(ctx, (cudaError_t)ctx->inject_error, "kernel launch (injected failure)");
 }
 
 inline bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }

@@ -89,11 +89,12 @@ cudaError_t launch_aggregate_f32(const float* cost, int ld, const uint8_t* guide
 // aligned.  err: device int set to nonzero if a bounded wait inside the kernel
 // gave up.
 int tc_supported(int D, int radius);
-// max_rows (0 = the kernel's own maximum) caps the window rows per pipeline stage.
+// max_rows (0 = the kernel's own maximum) caps the window rows per pipeline
+// stage; wait_cycles (0 = about 2 s) limits each pipeline wait of the kernel.
 cudaError_t launch_aggregate_tc(const void* cost, const uint2* rgbx, int H, int W, int C, int D,
                                 int radius, float sigma_s, float sigma_r, bool bf16, float* agg_out,
                                 int32_t* disp_int, float* disp_sub, int* err, int num_sms, cudaStream_t stream,
-                                int max_rows = 0);
+                                int max_rows = 0, long long wait_cycles = 0);
 // Packed guide plane of an image: (RGBX, squared norm) per pixel, pitch rgbx_pitch(W); the
 // tensor-core path loads its guide tiles from it.
 cudaError_t launch_pack_rgbx(const uint8_t* img, int H, int W, int C, uint2* rgbx, cudaStream_t stream);
