@@ -260,19 +260,29 @@ fbs_status fbs_batch_set_plan(fbs_ctx *ctx, int n, const fbs_pair *pairs, int pl
  * so every GPU that loads it holds the array until the process exits (with
  * CUDA's default lazy module loading, from the first call of this entry point
  * on that GPU).
- *   - Limit: about H * W * (4 * round_up(D, 4) + 20) bytes (block statistics
- *     plus cost volume, each rounded up to 256 bytes) must fit in
+ *   - Limit: H * W * (4 * round_up(D, 4) + 20) bytes (block statistics
+ *     20 bytes a pixel, cost volume 4 * round_up(D, 4) bytes a pixel, the
+ *     four parts each rounded up to 256 bytes) must fit in
  *     FBS_NOALLOC_MAX_COST_BYTES, e.g. 640x480 with D <= 20 or 320x240 with
- *     D <= 100.  Larger requests return FBS_ERR_INVALID_ARG with the sizes in
+ *     D <= 104.  Larger requests return FBS_ERR_INVALID_ARG with the sizes in
  *     fbs_last_error() and launch nothing.
- *   - Set-up: the first call on each device looks up the array's device
- *     address (cudaGetSymbolAddress; no allocation) and caches it.  Make that
- *     first call before any stream capture.
- *   - Sharing: all calls on a device use the same array, which keeps the last
- *     call's contents.  Nothing in it has to start at zero: each call writes
- *     every element it later reads.  Calls whose kernels overlap on the GPU
- *     (different streams or host threads) race on the array; issue them on
- *     one stream.
+ *   - CUDA context: the context's device is made current (as every entry
+ *     point does) and the call then works in the CUDA context current on the
+ *     calling thread -- the device's primary context, or a driver-API context
+ *     of that device the caller has pushed.  Each call looks up the array's
+ *     address in that CUDA context (cudaGetSymbolAddress, a host-side lookup
+ *     that allocates nothing; with lazy module loading the first lookup in a
+ *     CUDA context also loads the library's device code there, so make one
+ *     call before any stream capture) and launches there.
+ *   - Sharing: all calls in one CUDA context use the same array, which keeps
+ *     the last call's contents.  Nothing in it has to start at zero: each
+ *     call writes every element it later reads.  Calls whose kernels overlap
+ *     on the GPU (different streams or host threads) race on the array; issue
+ *     them on one stream.
+ *   - Errors and accounting are those of fbs_compute_disparity: launch
+ *     failures return FBS_ERR_CUDA (FBS_ERR_OOM for an out-of-memory error),
+ *     and the kernels count under FBS_KERNEL_COST and FBS_KERNEL_AGG_F32 and
+ *     are timed when profiling is on.
  *   - The entry point calls no cudaMalloc, cudaFree or allocating library
  *     routine.
  */

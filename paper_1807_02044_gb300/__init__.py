@@ -225,9 +225,9 @@ FBS_NOALLOC_MAX_COST_BYTES = 32 * 1024 * 1024
 
 def fbs_compute_disparity_noalloc(ctx, left, right, H, W, C, D, radius, sigma_s, sigma_r, tau, disp_int,
                                   disp_subpix, stream=None):
-    """fbs_compute_disparity without device allocation: the cost volume goes to
-    the library's fixed static scratch (H*W*round_up(D,4)*4 bytes at most
-    FBS_NOALLOC_MAX_COST_BYTES)."""
+    """fbs_compute_disparity without device allocation: block statistics and
+    cost volume go to the library's fixed static scratch, so
+    H*W*(4*round_up(D,4)+20) bytes must not exceed FBS_NOALLOC_MAX_COST_BYTES."""
     _check(ctx, lib().fbs_compute_disparity_noalloc(ctx, _addr(left), _addr(right), H, W, C, D, radius, sigma_s,
                                                     sigma_r, tau, _addr(disp_int), _addr(disp_subpix),
                                                     _stream(stream)))

@@ -78,7 +78,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             if log:
                 sys.stderr.write(f"== {os.path.basename(obj)}\n{log}\n")
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp] + [o for o, _ in results]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp] + [o for o, _ in results] + ["-ldl"]   # NVTX loads a tool on demand
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{p.stdout}\n{p.stderr}")

@@ -116,12 +116,6 @@ fbs_status check_path_args(fbs_ctx* ctx, const uint8_t* left, const uint8_t* rig
     return s;
 }
 
-int ctx_device(const fbs_ctx* ctx) { return ctx->device; }
-int ctx_cost_mode(const fbs_ctx* ctx) { return ctx->opt.cost; }
-int ctx_precision(const fbs_ctx* ctx) { return ctx->opt.prec; }
-cudaStream_t ctx_stream(fbs_ctx* ctx, void* cuda_stream) { return pick_stream(ctx, cuda_stream); }
-fbs_status ctx_error(fbs_ctx* ctx, fbs_status st, const char* msg) { return fail(ctx, st, "%s", msg); }
-void ctx_count_launch(fbs_ctx* ctx, int kind, long long kernels) { ctx->launches[kind] += kernels; }
 
 thread_local long long tl_kernel_launches = 0;
 

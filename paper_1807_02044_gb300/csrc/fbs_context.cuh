@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdarg>
@@ -169,6 +170,16 @@ inline cudaEvent_t take_event(fbs_ctx* ctx)
 
 // Bracket the kernel launches of one step for the accounting API (events
 // around them when profiling; the number of kernels they launched).
+// NVTX range names of the kernel kinds (host-side trace of each stage; the
+// calls cost a few nanoseconds when no tracing tool is attached).
+inline const char* kind_range_name(int kind)
+{
+    static const char* const names[FBS_KERNEL_KINDS] = {"fbs cost build", "fbs aggregation fp32",
+                                                        "fbs aggregation tensor core", "fbs other",
+                                                        "fbs batch graph", "fbs band network"};
+    return kind >= 0 && kind < FBS_KERNEL_KINDS ? names[kind] : "fbs";
+}
+
 struct LaunchScope {
     fbs_ctx* ctx;
     int kind;
@@ -177,6 +188,7 @@ struct LaunchScope {
     long long k0 = fbs::launch_count();   // kernels noted inside the scope are counted
     LaunchScope(fbs_ctx* c, int k, cudaStream_t s) : ctx(c), kind(k), st(s)
     {
+        nvtxRangePushA(kind_range_name(kind));
         if (ctx->profiling) {
             a = take_event(ctx);
             if (a) cudaEventRecord(a, st);
@@ -184,6 +196,7 @@ struct LaunchScope {
     }
     ~LaunchScope()
     {
+        nvtxRangePop();
         ctx->launches[kind] += fbs::launch_count() - k0;
         if (a) {
             cudaEvent_t b = take_event(ctx);

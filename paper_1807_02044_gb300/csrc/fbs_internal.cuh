@@ -162,12 +162,6 @@ cudaError_t launch_aggregate_f32_batched(const BatchPair* pairs, int npairs, int
 fbs_status check_path_args(fbs_ctx* ctx, const uint8_t* left, const uint8_t* right, int H, int W, int C,
                            int D, int radius, float sigma_s, float sigma_r, float tau,
                            const int32_t* disp_int, const float* disp_subpix);
-int ctx_device(const fbs_ctx* ctx);
-int ctx_cost_mode(const fbs_ctx* ctx);
-int ctx_precision(const fbs_ctx* ctx);
-cudaStream_t ctx_stream(fbs_ctx* ctx, void* cuda_stream);
-fbs_status ctx_error(fbs_ctx* ctx, fbs_status st, const char* msg);
-void ctx_count_launch(fbs_ctx* ctx, int kind, long long kernels);
 // Release the band form's state (called by fbs_destroy).
 void band_free(fbs_ctx* ctx);
 // The single-view tensor-core path of fbs_compute_disparity (context scratch

@@ -52,6 +52,51 @@ def test_null_context_calls_fail_cleanly(fbs):
     assert lib.fbs_create(None, None, 0) == fbs.FBS_ERR_INVALID_ARG
 
 
+def _header_constants():
+    """Every enum value and numeric #define named FBS_* in include/*.h."""
+    out = {}
+    for fname in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fname.endswith(".h"):
+            continue
+        text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", fname)).read(), flags=re.S)
+        for name, expr in re.findall(r"#define\s+(FBS_[A-Z0-9_]+)\s+([^\n]+)", text):
+            expr = re.sub(r"(\d+)[uUlL]+\b", r"\1", expr.strip())
+            if re.fullmatch(r"[\d\s()*+<-]+", expr):
+                out[name] = eval(expr)
+        for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+            for name, val in re.findall(r"(FBS_[A-Z0-9_]+)\s*=\s*(\d+)", body):
+                out[name] = int(val)
+    return out
+
+
+def test_python_constants_match_the_header(fbs):
+    consts = _header_constants()
+    assert consts["FBS_NOALLOC_MAX_COST_BYTES"] == 32 * 1024 * 1024
+    assert consts["FBS_ERR_TIMEOUT"] == 4 and consts["FBS_PREC_F16"] == 2
+    for name, val in consts.items():
+        assert hasattr(fbs, name), f"{name} declared in include/ but not bound"
+        assert getattr(fbs, name) == val, f"{name}: binding {getattr(fbs, name)} != header {val}"
+
+
+def test_noalloc_limit_formula_matches_the_header_examples(fbs):
+    """The documented limit H*W*(4*round_up(D,4)+20) bytes: 640x480 fits up to
+    D=20 and 320x240 up to D=104, the largest D of each that fits."""
+    cap = fbs.FBS_NOALLOC_MAX_COST_BYTES
+
+    def need(H, W, D):
+        n = 2 * H * W
+        r = lambda b: (b + 255) // 256 * 256
+        return r(2 * n) + r(4 * n) + r(4 * n) + 4 * H * W * ((D + 3) // 4 * 4)
+
+    def largest_D(H, W):
+        return max(D for D in range(1, 1025) if need(H, W, D) <= cap)
+
+    assert largest_D(480, 640) == 20
+    assert largest_D(240, 320) == 104
+    for H, W, D in [(480, 640, 20), (240, 320, 104), (100, 200, 64)]:
+        assert abs(need(H, W, D) - H * W * (4 * ((D + 3) // 4 * 4) + 20)) < 4 * 256
+
+
 def test_default_options(fbs):
     o = fbs.fbs_default_options()
     assert (o.cost, o.prec, o.fused, o.workspace_cap) == (0, 0, 0, 0)
