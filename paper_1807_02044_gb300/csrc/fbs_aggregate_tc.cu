@@ -40,32 +40,13 @@
 #include <cuda_fp16.h>
 
 #include "fbs_internal.cuh"
-#include "packed_f32.cuh"
-#include "tc_ptx.cuh"
+#include "tc_aggregate.cuh"
 
 namespace fbs {
 namespace {
 
-using namespace tc;
+using namespace tca;
 
-constexpr int kTW = 16;         // tile width
-constexpr int kTH = 8;          // tile height
-constexpr int kM = kTW * kTH;   // 128 = MMA M = TMEM lanes
-constexpr int kProducerWarps = 16;                 // warps 0-15
-static_assert(kProducerWarps == 16 && kTH == 8 && kTW == 16,
-              "producer warp w covers pixel rows 2 (w >> 2), +1 and the stage rows r % 4 == w % 4");
-constexpr int kEpiWarp0 = kProducerWarps;          // 4 epilogue warps: TMEM lane quarters 0-3
-constexpr int kEpilogue = 128;
-constexpr int kTmaWarp = kEpiWarp0 + 4;
-constexpr int kMmaWarp = kTmaWarp + 1;
-constexpr int kThreads = 32 * (kMmaWarp + 1);
-constexpr int kMaxR = 8;          // window rows per stage, at most
-// Byte distance between the A operand's core matrices adjacent along K: the
-// 2048 bytes of 128 rows x 16 bytes, plus 64 bytes of padding, so that the
-// producers' 4-byte stores to the same row of two K-blocks fall in different
-// shared-memory banks.
-constexpr uint32_t kALbo = 2048 + 64;
-constexpr int kMaxRho2 = 2 * 24 + 1;   // row offsets -rho .. rho of the largest radius
 struct TcParams {
     int H, W, C, D;
     int N;          // round_up(D, 16): disparity rows the TMA box loads
@@ -79,46 +60,6 @@ struct TcParams {
     float neg_ks, neg_kr;
     uint32_t idesc, idesc16;
     long long wait_cycles;   // limit of one pipeline wait (on another role's progress)
-};
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
-            dst),
-        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-template <bool BF16>
-struct Op16;
-template <>
-struct Op16<true> {
-    using T = __nv_bfloat16;
-    static __device__ __forceinline__ T from(float v) { return __float2bfloat16_rn(v); }
-    static __device__ __forceinline__ float to(T v) { return __bfloat162float(v); }
-};
-template <>
-struct Op16<false> {
-    using T = __half;
-    static __device__ __forceinline__ T from(float v) { return __float2half_rn(v); }
-    static __device__ __forceinline__ float to(T v) { return __half2float(v); }
 };
 
 struct TcSmem {
@@ -151,27 +92,6 @@ __host__ __device__ inline TcSmem tc_smem_layout(int KW, int Nb, int NH, int R, 
     return s;
 }
 
-// Bounded wait (limit in SM clock cycles) that also gives up as soon as
-// another role has aborted.  The waits that only let the CTA's own copies and
-// MMAs land before it frees its tensor memory use mbar_wait's fixed ~2 s bound.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
-                                                   long long limit)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    for (unsigned i = 0; i < kWaitIters; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (clock64() - t0 > limit) break;
-    }
-    return false;
-}
-__device__ __forceinline__ void raise_abort(volatile uint32_t* abort_flag, int* err, int code)
-{
-    if (*abort_flag == 0) *abort_flag = (uint32_t)code;
-    atomicCAS(err, 0, code);
-}
-
 // The persistent tile walk of a CTA (tiles blockIdx.x, + gridDim.x, ...) with
 // the tile's column and row carried incrementally (no division per tile).
 struct TileWalk {
@@ -190,10 +110,6 @@ struct TileWalk {
         }
     }
 };
-
-// 2^23 as an FP32 bit pattern: for 0 <= c < 2^23 the pattern kMagic + c is the
-// float 2^23 + c exactly, so subtracting 2^23 gives float(c) exactly.
-constexpr uint32_t kMagic = 0x4B000000u;
 
 // Warp roles: 0-15 weight producers, 16-19 epilogue (TMEM lane quarters 0-3),
 // 20 TMA producer (guide tiles and cost rows), 21 MMA issuer.  NPT = column
@@ -319,29 +235,17 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
         const int np = p.rho + 1;
         // pair j of the thread: columns k, k + 1 with k = c0 + 2 h + 4 j, guide
         // entries at byte 8 (c0 + 2 h) + 32 j of a guide row
-        uint32_t aoff[NPT];
         bool on[NPT];
 #pragma unroll
-        for (int j = 0; j < NPT; ++j) {
-            const int k = c0 + 2 * h + 4 * j;
+        for (int j = 0; j < NPT; ++j)
             on[j] = PM == 0 ? true : PM == 1 ? (j < NPT - 1 || h == 0) : 2 * j + h < np;
-            aoff[j] = (uint32_t)((k >> 3) * kALbo + m0 * 16 + (k & 7) * 2);
-        }
+        const TcPairOffsets po = tc_pair_offsets(c0 + 2 * h, m0);
         const uint32_t gcol = (uint32_t)(c0 + 2 * h) * 8;   // byte offset of pair 0 in a guide row
         const uint32_t g_row = (uint32_t)KW * 8;            // bytes of one guide row
         const float ninf = __int_as_float(0xff800000);
         const uint64_t magic2 = f2_pack(-8388608.f, -8388608.f);
         const uint64_t nkr2 = f2_pack(p.neg_kr, p.neg_kr);
         const unsigned two_rho = (unsigned)(2 * p.rho);
-        // the two 16-bit weights of one column pair of one pixel
-        auto weights = [&](const uint4 q, uint32_t pcol, uint32_t pp, uint64_t sxy) -> uint32_t {
-            const uint32_t e0 = q.y + pp - 2u * __dp4a(q.x, pcol, 0u);
-            const uint32_t e1 = q.w + pp - 2u * __dp4a(q.z, pcol, 0u);
-            const uint64_t c = f2_add(u2_pack(e0, e1), magic2);
-            float a0, a1;
-            f2_unpack(f2_fma(c, nkr2, sxy), a0, a1);
-            return pack_16x2<BF16>(ex2_approx(a0), ex2_approx(a1));
-        };
         uint32_t gs = 0, gu = 0, t = 0;   // stage slot and use count of the next stage
         bool stop = false;
         for (TileWalk tw(p.ntx); tw.tile < p.ntiles && !stop; tw.next(), ++t) {
@@ -372,27 +276,10 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                 sxp[j] = f2_pack(s0, s1);
             }
             const uint8_t* gth = gt + gcol;
-            // one window row of the thread's pairs: which & 1 computes the upper
-            // pixel, which & 2 the lower one; a pixel not computed gets zeros
             auto row_pairs = [&](uint8_t* arow, const uint8_t* grow, uint64_t sy0, uint64_t sy1, int which)
                                  __attribute__((always_inline)) {
-                // at most 5 pairs at a time: their loads first
-#pragma unroll
-                for (int j0 = 0; j0 < NPT; j0 += 5) {
-                    uint4 q[5];
-                    if (which != 0) {
-#pragma unroll
-                        for (int i = 0; i < 5 && j0 + i < NPT; ++i)
-                            if (on[j0 + i]) q[i] = *(const uint4*)(grow + 32 * (j0 + i));
-                    }
-#pragma unroll
-                    for (int i = 0; i < 5 && j0 + i < NPT; ++i) {
-                        const int j = j0 + i;
-                        if (!on[j]) continue;
-                        *(uint32_t*)(arow + aoff[j]) = (which & 1) ? weights(q[i], pcol0, pp0, f2_add(sxp[j], sy0)) : 0u;
-                        *(uint32_t*)(arow + aoff[j] + 256) = (which & 2) ? weights(q[i], pcol1, pp1, f2_add(sxp[j], sy1)) : 0u;
-                    }
-                }
+                tc_row_pairs<BF16, NPT>(arow, grow, po, on, sxp, sy0, sy1, which, pcol0, pp0, pcol1, pp1, magic2,
+                                        nkr2);
             };
             const int hr_lo = max(0, p.rho - ty0);
             const int hr_hi = min(p.NH, p.H - ty0 + p.rho);
@@ -455,68 +342,15 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
             const int tx0 = tw.tx * kTW, ty0 = tw.ty * kTH;
             const int py = ty0 + (m >> 4), px = tx0 + (m & 15);
             const bool pvalid = py < p.H && px < p.W;
-            float dv[16];
-            tmem_ld16(tbase + p.den_col, dv);
-            const float inv = 1.f / dv[0];
-            const float finf = __int_as_float(0x7f800000);
-            float best = finf, a_prev = 0.f, a_next = 0.f, last = 0.f;
-            int bidx = 0;
-            bool pend = false;   // the best is the previous chunk's last value: its successor comes next
             float* arow = (agg_out && pvalid) ? agg_out + ((size_t)py * p.W + px) * p.D : nullptr;
-            const uint64_t inv2 = f2_pack(inv, inv);
-            // WTA (smallest d on ties) over chunks of 16 values, keeping the
-            // neighbours of the running best; two chunks per accumulator read
-            for (int c0 = 0; c0 < p.N; c0 += 32) {
-                float v[2][16];
-                if (c0 + 16 < p.N)
-                    tmem_ld16x2(tbase + (uint32_t)c0, tbase + (uint32_t)c0 + 16, v);
-                else
-                    tmem_ld16(tbase + (uint32_t)c0, v[0]);
-#pragma unroll
-                for (int hc = 0; hc < 2; ++hc) {
-                    const int cb = c0 + 16 * hc;
-                    if (cb >= p.N) break;
-                    float* w = v[hc];
-#pragma unroll
-                    for (int i = 0; i < 16; i += 2) f2_unpack(f2_mul(f2_pack(w[i], w[i + 1]), inv2), w[i], w[i + 1]);
-                    if (arow) {
-#pragma unroll
-                        for (int i = 0; i < 16; ++i)
-                            if (cb + i < p.D) arow[cb + i] = w[i];
-                    }
-                    if (cb + 16 > p.D) {
-                        // disparities past D (zero cost rows) never win
-#pragma unroll
-                        for (int i = 0; i < 16; ++i)
-                            if (cb + i >= p.D) w[i] = finf;
-                    }
-                    a_next = pend ? w[0] : a_next;
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const bool lt = w[i] < best;
-                        best = lt ? w[i] : best;
-                        bidx = lt ? cb + i : bidx;
-                        a_prev = lt ? (i > 0 ? w[i - 1] : last) : a_prev;
-                        if (i < 15)
-                            a_next = lt ? w[i + 1] : a_next;
-                        else
-                            pend = lt;
-                    }
-                    last = w[15];
-                }
-            }
+            const TcWta r = tc_wta(tbase, p.den_col, p.N, p.D, arow);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty0 + 8 * ab);
             if (pvalid) {
-                float ds = (float)bidx;
-                if (bidx > 0 && bidx < p.D - 1) {
-                    const float dd = 2.f * a_prev + 2.f * a_next - 4.f * best;
-                    if (dd > 0.f) ds = (float)bidx + (a_prev - a_next) / dd;
-                }
                 const size_t o = (size_t)py * p.W + px;
-                if (disp_int) disp_int[o] = bidx;
-                if (disp_sub) disp_sub[o] = ds;
+                if (disp_int) disp_int[o] = r.bidx;
+                if (disp_sub) disp_sub[o] = tc_subpixel(r, p.D);
             }
         }
     } else if (warp == kTmaWarp) {
@@ -640,26 +474,6 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
     if (warp == 0) tmem_dealloc(tmem, p.tmem_cols);
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn()
-{
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)f;
-    }
-    return fn;
-}
-
-int round_up(int v, int a) { return (v + a - 1) / a * a; }
-
 template <bool BF16>
 __global__ void hwd_to_xblock16_kernel(const float* __restrict__ in, int H, int W, int D,
                                        typename Op16<BF16>::T* __restrict__ out)
@@ -771,12 +585,8 @@ bool tc_plan(int H, int W, int C, int D, int radius, float sigma_s, float sigma_
     uint32_t cols = 32;
     while (cols < p.nacc * total_n) cols <<= 1;
     p.tmem_cols = cols;
-    // kind::f16 instruction descriptor: D = F32, A = B = BF16 (1) or F16 (0),
-    // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
-    const uint32_t fmt = bf16 ? 1u : 0u;
-    const uint32_t base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kM >> 4) << 24);
-    p.idesc = base | ((uint32_t)((p.ones_sep ? p.N : p.Nb) >> 3) << 17);
-    p.idesc16 = base | (2u << 17);
+    p.idesc = tc_idesc(bf16, p.ones_sep ? p.N : p.Nb);
+    p.idesc16 = tc_idesc(bf16, 16);
     // R window rows per stage and S stages: the largest R (<= kMaxR) with at least
     // 2 stages in 227 KB, then as many stages (<= 6) as fit.  Fewer, larger
     // stages per tile measured faster than deeper pipelines of small stages:
@@ -854,30 +664,9 @@ cudaError_t launch_aggregate_tc(const void* cost, const uint2* rgbx, int H, int 
         if (c.used && c.key == key) hit = &c;
     if (!hit) {
         MapEntry fresh{};
-        // x-blocked volume as a 4-D tensor: (16 block rows d x 8 columns = 256
-        // contiguous bytes, group of 16 block rows, block, image row); a box
-        // covers all Nb block rows of the KW/8 blocks of R window rows and lands
-        // in shared memory as [R][KW/8][Nb][8], the B operand's K-major
-        // core-matrix order.  The 256-byte inner dimension keeps the copy at a
-        // few wide requests per block instead of one per 16-byte block row.
-        const int nxb = (W + 7) / 8;
-        cuuint64_t dims[4] = {128, (cuuint64_t)(p.Nb / 16), (cuuint64_t)nxb, (cuuint64_t)H};
-        cuuint64_t strides[3] = {256, (cuuint64_t)p.Nb * 16, (cuuint64_t)nxb * p.Nb * 16};
-        cuuint32_t box[4] = {128, (cuuint32_t)(p.Nb / 16), (cuuint32_t)(p.KW / 8), (cuuint32_t)p.R};
-        cuuint32_t estr[4] = {1, 1, 1, 1};
-        CUresult r = enc(&fresh.map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4,
-                         const_cast<void*>(cost), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-        cuuint64_t gdims[2] = {(cuuint64_t)W, (cuuint64_t)H};
-        cuuint64_t gstrides[1] = {(cuuint64_t)rgbx_pitch(W) * 8};
-        cuuint32_t gbox[2] = {(cuuint32_t)p.KW, (cuuint32_t)p.NH};
-        cuuint32_t gestr[2] = {1, 1};
-        r = enc(&fresh.gmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint2*>(rgbx), gdims, gstrides, gbox,
-                gestr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        if (encode_cost_map(enc, &fresh.map, cost, H, W, p.Nb, p.KW, p.R, bf16) != CUDA_SUCCESS ||
+            encode_guide_map(enc, &fresh.gmap, rgbx, H, W, rgbx_pitch(W), p.KW, p.NH) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
         fresh.key = key;
         fresh.used = true;
         hit = &cache[next_slot];

@@ -215,7 +215,7 @@ fbs_status fbs_destroy(fbs_ctx* ctx)
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->io) cudaFree(ctx->io);
     if (ctx->derr) cudaFree(ctx->derr);
-    for (auto& kv : ctx->bgraphs) cudaGraphExecDestroy(kv.second.exec);
+    for (auto& kv : ctx->bgraphs) drop_batch_graph(kv.second);
     for (int k = 0; k < 3; ++k) {
         if (ctx->bbranch[k]) cudaStreamDestroy(ctx->bbranch[k]);
         if (ctx->bjoin[k]) cudaEventDestroy(ctx->bjoin[k]);

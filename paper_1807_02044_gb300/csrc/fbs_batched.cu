@@ -24,6 +24,11 @@
 // kernels' arguments (and the tensor maps) hold the pairs' addresses, so
 // these graphs are keyed by the buffers too.
 //
+// Plan 6 of the tensor-core form keeps the per-pair cost builds (2 branches)
+// and replaces the per-pair aggregations by persistent launches that walk
+// the tiles of every pair, one launch per radius variant present in the batch
+// (fbs_aggregate_tc_batch.cu).
+//
 // Either way each pair's results are bit-identical to fbs_compute_disparity
 // in the same precision (the same kernels run on the same data in the same
 // order).  The first call of a new shape (the list of H, W, C, D, radius, the
@@ -49,8 +54,11 @@ constexpr int kMaxPairs = 4096;
 // = largest first; plans 4-6 branched with kBranches[plan - 4] branches.
 constexpr int kPersistentPlans = 4;
 constexpr int kPlans = 7;
-// tensor cores: plan = 2 * branch choice + stage choice
-constexpr int kTcPlans = 6;
+// tensor cores: plans 0-5 = 2 * branch choice + stage choice; plan 6 the
+// cost builds on 2 branches, then persistent aggregations over every pair's
+// tiles (one launch per radius variant)
+constexpr int kTcPersistentPlan = 6;
+constexpr int kTcPlans = 7;
 constexpr int kBranches[3] = {1, 2, 4};
 constexpr int kTcRowCap[2] = {0, 3};   // window rows per stage: 0 = the kernel's maximum
 constexpr size_t kMaxBranchGraphs = 32;   // branched graphs kept for distinct buffer sets
@@ -97,7 +105,7 @@ fbs_status ensure_batch_buffers(fbs_ctx* ctx, int n)
     if (ctx->bpairs && ctx->bpairs_cap >= n) return FBS_OK;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise before growing the batch table");
-    for (auto& kv : ctx->bgraphs) cudaGraphExecDestroy(kv.second.exec);
+    for (auto& kv : ctx->bgraphs) drop_batch_graph(kv.second);
     ctx->bgraphs.clear();
     if (ctx->bpairs) cudaFree(ctx->bpairs);
     for (int k = 0; k < 2; ++k)
@@ -288,8 +296,12 @@ fbs_status ensure_branches(fbs_ctx* ctx)
 
 // Capture every pair's launches of the single-pair form of the context's
 // precision, spread over nb branches, into one graph (rows: the tensor-core
-// stage cap).
-fbs_status build_branch_graph(fbs_ctx* ctx, int n, const fbs_pair* pairs, int nb, int rows, fbs_batch_graph* g)
+// stage cap).  With `persistent` (tensor cores) the graph holds only the
+// pairs' cost builds on the branches and, after they join, the persistent
+// aggregation launches over every pair's tiles (one per radius variant),
+// whose pair table the graph owns.
+fbs_status build_branch_graph(fbs_ctx* ctx, int n, const fbs_pair* pairs, int nb, int rows, bool persistent,
+                              fbs_batch_graph* g)
 {
     const bool tc = tc_batch(ctx);
     const bool bf16 = ctx->opt.prec == FBS_PREC_BF16;
@@ -297,6 +309,29 @@ fbs_status build_branch_graph(fbs_ctx* ctx, int n, const fbs_pair* pairs, int nb
     fbs_status st = ensure_branches(ctx);
     if (st != FBS_OK) return st;
     const std::vector<int> order = largest_first(n, pairs);
+    fbs::TcBatchLaunch tcl{};
+    if (persistent) {
+        // the pair table (tensor maps of each pair's slice of the scratch) is
+        // built and uploaded before the capture
+        std::vector<fbs::TcBatchMember> mem(n);
+        size_t off = 0;
+        for (int k = 0; k < n; ++k) {
+            const fbs_pair& q = pairs[order[k]];
+            uint8_t* base = (uint8_t*)ctx->ws + off;
+            off += pair_bytes(q, true);
+            mem[k] = fbs::TcBatchMember{base + align256(fbs::rgbx_bytes(q.H, q.W)), (const uint2*)base, q.H, q.W, q.C,
+                                        q.D, q.radius, q.sigma_s, q.sigma_r, q.disp_int, q.disp_subpix};
+        }
+        std::vector<uint8_t> host(fbs::tc_batch_table_bytes(n));
+        cudaError_t e = fbs::tc_batch_prepare(n, mem.data(), bf16, host.data(), &tcl);
+        if (e == cudaSuccess) e = cudaMalloc(&g->table, host.size());
+        if (e == cudaSuccess) e = cudaMemcpy(g->table, host.data(), host.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (g->table) cudaFree(g->table);
+            g->table = nullptr;
+            return cuda_fail(ctx, e, "persistent batch pair table");
+        }
+    }
     cudaStream_t cs = ctx->stream;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "begin graph capture");
@@ -336,7 +371,7 @@ fbs_status build_branch_graph(fbs_ctx* ctx, int n, const fbs_pair* pairs, int nb
         e = fbs::launch_cost_build_xblock16(sc, q.left, q.right, q.H, q.W, q.C, q.D, mode, q.tau, bf16, cost, s);
         g->kernels[FBS_KERNEL_COST] += fbs::launch_count() - k0;
         k0 = fbs::launch_count();
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && !persistent)
             e = fbs::launch_aggregate_tc(cost, sc.rgbx, q.H, q.W, q.C, q.D, q.radius, q.sigma_s, q.sigma_r, bf16,
                                          nullptr, q.disp_int, q.disp_subpix, ctx->derr, ctx->num_sms, s, rows,
                                          ctx->wait_cycles);
@@ -348,17 +383,28 @@ fbs_status build_branch_graph(fbs_ctx* ctx, int n, const fbs_pair* pairs, int nb
         if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(cs, ctx->bjoin[k - 1], 0);
         if (e == cudaSuccess) e = e1;
     }
+    if (persistent && e == cudaSuccess) {
+        const long long k0 = fbs::launch_count();
+        e = fbs::launch_aggregate_tc_batch(g->table, tcl, bf16, ctx->derr, ctx->num_sms, ctx->wait_cycles, cs);
+        g->kernels[FBS_KERNEL_AGG_TC] += fbs::launch_count() - k0;
+    }
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "branched batch graph capture");
+    if (e != cudaSuccess) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->table) cudaFree(g->table);
+        g->exec = nullptr;
+        g->table = nullptr;
+        return cuda_fail(ctx, e, "branched batch graph capture");
+    }
     return FBS_OK;
 }
 
 fbs_status run_branch_plan(fbs_ctx* ctx, const std::string& sig, int n, const fbs_pair* pairs, int plan, int nb,
-                           int rows, cudaStream_t stream)
+                           int rows, bool persistent, cudaStream_t stream)
 {
     size_t need = 0;
     for (int i = 0; i < n; ++i) need += pair_bytes(pairs[i], tc_batch(ctx));
@@ -381,7 +427,7 @@ fbs_status run_branch_plan(fbs_ctx* ctx, const std::string& sig, int n, const fb
             if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise before dropping batch graphs");
             for (auto g = ctx->bgraphs.begin(); g != ctx->bgraphs.end();) {
                 if (g->first.compare(0, 2, "g|") == 0) {
-                    cudaGraphExecDestroy(g->second.exec);
+                    drop_batch_graph(g->second);
                     g = ctx->bgraphs.erase(g);
                 } else {
                     ++g;
@@ -389,7 +435,7 @@ fbs_status run_branch_plan(fbs_ctx* ctx, const std::string& sig, int n, const fb
             }
         }
         fbs_batch_graph g;
-        st = build_branch_graph(ctx, n, pairs, nb, rows, &g);
+        st = build_branch_graph(ctx, n, pairs, nb, rows, persistent, &g);
         if (st != FBS_OK) return st;
         it = ctx->bgraphs.emplace(key.str(), g).first;
     }
@@ -402,10 +448,12 @@ fbs_status run_branch_plan(fbs_ctx* ctx, const std::string& sig, int n, const fb
 fbs_status run_any_plan(fbs_ctx* ctx, const std::string& sig, int n, const fbs_pair* pairs, int plan,
                         cudaStream_t stream)
 {
-    if (tc_batch(ctx))
-        return run_branch_plan(ctx, sig, n, pairs, plan, kBranches[plan >> 1], kTcRowCap[plan & 1], stream);
+    if (tc_batch(ctx)) {
+        if (plan == kTcPersistentPlan) return run_branch_plan(ctx, sig, n, pairs, plan, 2, 0, true, stream);
+        return run_branch_plan(ctx, sig, n, pairs, plan, kBranches[plan >> 1], kTcRowCap[plan & 1], false, stream);
+    }
     if (plan < kPersistentPlans) return run_plan(ctx, sig, n, pairs, plan, stream);
-    return run_branch_plan(ctx, sig, n, pairs, plan, kBranches[plan - kPersistentPlans], 0, stream);
+    return run_branch_plan(ctx, sig, n, pairs, plan, kBranches[plan - kPersistentPlans], 0, false, stream);
 }
 
 }  // namespace

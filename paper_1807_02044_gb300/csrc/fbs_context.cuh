@@ -22,7 +22,17 @@ struct fbs_batch_graph {
     cudaGraphExec_t exec = nullptr;
     int slot = 0;
     long long kernels[FBS_KERNEL_KINDS] = {};   // kernels one replay runs, per kind
+    void* table = nullptr;                      // device pair table the graph's kernels read (if any)
 };
+
+// Release a batch graph and what it owns (the caller has synchronised).
+inline void drop_batch_graph(fbs_batch_graph& g)
+{
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.table) cudaFree(g.table);
+    g.exec = nullptr;
+    g.table = nullptr;
+}
 
 struct fbs_ctx {
     int device = 0;

@@ -95,6 +95,38 @@ cudaError_t launch_aggregate_tc(const void* cost, const uint2* rgbx, int H, int 
                                 int radius, float sigma_s, float sigma_r, bool bf16, float* agg_out,
                                 int32_t* disp_int, float* disp_sub, int* err, int num_sms, cudaStream_t stream,
                                 int max_rows = 0, long long wait_cycles = 0);
+// Persistent tensor-core aggregation over a batch.  The members are grouped
+// by the producers' column-pair variant (a function of the radius); one
+// persistent launch per group walks the tiles of all its members (largest
+// tiles first, CTA b takes work items b, b + grid, ...), each member with its
+// own tensor maps, size and D, read from a device table.  tc_batch_prepare
+// fills the table (host memory of tc_batch_table_bytes(n) bytes, to be copied
+// to a device buffer of that size that stays allocated while launches use it)
+// and the launch description; the per-pixel results equal
+// launch_aggregate_tc's bit for bit.
+struct TcBatchMember {
+    const void* cost;      // 16-bit x-blocked volume written by launch_cost_build_xblock16
+    const uint2* rgbx;     // its packed guide
+    int H, W, C, D, radius;
+    float sigma_s, sigma_r;
+    int32_t* disp_int;
+    float* disp_sub;
+};
+struct TcBatchGroup {
+    int variant, first, npairs, nitems;    // members first .. first + npairs - 1 of the table
+    int R, S, nacc, kw_max, nh_max, any_ones;
+    uint32_t a_stage, b_stage, acc_stride, tmem_cols;
+    size_t smem;
+};
+struct TcBatchLaunch {
+    int ngroups;
+    TcBatchGroup group[18];
+};
+size_t tc_batch_table_bytes(int n);
+cudaError_t tc_batch_prepare(int n, const TcBatchMember* members, bool bf16, void* host_table, TcBatchLaunch* out);
+// Launches every group in order on `stream` (one kernel each).
+cudaError_t launch_aggregate_tc_batch(const void* dev_table, const TcBatchLaunch& launch, bool bf16, int* err,
+                                      int num_sms, long long wait_cycles, cudaStream_t stream);
 // Packed guide plane of an image: (RGBX, squared norm) per pixel, pitch rgbx_pitch(W); the
 // tensor-core path loads its guide tiles from it.
 cudaError_t launch_pack_rgbx(const uint8_t* img, int H, int W, int C, uint2* rgbx, cudaStream_t stream);

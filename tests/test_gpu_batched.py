@@ -2,7 +2,9 @@
 reproduce fbs_compute_disparity bit for bit in the context's precision (FP32:
 one persistent launch per stage, same tile code, same data, same order;
 BF16 / FP16: the single-pair tensor-core launches spread over concurrent graph
-branches), under every plan, and the autotuner's choice must persist."""
+branches, or the cost builds and one persistent tensor-core launch over the
+tiles of every pair), under every plan, and the autotuner's choice must
+persist."""
 
 import os
 
@@ -108,7 +110,7 @@ def test_batched_rejects_bad_pairs(fbs):
             fbs.fbs_compute_disparity_batched(ctx.ctx, pairs)
         assert ei.value.status == fbs.FBS_ERR_UNSUPPORTED and "pair 2" in str(ei.value)
         with pytest.raises(fbs.FBSError) as ei:
-            fbs.fbs_batch_set_plan(ctx.ctx, pairs, 6)
+            fbs.fbs_batch_set_plan(ctx.ctx, pairs, 7)
         assert ei.value.status == fbs.FBS_ERR_INVALID_ARG
 
 
@@ -133,6 +135,17 @@ def test_fp32_batch_equals_per_pair_under_every_plan(fbs, mode):
             fbs.fbs_batch_set_plan(ctx.ctx, pairs, 7)
 
 
+def _tc_variants(pairs):
+    """Radius variants of the tensor-core producers in a batch: the persistent
+    plan launches one aggregation per variant (column pairs per thread
+    ceil((r + 1) / 2) exact up to 8, split by the parity of r; 10 and 13
+    above)."""
+    def v(r):
+        npt = (r + 2) // 2
+        return (npt, r & 1) if npt <= 8 else (10 if npt <= 10 else 13,)
+    return len({v(q["radius"]) for q in pairs})
+
+
 def _per_pair(ctx, pairs):
     ref = []
     for q in pairs:
@@ -149,7 +162,7 @@ def test_tensor_core_batch_equals_per_pair_under_every_plan(fbs, prec, mode):
     pairs[0]["D"], pairs[0]["radius"] = 256, 9    # the largest disparity range, more than one TMEM block
     with fbs.Context(0, cost=mode, prec=p) as ctx:
         ref = _per_pair(ctx, pairs)
-        for plan in range(6):
+        for plan in range(7):
             for q in pairs:
                 q["disp_int"].fill_(-7)
                 q["disp_subpix"].fill_(-7.0)
@@ -171,15 +184,17 @@ def test_tensor_core_batch_autotunes_and_follows_new_buffers(fbs):
         fbs.fbs_compute_disparity_batched(ctx.ctx, pairs, torch.cuda.current_stream())
         torch.cuda.synchronize()
         plan = fbs.fbs_batch_plan(ctx.ctx, pairs)
-        assert 0 <= plan < 6
+        assert 0 <= plan < 7
         ref = _per_pair(ctx, pairs)
         for q, (di, ds) in zip(pairs, ref):
             assert torch.equal(q["disp_int"], di) and torch.equal(q["disp_subpix"], ds)
-        # every kernel is counted: per pair one cost kernel and one aggregation
+        # every kernel is counted: per pair one cost kernel, and one aggregation
+        # per pair or (plan 6) one persistent aggregation per radius variant
         fbs.fbs_profile(ctx.ctx, 1)
         fbs.fbs_compute_disparity_batched(ctx.ctx, pairs, torch.cuda.current_stream())
         torch.cuda.synchronize()
-        assert fbs.fbs_profile_read(ctx.ctx, fbs.FBS_KERNEL_AGG_TC)[1] == len(pairs)
+        assert fbs.fbs_profile_read(ctx.ctx, fbs.FBS_KERNEL_AGG_TC)[1] == (_tc_variants(pairs) if plan == 6
+                                                                           else len(pairs))
         assert fbs.fbs_profile_read(ctx.ctx, fbs.FBS_KERNEL_COST)[1] == len(pairs)
         fbs.fbs_profile(ctx.ctx, 0)
         # new output buffers and new images of the same shapes: a new graph, the same results as per-pair calls
@@ -193,3 +208,59 @@ def test_tensor_core_batch_autotunes_and_follows_new_buffers(fbs):
         for (gi, gs), (di, ds) in zip(got, ref2):
             assert torch.equal(gi, di) and torch.equal(gs, ds)
         fbs.fbs_sync(ctx.ctx)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_persistent_tensor_core_plan_covers_every_radius_variant(fbs, prec):
+    """Plan 6 (persistent tensor-core launches over every pair's tiles) on
+    a batch whose radii reach every instantiated column-pair variant (radius
+    0 .. 24, odd and even, including the two generic wide ones) and whose
+    disparity ranges span one to more than one TMEM block (D up to 256, where
+    the normaliser takes its own MMA): bit-identical to per-pair calls."""
+    p = fbs.FBS_PREC_BF16 if prec == "bf16" else fbs.FBS_PREC_F16
+    rng = np.random.default_rng(77)
+    radii = list(range(0, 17)) + [17, 19, 20, 22, 24]
+    Ds = [8, 16, 24, 40, 64, 100, 128, 200, 256]
+    pairs = []
+    for i, r in enumerate(radii):
+        H, W = int(rng.integers(9, 70)), int(rng.integers(17, 120))
+        C = int(rng.choice([1, 3]))
+        D = Ds[i % len(Ds)]
+        L = rng.integers(0, 256, size=(H, W, C)).astype(np.uint8)
+        R = np.roll(L, -int(rng.integers(0, 6)), axis=1)
+        pairs.append(dict(left=torch.from_numpy(L).cuda(), right=torch.from_numpy(R).cuda(), H=H, W=W, C=C, D=D,
+                          radius=r, sigma_s=float(max(r, 1)), sigma_r=12.0, tau=20.0,
+                          disp_int=torch.full((H, W), -7, dtype=torch.int32, device="cuda"),
+                          disp_subpix=torch.full((H, W), -7.0, dtype=torch.float32, device="cuda")))
+    with fbs.Context(0, prec=p) as ctx:
+        ref = _per_pair(ctx, pairs)
+        fbs.fbs_batch_set_plan(ctx.ctx, pairs, 6)
+        fbs.fbs_profile(ctx.ctx, 1)
+        for rep in range(2):   # the second call replays the same graph
+            fbs.fbs_compute_disparity_batched(ctx.ctx, pairs, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            fbs.fbs_sync(ctx.ctx)
+            for i, (q, (di, ds)) in enumerate(zip(pairs, ref)):
+                assert torch.equal(q["disp_int"], di), (rep, i, q["radius"], q["D"])
+                assert torch.equal(q["disp_subpix"], ds), (rep, i, q["radius"], q["D"])
+        assert fbs.fbs_profile_read(ctx.ctx, fbs.FBS_KERNEL_AGG_TC)[1] == 2 * _tc_variants(pairs) == 2 * 18
+        fbs.fbs_profile(ctx.ctx, 0)
+
+
+def test_persistent_tensor_core_plan_member_matches_oracle(fbs, oracle_mod):
+    """A BF16 member of the persistent plan against the FP64 oracle: integer
+    and subpixel disparities under the 16-bit rules (aggregated-cost bound
+    3 u R + 1e-5, u = 2^-9, R = 2)."""
+    from tests._compare import check_disparities
+    pairs = _batch(13, n=5)
+    with fbs.Context(0, prec=fbs.FBS_PREC_BF16) as ctx:
+        fbs.fbs_batch_set_plan(ctx.ctx, pairs, 6)
+        fbs.fbs_compute_disparity_batched(ctx.ctx, pairs, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        fbs.fbs_sync(ctx.ctx)
+    tol = 3 * 2.0 ** -9 * 2.0 + 1e-5
+    for q in pairs:
+        L, R = q["left"].cpu().numpy(), q["right"].cpu().numpy()
+        ref_di, ref_ds, ref_agg = oracle_mod.fbs(L, R, q["D"], q["radius"], q["sigma_s"], q["sigma_r"], want_agg=True)
+        check_disparities(q["disp_int"].cpu().numpy(), q["disp_subpix"].cpu().numpy(), ref_agg, ref_di, ref_ds, 2.0,
+                          tol=tol)
