@@ -356,26 +356,40 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
     } else if (warp == kTmaWarp) {
         // ================= TMA producer of guide tiles and cost rows ==========
         if (lane == 0) {
-            uint32_t g = 0, gs = 0, gu = 0, t = 0, gpend = 0;
+            uint32_t g = 0, gs = 0, gu = 0, t = 0, gpend = 0;   // gpend: guide tiles issued
             const uint32_t guide_bytes = (uint32_t)p.NH * KW * 8;
+            // guide tile of tile number tt at (tx0, ty0) into slot tt & 1, once the
+            // producers have released that slot (tile tt - 2); without `block`
+            // only when the slot is already free.  Returns false on abort.
+            auto issue_guide = [&](uint32_t tt, int tx0, int ty0, bool block) -> bool {
+                const uint32_t tb = tt & 1, u = tt >> 1;
+                if (u > 0) {
+                    if (!block) {
+                        if (!mbar_try_wait(g_empty0 + 8 * tb, (u - 1) & 1)) return true;
+                    } else if (!mbar_wait_or_abort(g_empty0 + 8 * tb, (u - 1) & 1, abort_flag, p.wait_cycles)) {
+                        raise_abort(abort_flag, err, 7);
+                        return false;
+                    }
+                }
+                mbar_expect_tx(g_full0 + 8 * tb, guide_bytes);
+                tma_load_2d(smem_u32(gtile + tb * (p.NH * KW)), &gmap, tx0 - p.rho8, ty0 - p.rho, g_full0 + 8 * tb);
+                gpend = tt + 1;
+                return true;
+            };
             bool stop = false;
             for (TileWalk tw(p.ntx); tw.tile < p.ntiles && !stop; tw.next(), ++t) {
                 const int tx0 = tw.tx * kTW, ty0 = tw.ty * kTH;
                 const int xlo = tx0 - p.rho8;
-                {
-                    const uint32_t tb = t & 1, u = t >> 1;
-                    if (u > 0 && !mbar_wait_or_abort(g_empty0 + 8 * tb, (u - 1) & 1, abort_flag, p.wait_cycles)) {
-                        raise_abort(abort_flag, err, 7);
-                        break;
-                    }
-                    mbar_expect_tx(g_full0 + 8 * tb, guide_bytes);
-                    tma_load_2d(smem_u32(gtile + tb * (p.NH * KW)), &gmap, xlo, ty0 - p.rho, g_full0 + 8 * tb);
-                    gpend = t + 1;
-                }
+                if (gpend == t && !issue_guide(t, tx0, ty0, true)) break;
+                // the next tile's guide goes out as soon as its slot is free,
+                // between this tile's cost rows, so that it has landed when the
+                // producers reach that tile
+                TileWalk nx = tw;
+                nx.next();
+                const bool has_next = nx.tile < p.ntiles;
                 const int hr_lo = max(0, p.rho - ty0);
                 const int hr_hi = min(p.NH, p.H - ty0 + p.rho);
                 for (int h0 = hr_lo; h0 < hr_hi; h0 += R) {
-                    const int nr = min(R, hr_hi - h0);
                     const uint32_t s = gs, use = gu;   // g % S, g / S
                     if (use > 0 && !mbar_wait_or_abort(empty0 + 8 * s, (use - 1) & 1, abort_flag, p.wait_cycles)) {
                         raise_abort(abort_flag, err, 2);
@@ -389,6 +403,10 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                     if (++gs == (uint32_t)S) {
                         gs = 0;
                         ++gu;
+                    }
+                    if (has_next && gpend == t + 1 && !issue_guide(t + 1, nx.tx * kTW, nx.ty * kTH, false)) {
+                        stop = true;
+                        break;
                     }
                 }
             }

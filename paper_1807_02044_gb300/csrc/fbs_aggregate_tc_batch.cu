@@ -418,10 +418,32 @@ aggregate_tc_batch_kernel(const __grid_constant__ TcBatchArgs a, int* __restrict
     } else if (warp == kTmaWarp) {
         // ================= TMA producer of guide tiles and cost rows ==========
         if (lane == 0) {
-            uint32_t g = 0, gs = 0, gu = 0, t = 0, gpend = 0;
-            MemberView P;
+            uint32_t g = 0, gs = 0, gu = 0, t = 0, gpend = 0;   // gpend: guide tiles issued
+            MemberView P, Q;   // the member of this tile and of the next one
             P.end = -1;
             P.index = 0;
+            Q.end = -1;
+            Q.index = 0;
+            // guide tile of tile number tt (item `it` of member M) into slot
+            // tt & 1, once the producers have released that slot; without
+            // `block` only when it is already free.  Returns false on abort.
+            auto issue_guide = [&](uint32_t tt, const MemberView& M, int it, bool block) -> bool {
+                const uint32_t tb = tt & 1, u = tt >> 1;
+                if (u > 0) {
+                    if (!block) {
+                        if (!mbar_try_wait(g_empty0 + 8 * tb, (u - 1) & 1)) return true;
+                    } else if (!mbar_wait_or_abort(g_empty0 + 8 * tb, (u - 1) & 1, abort_flag, a.wait_cycles)) {
+                        raise_abort(abort_flag, err, 7);
+                        return false;
+                    }
+                }
+                int gx0, gy0;
+                tile_of(M, it, gx0, gy0);
+                mbar_expect_tx(g_full0 + 8 * tb, (uint32_t)M.NH * M.KW * 8);
+                tma_load_2d(smem_u32(g_base + tb * g_slot), &M.p->gmap, gx0 - M.rho8, gy0 - M.rho, g_full0 + 8 * tb);
+                gpend = tt + 1;
+                return true;
+            };
             bool stop = false;
             for (int item = (int)blockIdx.x; item < a.nitems && !stop; item += grid, ++t) {
                 if (item >= P.end) {
@@ -432,16 +454,11 @@ aggregate_tc_batch_kernel(const __grid_constant__ TcBatchArgs a, int* __restrict
                 int tx0, ty0;
                 tile_of(P, item, tx0, ty0);
                 const int xlo = tx0 - P.rho8;
-                {
-                    const uint32_t tb = t & 1, u = t >> 1;
-                    if (u > 0 && !mbar_wait_or_abort(g_empty0 + 8 * tb, (u - 1) & 1, abort_flag, a.wait_cycles)) {
-                        raise_abort(abort_flag, err, 7);
-                        break;
-                    }
-                    mbar_expect_tx(g_full0 + 8 * tb, (uint32_t)P.NH * P.KW * 8);
-                    tma_load_2d(smem_u32(g_base + tb * g_slot), &P.p->gmap, xlo, ty0 - P.rho, g_full0 + 8 * tb);
-                    gpend = t + 1;
-                }
+                if (gpend == t && !issue_guide(t, P, item, true)) break;
+                // the next tile's guide goes out as soon as its slot is free
+                const int next = item + grid;
+                const bool has_next = next < a.nitems;
+                if (has_next && next >= Q.end) view_member(Q, pairs, member_of(pairs, a.npairs, Q.index, next));
                 const uint32_t box = (uint32_t)P.R * (P.KW / 8) * P.Nb * 16;
                 const int hr_lo = max(0, P.rho - ty0);
                 const int hr_hi = min(P.NH, P.H - ty0 + P.rho);
@@ -459,6 +476,10 @@ aggregate_tc_batch_kernel(const __grid_constant__ TcBatchArgs a, int* __restrict
                     if (++gs == (uint32_t)S) {
                         gs = 0;
                         ++gu;
+                    }
+                    if (has_next && gpend == t + 1 && !issue_guide(t + 1, Q, next, false)) {
+                        stop = true;
+                        break;
                     }
                 }
             }
