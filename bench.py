@@ -276,13 +276,19 @@ def _config(p, args, impl):
 # ---------------------------------------------------------------------------
 def _traffic_for(kernel_file, kernel_name):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of the kernel (else None)."""
+    on the current source of the kernel (else None).  kernel_file is one path
+    or a list of paths (the kernel's .cu and the headers holding its code),
+    hashed in order."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
+    files = [kernel_file] if isinstance(kernel_file, str) else list(kernel_file)
     try:
         with open(path) as f:
             t = json.load(f)
-        with open(kernel_file, "rb") as f:
-            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        hs = hashlib.sha256()
+        for fn in files:
+            with open(fn, "rb") as f:
+                hs.update(f.read())
+        h = hs.hexdigest()[:16]
     except (OSError, ValueError):
         return None
     ent = t.get(kernel_name)
@@ -464,7 +470,8 @@ def run_ours(args):
                     "unit": "TFLOP/s", "peak_source": f"bf16_tflops burst ({peak_src}); FP16 dense equals BF16",
                     "issued_dense_tflops": issued / (agg_launch_ms * 1e-3) / 1e12,
                     "issued_over_algorithmic": issued / flops,
-                    "traffic": _traffic_for(os.path.join(csrc, "fbs_aggregate_tc.cu"), "aggregate_tc_kernel")}
+                    "traffic": _traffic_for([os.path.join(csrc, "fbs_aggregate_tc.cu"), os.path.join(csrc, "tc_aggregate.cuh")],
+                                           "aggregate_tc_kernel")}
     roofline.update({"algorithmic": "2 flop per tap (one multiply-add per window tap per disparity), "
                                     "H*W*D*(2r+1)^2 taps", "avg_launch_ms": agg_launch_ms, "launches": agg_n})
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
