@@ -67,13 +67,13 @@ def _load():
             lib.oracle_fbs_right_rows.restype = I
             lib.oracle_lrc.argtypes = [P, P, I, I, P]
             lib.oracle_band_downsample.argtypes = [P, I, I, I, P]
-            lib.oracle_band_features.argtypes = [P, P, I, I, I, I, P, P]
+            lib.oracle_band_features.argtypes = [P, P, I, I, I, I, P, P, P]
             lib.oracle_band_features.restype = I
             lib.oracle_band_limits.argtypes = [P, P, I, I, I, ctypes.c_float, P, P]
             lib.oracle_fbs_band_points.argtypes = [P, P, I, I, I, I, I, Dd, Dd, I, P, P, P, P, P, P, P]
             lib.oracle_fbs_band_points.restype = I
             lib.oracle_band_targets.argtypes = [P, P, I, I, I, I, P, P, P]
-            lib.oracle_band_feature_points.argtypes = [P, P, I, I, I, I, ctypes.c_float, P, P]
+            lib.oracle_band_feature_points.argtypes = [P, P, I, I, I, I, Dd, P, P, Dd, P]
             lib.oracle_band_feature_points.restype = I
             _lib = lib
     return _lib
@@ -219,16 +219,19 @@ def band_downsample(img):
     return out
 
 
-def band_features(left, right, D):
-    """B1-B3: features [Hq][Wq][6] (float32) and the coarse winner e* (int32)."""
+def band_features(left, right, D, with_gap=False):
+    """B1-B3: features [Hq][Wq][6] (float64) and the coarse winner e* (int32);
+    with_gap also returns, per quarter pixel, the second smallest minus the
+    smallest coarse aggregated cost (the distance of the winner from a tie)."""
     L, R = _img(left), _img(right)
     H, W, C = L.shape
     Hq, Wq, _ = quarter_shape(H, W, D)
-    feat = np.empty((Hq, Wq, 6), np.float32)
+    feat = np.empty((Hq, Wq, 6), np.float64)
     est = np.empty((Hq, Wq), np.int32)
-    if _load().oracle_band_features(_ptr(L), _ptr(R), H, W, C, D, _ptr(feat), _ptr(est)) != 0:
+    gap = np.empty((Hq, Wq), np.float64)
+    if _load().oracle_band_features(_ptr(L), _ptr(R), H, W, C, D, _ptr(feat), _ptr(est), _ptr(gap)) != 0:
         raise MemoryError("oracle_band_features could not allocate")
-    return feat, est
+    return (feat, est, gap) if with_gap else (feat, est)
 
 
 def band_limits(centre, conf, D, half_band, theta):
@@ -276,15 +279,19 @@ def band_targets(label_int, label_sub, D, half_band, centre_q):
     return t, y
 
 
-def band_feature_points(left, right, D, theta_m):
-    """B7: feature-point centre and confidence (float32, H x W)."""
+def band_feature_points(left, right, D, theta_m, tol=None):
+    """B7: feature-point centre and confidence (float32, H x W).  With tol, also
+    the pixels whose 5x5 quarter window holds a decision within tol of
+    changing (a margin within tol of theta_m, or a winner within tol of a tie)."""
     L, R = _img(left), _img(right)
     H, W, C = L.shape
     c = np.empty((H, W), np.float32)
     k = np.empty((H, W), np.float32)
-    if _load().oracle_band_feature_points(_ptr(L), _ptr(R), H, W, C, D, float(theta_m), _ptr(c), _ptr(k)) != 0:
+    amb = np.zeros((H, W), np.uint8)
+    if _load().oracle_band_feature_points(_ptr(L), _ptr(R), H, W, C, D, float(theta_m), _ptr(c), _ptr(k),
+                                          float(tol or 0.0), _ptr(amb)) != 0:
         raise MemoryError("oracle_band_feature_points could not allocate")
-    return c, k
+    return (c, k, amb.astype(bool)) if tol is not None else (c, k)
 
 
 def e_pep(estimate, truth, eps, mask=None):

@@ -25,18 +25,17 @@
  *   B2  coarse cost: Eq. (1)-(3) with varrho = 1 on the quarter-resolution
  *       intensity, quarter disparities e in [0, Dq), the same boundary rules
  *       as the full-resolution cost (clamped blocks, cost 2 when X - e < 0,
- *       c = 0 for a flat block); cost K = 1 - c.  Sums are exact integers;
- *       the normalisation is evaluated in FP32 with correctly rounded
- *       operations in a fixed order, so the kernels reach the same bits and
- *       the same winners (the winner is an integer decided by floating point,
- *       and both sides decide it in the same precision).
+ *       c = 0 for a flat block); cost K = 1 - c.  Sums are exact integers,
+ *       the normalisation is FP64.
  *   B3  coarse aggregation: Kbar(X, Y, e) = the mean of K(X', Y', e) over the
- *       5x5 quarter-resolution window around (X, Y) clipped to the image,
- *       evaluated in FP32 as row sums (X' ascending), then the sum of those
- *       row sums (Y' ascending), then one division by the number of in-image
- *       taps -- a box-filter counterpart, at quarter resolution, of the
+ *       5x5 quarter-resolution window around (X, Y) clipped to the image
+ *       (FP64) -- a box-filter counterpart, at quarter resolution, of the
  *       aggregation of Sec. II-B, which makes the coarse winner reliable.
- *       Features per quarter pixel (all FP32, same operation order):
+ *       The kernels evaluate B2-B3 in FP32; the tests allow the FP32
+ *       rounding bound and compare the integer decisions (the winner, the
+ *       feature points of B7) exactly wherever the FP64 values are not
+ *       within that bound of a tie or of the threshold.
+ *       Features per quarter pixel (FP64):
  *         f0 = G_l / (16 * 255 * C) - 0.5      (left intensity)
  *         f1 = e* / Dq                         (coarse winner of Kbar, smallest e on ties)
  *         f2 = Kbar(e*)                        (its cost)
@@ -54,7 +53,7 @@
  *       ends play the role of 0 and D - 1).
  *   B7  feature-point proposal (the paper's future work, Sec. V: reliable
  *       feature points suggest the search range of their neighbours): a
- *       quarter pixel is a feature point when its margin f3 >= theta_m (FP32);
+ *       quarter pixel is a feature point when its margin f3 >= theta_m;
  *       a full-resolution pixel in quarter pixel i takes the feature points of
  *       the 5x5 quarter window around i (clipped); with at least 3 of them and
  *       max e* - min e* <= 2 its centre is 2 (max e* + min e*) (= 4 x the
@@ -97,9 +96,9 @@ void oracle_band_downsample(const uint8_t *img, int H, int W, int C, int32_t *gq
 }
 
 /* B2: coarse cost K(X, Y, e) from the two quarter-resolution planes. */
-static float coarse_cost(const int32_t *gl, const int32_t *gr, int Hq, int Wq, int X, int Y, int e)
+static double coarse_cost(const int32_t *gl, const int32_t *gr, int Hq, int Wq, int X, int Y, int e)
 {
-    if (X - e < 0) return 2.0f;
+    if (X - e < 0) return 2.0;
     int64_t Sl = 0, Ql = 0, Sr = 0, Qr = 0, P = 0;
     for (int j = -1; j <= 1; ++j) {
         const int y = bclampi(Y + j, 0, Hq - 1);
@@ -115,81 +114,75 @@ static float coarse_cost(const int32_t *gl, const int32_t *gr, int Hq, int Wq, i
     }
     const int64_t Vl = 9 * Ql - Sl * Sl;
     const int64_t Vr = 9 * Qr - Sr * Sr;
-    if (Vl == 0 || Vr == 0) return 1.0f;
+    if (Vl == 0 || Vr == 0) return 1.0;
     const int64_t num = 9 * P - Sl * Sr;
-    const float vv = (float)Vl * (float)Vr;
-    const float c = (float)num / sqrtf(vv);
-    return 1.0f - c;
+    return 1.0 - (double)num / sqrt((double)Vl * (double)Vr);
 }
 
 #define BAND_AGG_R 2   /* 5x5 coarse aggregation window */
 
 /*
- * B1-B3: features [Hq][Wq][6] (FP32) and the coarse winner e* [Hq][Wq] of a
- * pair.  Scratch is allocated here.  Returns 0, or -1 when out of memory.
+ * B1-B3: features [Hq][Wq][6] (FP64) and the coarse winner e* [Hq][Wq] of a
+ * pair; gap [Hq][Wq] (nullable): second smallest minus smallest Kbar of each
+ * quarter pixel (how close its winner is to a tie).  Scratch is allocated
+ * here.  Returns 0, or -1 when out of memory.
  */
-int oracle_band_features(const uint8_t *L, const uint8_t *R, int H, int W, int C, int D, float *feat,
-                         int32_t *estar)
+int oracle_band_features(const uint8_t *L, const uint8_t *R, int H, int W, int C, int D, double *feat,
+                         int32_t *estar, double *gap)
 {
     const int Hq = (H + 3) / 4, Wq = (W + 3) / 4, Dq = (D + 3) / 4;
     const size_t nq = (size_t)Hq * Wq;
     int32_t *gl = (int32_t *)malloc(sizeof(int32_t) * nq);
     int32_t *gr = (int32_t *)malloc(sizeof(int32_t) * nq);
-    float *K = (float *)malloc(sizeof(float) * nq * Dq);
-    float *Kh = (float *)malloc(sizeof(float) * nq * Dq);
-    if (!gl || !gr || !K || !Kh) { free(gl); free(gr); free(K); free(Kh); return -1; }
+    double *K = (double *)malloc(sizeof(double) * nq * Dq);
+    double *Kb = (double *)malloc(sizeof(double) * Dq);
+    if (!gl || !gr || !K || !Kb) { free(gl); free(gr); free(K); free(Kb); return -1; }
     oracle_band_downsample(L, H, W, C, gl);
     oracle_band_downsample(R, H, W, C, gr);
     for (int Y = 0; Y < Hq; ++Y)
         for (int X = 0; X < Wq; ++X)
             for (int e = 0; e < Dq; ++e) K[((size_t)Y * Wq + X) * Dq + e] = coarse_cost(gl, gr, Hq, Wq, X, Y, e);
-    /* B3: row sums, then column sums of the row sums, then the mean */
-    for (int Y = 0; Y < Hq; ++Y)
-        for (int X = 0; X < Wq; ++X)
-            for (int e = 0; e < Dq; ++e) {
-                float s = 0.0f;
-                for (int x = X - BAND_AGG_R; x <= X + BAND_AGG_R; ++x)
-                    if (x >= 0 && x < Wq) s += K[((size_t)Y * Wq + x) * Dq + e];
-                Kh[((size_t)Y * Wq + X) * Dq + e] = s;
-            }
-    const float gscale = (float)(16 * 255 * C);
-    float *Kb = K;   /* K is no longer needed: reuse it for one pixel's Kbar */
+    const double gscale = 16.0 * 255.0 * C;
     for (int Y = 0; Y < Hq; ++Y) {
-        const int y0 = Y - BAND_AGG_R < 0 ? 0 : Y - BAND_AGG_R;
-        const int y1 = Y + BAND_AGG_R > Hq - 1 ? Hq - 1 : Y + BAND_AGG_R;
         for (int X = 0; X < Wq; ++X) {
-            const int x0 = X - BAND_AGG_R < 0 ? 0 : X - BAND_AGG_R;
-            const int x1 = X + BAND_AGG_R > Wq - 1 ? Wq - 1 : X + BAND_AGG_R;
-            const float n = (float)((y1 - y0 + 1) * (x1 - x0 + 1));
+            /* B3: mean over the clipped 5x5 window */
             for (int e = 0; e < Dq; ++e) {
-                float s = 0.0f;
-                for (int y = y0; y <= y1; ++y) s += Kh[((size_t)y * Wq + X) * Dq + e];
+                double s = 0.0;
+                int n = 0;
+                for (int y = Y - BAND_AGG_R; y <= Y + BAND_AGG_R; ++y)
+                    for (int x = X - BAND_AGG_R; x <= X + BAND_AGG_R; ++x)
+                        if (y >= 0 && y < Hq && x >= 0 && x < Wq) {
+                            s += K[((size_t)y * Wq + x) * Dq + e];
+                            ++n;
+                        }
                 Kb[e] = s / n;
             }
             int best = 0;
             for (int e = 1; e < Dq; ++e)
                 if (Kb[e] < Kb[best]) best = e;
-            float k2 = 2.0f;
-            for (int e = 0; e < Dq; ++e)
+            double k2 = 2.0, second = INFINITY;
+            for (int e = 0; e < Dq; ++e) {
                 if (abs(e - best) >= 2 && Kb[e] < k2) k2 = Kb[e];
-            const float k1 = Kb[best];
-            const float km = best > 0 ? Kb[best - 1] : 2.0f;
-            const float kp = best < Dq - 1 ? Kb[best + 1] : 2.0f;
-            float *f = feat + ((size_t)Y * Wq + X) * 6;
-            f[0] = (float)gl[(size_t)Y * Wq + X] / gscale - 0.5f;
-            f[1] = (float)best / (float)Dq;
+                if (e != best && Kb[e] < second) second = Kb[e];
+            }
+            const double k1 = Kb[best];
+            const double km = best > 0 ? Kb[best - 1] : 2.0;
+            const double kp = best < Dq - 1 ? Kb[best + 1] : 2.0;
+            double *f = feat + ((size_t)Y * Wq + X) * 6;
+            f[0] = gl[(size_t)Y * Wq + X] / gscale - 0.5;
+            f[1] = (double)best / Dq;
             f[2] = k1;
-            const float margin = k2 - k1;
-            f[3] = margin < 1.0f ? margin : 1.0f;
+            f[3] = k2 - k1 < 1.0 ? k2 - k1 : 1.0;
             f[4] = km - k1;
             f[5] = kp - k1;
             estar[(size_t)Y * Wq + X] = best;
+            if (gap) gap[(size_t)Y * Wq + X] = second - k1;
         }
     }
     free(gl);
     free(gr);
     free(K);
-    free(Kh);
+    free(Kb);
     return 0;
 }
 
@@ -299,27 +292,36 @@ void oracle_band_targets(const int32_t *label_int, const float *label_sub, int H
     }
 }
 
-/* B7: feature-point centre and confidence [H][W] (FP32) of a pair. */
-int oracle_band_feature_points(const uint8_t *L, const uint8_t *R, int H, int W, int C, int D, float theta_m,
-                               float *centre, float *conf)
+/*
+ * B7: feature-point centre and confidence [H][W] (FP32 outputs) of a pair.
+ * ambiguous [H][W] (nullable) is set where the window holds a quarter pixel
+ * whose decision is within tol of changing: a margin within tol of theta_m,
+ * or a winner within tol of a tie (then its e* and margin may differ under
+ * rounding).
+ */
+int oracle_band_feature_points(const uint8_t *L, const uint8_t *R, int H, int W, int C, int D, double theta_m,
+                               float *centre, float *conf, double tol, uint8_t *ambiguous)
 {
     const int Hq = (H + 3) / 4, Wq = (W + 3) / 4;
-    float *feat = (float *)malloc(sizeof(float) * (size_t)Hq * Wq * 6);
+    double *feat = (double *)malloc(sizeof(double) * (size_t)Hq * Wq * 6);
+    double *gap = (double *)malloc(sizeof(double) * (size_t)Hq * Wq);
     int32_t *est = (int32_t *)malloc(sizeof(int32_t) * (size_t)Hq * Wq);
-    if (!feat || !est || oracle_band_features(L, R, H, W, C, D, feat, est) != 0) {
+    if (!feat || !gap || !est || oracle_band_features(L, R, H, W, C, D, feat, est, gap) != 0) {
         free(feat);
+        free(gap);
         free(est);
         return -1;
     }
     for (int y = 0; y < H; ++y) {
         for (int x = 0; x < W; ++x) {
             const int Y = y / 4, X = x / 4;
-            int n = 0, emin = 1 << 30, emax = -1;
+            int n = 0, emin = 1 << 30, emax = -1, amb = 0;
             for (int j = Y - 2; j <= Y + 2; ++j) {
                 if (j < 0 || j >= Hq) continue;
                 for (int i = X - 2; i <= X + 2; ++i) {
                     if (i < 0 || i >= Wq) continue;
                     const size_t q = (size_t)j * Wq + i;
+                    if (fabs(feat[q * 6 + 3] - theta_m) <= tol || gap[q] <= tol) amb = 1;
                     if (!(feat[q * 6 + 3] >= theta_m)) continue;
                     ++n;
                     if (est[q] < emin) emin = est[q];
@@ -334,9 +336,11 @@ int oracle_band_feature_points(const uint8_t *L, const uint8_t *R, int H, int W,
                 centre[p] = 0.0f;
                 conf[p] = 0.0f;
             }
+            if (ambiguous) ambiguous[p] = (uint8_t)amb;
         }
     }
     free(feat);
+    free(gap);
     free(est);
     return 0;
 }

@@ -41,21 +41,57 @@ def _rand_pair(seed, H, W, C=3, shift=5):
 
 
 # ---------------------------------------------------------------------------
-# Features and band limits: bit-exact
+# Features (against the FP64 oracle within the FP32 rounding bound), band
+# limits (bit-exact)
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("H,W,C,D", [(37, 45, 3, 40), (64, 200, 3, 128), (23, 530, 1, 64), (8, 8, 3, 4)])
-def test_features_bit_exact(fbs, oracle_mod, H, W, C, D):
-    L, R = _rand_pair(H * W + D, H, W, C, shift=9)
-    Hq, Wq, _ = oracle_mod.quarter_shape(H, W, D)
+# FP32 unit roundoff, and the bound on the kernels' coarse aggregated cost:
+# K = 1 - num / sqrt(Vl Vr) from exact integers rounds the two conversions,
+# the product, the square root, the conversion of num, the division and the
+# subtraction (|c| <= 1, |K| <= 2): |dK| <= 6.5 u.  Kbar sums at most 25 such
+# values (|K| <= 2) as row sums and a sum of row sums, then divides by the
+# n >= 9 in-image taps: |dKbar| <= (4u 2n + 4u 2n + 6.5u n) / n + 2u = 24.5 u;
+# the tests use 32 u.
+U32 = 2.0 ** -24
+TOL_KBAR = 32 * U32
+
+
+def _gpu_features(fbs, L, R, D):
+    H, W = L.shape[:2]
+    C = L.shape[2] if L.ndim == 3 else 1
+    Hq, Wq = (H + 3) // 4, (W + 3) // 4
     feat = torch.empty((Hq, Wq, 6), dtype=torch.float32, device="cuda")
     est = torch.empty((Hq, Wq), dtype=torch.int32, device="cuda")
     with fbs.Context(0) as ctx:
         fbs.fbs_band_features(ctx.ctx, _dev(L), _dev(R), H, W, C, D, feat, est)
         torch.cuda.synchronize()
         fbs.fbs_sync(ctx.ctx)
-    rf, re = oracle_mod.band_features(L, R, D)
-    assert np.array_equal(est.cpu().numpy(), re)
-    assert np.array_equal(feat.cpu().numpy().view(np.uint32), rf.view(np.uint32))
+    return feat.cpu().numpy(), est.cpu().numpy()
+
+
+@pytest.mark.parametrize("H,W,C,D", [(37, 45, 3, 40), (64, 200, 3, 128), (23, 530, 1, 64), (8, 8, 3, 4)])
+def test_features_match_the_fp64_oracle(fbs, oracle_mod, H, W, C, D):
+    """B1-B3 against the FP64 oracle: the coarse winner identical wherever the
+    oracle's best and second best Kbar are more than 2 TOL_KBAR apart (at the
+    others the kernel's winner must itself be within 2 TOL_KBAR of the best);
+    f2 = Kbar(e*) within TOL_KBAR, the differences f3..f5 within 2 TOL_KBAR +
+    2u, f0 within 2u, f1 = e*/Dq exact in FP32."""
+    L, R = _rand_pair(H * W + D, H, W, C, shift=9)
+    gf, ge = _gpu_features(fbs, L, R, D)
+    rf, re, gap = oracle_mod.band_features(L, R, D, with_gap=True)
+    Dq = (D + 3) // 4
+    gf = gf.astype(np.float64)
+    tie = gap <= 2 * TOL_KBAR
+    assert np.array_equal(ge[~tie], re[~tie])
+    assert np.all(np.abs(gf[..., 2] - rf[..., 2])[tie] <= 2 * TOL_KBAR)
+    same = ge == re
+    assert np.all(np.abs(gf[..., 2] - rf[..., 2])[same] <= TOL_KBAR)
+    for k in (3, 4, 5):
+        assert np.all(np.abs(gf[..., k] - rf[..., k])[same] <= 2 * TOL_KBAR + 2 * U32), k
+    assert np.all(np.abs(gf[..., 0] - rf[..., 0]) <= 2 * U32)
+    assert np.array_equal(gf[..., 1], (np.float32(1) * ge.astype(np.float32) / np.float32(Dq)).astype(np.float64))
+    err = np.abs(gf[..., 2:] - rf[..., 2:])[same].max() if same.any() else 0.0
+    print(f"{W}x{H} D={D}: {int(tie.sum())} near-tie quarter pixels of {tie.size}, "
+          f"{int((~same).sum())} winners differ, max |d feature| {err:.2e} (bound {2 * TOL_KBAR + 2 * U32:.2e})")
 
 
 def test_features_of_a_shift_by_four_k(fbs, oracle_mod):
@@ -221,8 +257,9 @@ def test_forward_layers_match_elementwise(fbs, oracle_mod, H, W, D):
         torch.cuda.synchronize()
         fbs.fbs_sync(ctx.ctx)
     (x0, ys, O), _ = br.split_trace(acts.cpu().numpy(), None, Hq, Wq)
-    feat, est = oracle_mod.band_features(L, R, D)
-    # the network input: the six features rounded to BF16, two zero channels
+    feat, est = _gpu_features(fbs, L, R, D)
+    # the network input: the six features (checked against the FP64 oracle in
+    # test_features_match_the_fp64_oracle) rounded to BF16, two zero channels
     assert np.array_equal(x0[..., :6], bn.round_bf16(feat)) and not x0[..., 6:].any()
     assert np.array_equal(O, out.cpu().numpy().astype(np.float64))
     th64 = theta.astype(np.float64)
@@ -279,7 +316,7 @@ def test_backward_layers_match_elementwise(fbs, oracle_mod):
         torch.cuda.synchronize()
         fbs.fbs_sync(ctx.ctx)
     (x0, ys, O), (gs, go) = br.split_trace(acts.cpu().numpy(), grads.cpu().numpy(), Hq, Wq)
-    feat, est = oracle_mod.band_features(L, R, D)
+    feat, est = _gpu_features(fbs, L, R, D)
     th64 = theta.astype(np.float64)
     layers = bn.unpack(th64)
     N = Hq * Wq
@@ -336,7 +373,7 @@ def test_training_steps_reduce_the_loss(fbs, oracle_mod):
     must cut the loss by more than half."""
     H, W, D = 160, 256, 128
     L, R = _rand_pair(21, H, W, 3, shift=24)
-    _, est = oracle_mod.band_features(L, R, D)
+    _, est = _gpu_features(fbs, L, R, D)
     li = (4 * bn.upsample(est, H, W) + 3).astype(np.int32)
     ls = (li + 0.25).astype(np.float32)
     with fbs.Context(0) as ctx:
@@ -411,7 +448,7 @@ def test_band_argument_validation(fbs):
 
 
 @pytest.mark.parametrize("H,W,D,shift,th", [(37, 45, 40, 9, 0.05), (64, 200, 128, 24, 0.1), (23, 61, 16, 3, 0.0)])
-def test_feature_points_bit_exact(fbs, oracle_mod, H, W, D, shift, th):
+def test_feature_points_match_the_oracle(fbs, oracle_mod, H, W, D, shift, th):
     L, R = _rand_pair(H + W + shift, H, W, 3, shift=shift)
     c = torch.empty((H, W), device="cuda")
     k = torch.empty((H, W), device="cuda")
@@ -419,6 +456,11 @@ def test_feature_points_bit_exact(fbs, oracle_mod, H, W, D, shift, th):
         fbs.fbs_band_feature_points(ctx.ctx, _dev(L), _dev(R), H, W, 3, D, th, c, k)
         torch.cuda.synchronize()
         fbs.fbs_sync(ctx.ctx)
-    rc, rk = oracle_mod.band_feature_points(L, R, D, th)
-    assert np.array_equal(k.cpu().numpy(), rk)
-    assert np.array_equal(c.cpu().numpy(), rc)
+    # exact wherever no margin in the pixel's window is within the FP32 bound of
+    # theta and no winner there is within it of a tie
+    rc, rk, amb = oracle_mod.band_feature_points(L, R, D, th, tol=2 * TOL_KBAR + 2 * U32)
+    ok = ~amb
+    print(f"{W}x{H} D={D} theta {th}: {int(amb.sum())} of {amb.size} pixels next to an undecided quarter pixel")
+    assert ok.mean() >= 0.9
+    assert np.array_equal(k.cpu().numpy()[ok], rk[ok])
+    assert np.array_equal(c.cpu().numpy()[ok], rc[ok])

@@ -31,13 +31,15 @@ def test_downsample_constant_and_clamped_edges(oracle_mod):
 def test_coarse_cost_matches_pearson_in_fp64(oracle_mod):
     """The coarse cost is 1 - corrcoef of the two clamped 3x3 blocks of quarter
     intensities (numpy's own formula), averaged over the 5x5 quarter window
-    clipped to the image: f2 at the winner matches it to FP32 accuracy, the
-    winner is its argmin except at near ties, and f3..f5 follow."""
+    clipped to the image: f2 at the winner matches it to FP64 accuracy, the
+    winner is its argmin (except at ties closer than the FP64 rounding of two
+    different formulas), f3..f5 follow, and the reported gap is the distance
+    from the best to the second best."""
     rng = np.random.default_rng(3)
     H, W, D = 24, 40, 24
     L = rng.integers(0, 256, size=(H, W, 3)).astype(np.uint8)
     R = rng.integers(0, 256, size=(H, W, 3)).astype(np.uint8)
-    feat, est = oracle_mod.band_features(L, R, D)
+    feat, est, gap = oracle_mod.band_features(L, R, D, with_gap=True)
     gl = oracle_mod.band_downsample(L).astype(np.float64)
     gr = oracle_mod.band_downsample(R).astype(np.float64)
     Hq, Wq, Dq = oracle_mod.quarter_shape(H, W, D)
@@ -54,18 +56,19 @@ def test_coarse_cost_matches_pearson_in_fp64(oracle_mod):
             win = K[max(0, Y - 2):Y + 3, max(0, X - 2):X + 3]
             Kb = win.reshape(-1, Dq).mean(axis=0)
             e = est[Y, X]
-            assert abs(feat[Y, X, 2] - Kb[e]) <= 1e-5
+            assert abs(feat[Y, X, 2] - Kb[e]) <= 1e-12
             srt = np.sort(Kb)
-            if srt[1] - srt[0] > 1e-4:
+            if srt[1] - srt[0] > 1e-12:
                 assert e == np.argmin(Kb)
-            assert feat[Y, X, 1] == np.float32(e) / np.float32(Dq)
+            assert abs(gap[Y, X] - (srt[1] - srt[0])) <= 1e-12
+            assert feat[Y, X, 1] == e / Dq
             k2 = min([Kb[j] for j in range(Dq) if abs(j - e) >= 2] + [2.0])
-            assert abs(feat[Y, X, 3] - min(k2 - Kb[e], 1.0)) <= 2e-5
+            assert abs(feat[Y, X, 3] - min(k2 - Kb[e], 1.0)) <= 1e-12
             km = Kb[e - 1] if e > 0 else 2.0
             kp = Kb[e + 1] if e < Dq - 1 else 2.0
-            assert abs(feat[Y, X, 4] - (km - Kb[e])) <= 2e-5
-            assert abs(feat[Y, X, 5] - (kp - Kb[e])) <= 2e-5
-            assert feat[Y, X, 0] == np.float32(gl[Y, X]) / np.float32(16 * 255 * 3) - np.float32(0.5)
+            assert abs(feat[Y, X, 4] - (km - Kb[e])) <= 1e-12
+            assert abs(feat[Y, X, 5] - (kp - Kb[e])) <= 1e-12
+            assert abs(feat[Y, X, 0] - (gl[Y, X] / (16 * 255 * 3) - 0.5)) <= 1e-15
 
 
 @pytest.mark.parametrize("k", [2, 5])
@@ -78,7 +81,7 @@ def test_coarse_winner_recovers_a_shift_by_four_k(oracle_mod, k):
     feat, est = oracle_mod.band_features(L, R, D)
     interior = est[3:-3, k + 3:-3]
     assert np.all(interior == k)
-    assert np.all(np.abs(feat[3:-3, k + 3:-3, 2]) <= 1e-6)
+    assert np.all(np.abs(feat[3:-3, k + 3:-3, 2]) <= 1e-12)
 
 
 # ---------------------------------------------------------------------------
@@ -273,19 +276,23 @@ def test_feature_point_proposal_definition(oracle_mod):
     H, W, D, th = 30, 45, 32, 0.05
     L = rng.integers(0, 256, size=(H, W, 3)).astype(np.uint8)
     R = np.roll(L, -8, axis=1)
-    feat, est = oracle_mod.band_features(L, R, D)
-    c, k = oracle_mod.band_feature_points(L, R, D, th)
+    feat, est, gap = oracle_mod.band_features(L, R, D, with_gap=True)
+    tol = 1e-3
+    c, k, amb = oracle_mod.band_feature_points(L, R, D, th, tol=tol)
+    assert np.array_equal(oracle_mod.band_feature_points(L, R, D, th), (c, k))
     Hq, Wq = est.shape
-    fp = feat[..., 3] >= np.float32(th)
+    fp = feat[..., 3] >= th
+    undecided = (np.abs(feat[..., 3] - th) <= tol) | (gap <= tol)
     for y in range(H):
         for x in range(W):
             Y, X = y // 4, x // 4
-            sel = fp[max(0, Y - 2):Y + 3, max(0, X - 2):X + 3]
-            e = est[max(0, Y - 2):Y + 3, max(0, X - 2):X + 3][sel]
+            win = (slice(max(0, Y - 2), Y + 3), slice(max(0, X - 2), X + 3))
+            e = est[win][fp[win]]
             if e.size >= 3 and e.max() - e.min() <= 2:
                 assert k[y, x] == 1.0 and c[y, x] == 2.0 * (e.max() + e.min())
             else:
                 assert k[y, x] == 0.0
+            assert amb[y, x] == undecided[win].any()
 
 
 def test_feature_points_on_a_shift_by_four_k(oracle_mod):
