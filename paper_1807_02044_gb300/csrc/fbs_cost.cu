@@ -24,9 +24,10 @@
 //     aggregation): for a row y and a block of 8 columns, the Dp x 8 block is
 //     contiguous, so the tensor-core kernel's TMA reads contiguous blocks that
 //     land as K-major core matrices; columns x >= W of the last block are 0.
-//     One launch computes the statistics of the rows it stages, the costs
-//     (8 pixels x 8 disparities per thread), the pad rows D .. Dp-1 and the
-//     left image's packed guide.
+//     One launch computes the statistics of the rows it stages (a CTA covers
+//     4 output rows and stages their 6 grey rows once), the costs (8 pixels x
+//     8 disparities per thread), the pad rows D .. Dp-1 and the left image's
+//     packed guide.
 // Both round the normalisation the same way (ncc_cost), so the 16-bit volume
 // equals the FP32 volume rounded to 16 bits.
 //
@@ -471,11 +472,18 @@ __host__ __device__ inline int xb_blocks_per_cta(int D)
 // both when lanes write their 8 rows and when the warp reads 32 consecutive rows).
 constexpr int kXbWarpRows = 256 + 32;
 
+// Output rows per CTA: the CTA stages grey rows y0-1 .. y0+kXbRows once for all
+// of them (kXbRows + 2 rows of each image instead of 3 per output row).
+constexpr int kXbRows = 4;
+
 __host__ __device__ inline size_t cost_xb_stage_ints(int mode, int D)
 {
     const int npx = 8 * xb_blocks_per_cta(D);
     const int Ll = skew_len(npx + 2), Lr = skew_len(npx + D + 9), Lp = skew_len(npx);
-    const size_t n = mode == 0 ? (size_t)(3 * Ll + 3 * Lr + 2 * Lp + 2 * Lr) : (size_t)(Lp + Lr);
+    // NCC: grey rows of both images, then per output row the left and right
+    // block statistics; TAD: per output row the packed pixels of both images
+    const size_t n = mode == 0 ? (size_t)((kXbRows + 2) * (Ll + Lr) + kXbRows * (2 * Lp + 2 * Lr))
+                               : (size_t)kXbRows * (Lp + Lr);
     return (n + 3) & ~(size_t)3;   // the output buffers that follow are 16-byte aligned
 }
 
@@ -494,7 +502,8 @@ cost_xb_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int
     const int xbc = xb_blocks_per_cta(D);
     const int nxb = (W + 7) >> 3;
     const int xb0 = blockIdx.x * xbc;
-    const int y = blockIdx.y;
+    const int y0 = blockIdx.y * kXbRows;
+    const int nrows = min(kXbRows, H - y0);
     const int x0 = xb0 * 8;
     const int npx = xbc * 8;
     const int nl = npx + 2;            // left grey columns x0-1 .. x0+npx
@@ -504,79 +513,86 @@ cost_xb_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int
     const int rb = x0 - D - 8;
     const int Ll = skew_len(nl), Lr = skew_len(nr), Lp = skew_len(npx);
 
-    int* gl = sm_xb;                   // [3][Ll]
-    int* gr = gl + 3 * Ll;             // [3][Lr]
-    int* sl = gr + 3 * Lr;             // [Lp]
-    float* rl = (float*)(sl + Lp);     // [Lp]
-    int* sr = (int*)(rl + Lp);         // [Lr]
-    float* rr = (float*)(sr + Lr);     // [Lr]
-    uint32_t* pl = (uint32_t*)sm_xb;   // TAD: left pixels [Lp]
-    uint32_t* pr = pl + Lp;            // TAD: right pixels [Lr], origin rb
+    int* gl = sm_xb;                             // [kXbRows + 2][Ll]: grey rows y0-1 ..
+    int* gr = gl + (kXbRows + 2) * Ll;           // [kXbRows + 2][Lr]
+    int* sl = gr + (kXbRows + 2) * Lr;           // [kXbRows][Lp]
+    float* rl = (float*)(sl + kXbRows * Lp);     // [kXbRows][Lp]
+    int* sr = (int*)(rl + kXbRows * Lp);         // [kXbRows][Lr]
+    float* rr = (float*)(sr + kXbRows * Lr);     // [kXbRows][Lr]
+    uint32_t* pl = (uint32_t*)sm_xb;             // TAD: left pixels [kXbRows][Lp]
+    uint32_t* pr = pl + kXbRows * Lp;            // TAD: right pixels [kXbRows][Lr], origin rb
 
-    // staging: grey values (channel sums) of rows y-1..y+1 at clamped columns,
-    // then each staged block centre's statistics S, 1/sqrt(9Q - S^2) exactly as
-    // grey_stats_kernel computes them, and the left pixels' packed guide
+    // staging: grey values (channel sums) of rows y0-1 .. y0+nrows at clamped
+    // columns, then for each output row the statistics S, 1/sqrt(9Q - S^2) of
+    // every staged block centre exactly as grey_stats_kernel computes them, and
+    // the left pixels' packed guide
     auto grey = [&](const uint8_t* img, int yy, int x) -> int {
         const uint8_t* q = img + ((size_t)yy * W + x) * C;
         return C == 3 ? (int)q[0] + (int)q[1] + (int)q[2] : (int)q[0];
     };
-    auto colour = [&](const uint8_t* img, int x) -> uint32_t {
-        const uint8_t* q = img + ((size_t)y * W + clampi(x, 0, W - 1)) * C;
+    auto colour = [&](const uint8_t* img, int yy, int x) -> uint32_t {
+        const uint8_t* q = img + ((size_t)yy * W + clampi(x, 0, W - 1)) * C;
         return C == 3 ? (uint32_t)q[0] | ((uint32_t)q[1] << 8) | ((uint32_t)q[2] << 16) : (uint32_t)q[0];
     };
     if (MODE == 0) {
         for (int c = tid; c < nl; c += nthr) {
             const int x = clampi(x0 - 1 + c, 0, W - 1);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) gl[j * Ll + skew(c)] = grey(L, clampi(y - 1 + j, 0, H - 1), x);
+            for (int j = 0; j < nrows + 2; ++j) gl[j * Ll + skew(c)] = grey(L, clampi(y0 - 1 + j, 0, H - 1), x);
         }
         for (int c = tid; c < nr; c += nthr) {
             const int x = clampi(rb + c, 0, W - 1);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) gr[j * Lr + skew(c)] = grey(R, clampi(y - 1 + j, 0, H - 1), x);
+            for (int j = 0; j < nrows + 2; ++j) gr[j * Lr + skew(c)] = grey(R, clampi(y0 - 1 + j, 0, H - 1), x);
         }
         __syncthreads();
-        auto stats = [&](const int* g, int Lg, int c, int* s_out, float* rv_out) {
+        for (int e = tid; e < nrows * npx; e += nthr) {
+            // left centre x0 + i of output row k sits at staged column i + 1 of rows k .. k+2
+            const int k = e / npx, i = e - k * npx;
+            const int* g = gl + k * Ll;
             int sum = 0, sq = 0;
 #pragma unroll
             for (int j = 0; j < 3; ++j)
 #pragma unroll
-                for (int k = -1; k <= 1; ++k) {
-                    const int v = g[j * Lg + skew(c + k)];
+                for (int m = 0; m < 3; ++m) {
+                    const int v = g[j * Ll + skew(i + m)];
                     sum += v;
                     sq += v * v;
                 }
             const int var = 9 * sq - sum * sum;
-            s_out[skew(c)] = sum;
-            rv_out[skew(c)] = var > 0 ? rsqrtf((float)var) : 0.f;
-        };
-        for (int i = tid; i < npx; i += nthr) {
-            // left centre x0 + i sits at staged column i + 1
-            int sum = 0, sq = 0;
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const int v = gl[j * Ll + skew(i + k)];
-                    sum += v;
-                    sq += v * v;
-                }
-            const int var = 9 * sq - sum * sum;
-            sl[skew(i)] = sum;
-            rl[skew(i)] = var > 0 ? rsqrtf((float)var) : 0.f;
+            sl[k * Lp + skew(i)] = sum;
+            rl[k * Lp + skew(i)] = var > 0 ? rsqrtf((float)var) : 0.f;
             if (x0 + i < W) {
-                const uint32_t col = colour(L, x0 + i);
-                rgbx[(size_t)y * rgbx_pitch(W) + x0 + i] = make_uint2(col, (uint32_t)__dp4a(col, col, 0u));
+                const uint32_t col = colour(L, y0 + k, x0 + i);
+                rgbx[(size_t)(y0 + k) * rgbx_pitch(W) + x0 + i] = make_uint2(col, (uint32_t)__dp4a(col, col, 0u));
             }
         }
-        for (int c = 1 + tid; c < nr - 1; c += nthr) stats(gr, Lr, c, sr, rr);
-    } else {
-        for (int c = tid; c < npx; c += nthr) {
-            const uint32_t col = colour(L, x0 + c);
-            pl[skew(c)] = col;
-            if (x0 + c < W) rgbx[(size_t)y * rgbx_pitch(W) + x0 + c] = make_uint2(col, (uint32_t)__dp4a(col, col, 0u));
+        for (int e = tid; e < nrows * (nr - 2); e += nthr) {
+            const int k = e / (nr - 2), c = 1 + e - k * (nr - 2);
+            const int* g = gr + k * Lr;
+            int sum = 0, sq = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int m = -1; m <= 1; ++m) {
+                    const int v = g[j * Lr + skew(c + m)];
+                    sum += v;
+                    sq += v * v;
+                }
+            const int var = 9 * sq - sum * sum;
+            sr[k * Lr + skew(c)] = sum;
+            rr[k * Lr + skew(c)] = var > 0 ? rsqrtf((float)var) : 0.f;
         }
-        for (int c = tid; c < nr; c += nthr) pr[skew(c)] = colour(R, rb + c);
+    } else {
+        for (int e = tid; e < nrows * npx; e += nthr) {
+            const int k = e / npx, c = e - k * npx;
+            const uint32_t col = colour(L, y0 + k, x0 + c);
+            pl[k * Lp + skew(c)] = col;
+            if (x0 + c < W)
+                rgbx[(size_t)(y0 + k) * rgbx_pitch(W) + x0 + c] = make_uint2(col, (uint32_t)__dp4a(col, col, 0u));
+        }
+        for (int e = tid; e < nrows * nr; e += nthr) {
+            const int k = e / nr, c = e - k * nr;
+            pr[k * Lr + skew(c)] = colour(R, y0 + k, rb + c);
+        }
     }
     __syncthreads();
 
@@ -593,147 +609,161 @@ cost_xb_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int
     uint4* wbuf = (uint4*)(sm_xb + cost_xb_stage_ints(MODE, D)) + (size_t)(tid >> 5) * kXbWarpRows;
     uint4* mine = wbuf + 9 * lane;     // rows 8*lane + s at 9*lane + s
 
-    if (!active) {
-    } else if (MODE == 0) {
-        int glw[3][10], grw[3][10], sli[8], srw[8];
-        float rli[8], rrw[8];
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int c = 0; c < 10; ++c) glw[j][c] = gl[j * Ll + skew(xl + c)];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            sli[i] = sl[skew(xl + i)];
-            rli[i] = rl[skew(xl + i)];
-        }
-        // right block of (x, d) spans columns x-d-1 .. x-d+1: index (x - d - 1 + k) - rb
-        int base = xl - d0 - 1 + D + 8;
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int c = 0; c < 10; ++c) grw[j][c] = gr[j * Lr + skew(base + c)];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            srw[i] = sr[skew(base + 1 + i)];
-            rrw[i] = rr[skew(base + 1 + i)];
-        }
-        // the normalisation of a pixel pair is one packed multiply and one packed
-        // FMA (per lane exactly ncc_cost); threads whose 8 pixels are inside the
-        // image and match inside it for all 8 disparities skip the two masks
-        const uint64_t ones2 = f2_pack(1.f, 1.f);
-        auto sweep = [&](auto masked) {
-#pragma unroll
+    for (int k = 0; k < nrows; ++k) {
+        const int y = y0 + k;
+        // this output row's staged rows (grey rows k .. k+2 are y-1 .. y+1) and statistics
+        const int* glk = gl + k * Ll;
+        const int* grk = gr + k * Lr;
+        const int* slk = sl + k * Lp;
+        const float* rlk = rl + k * Lp;
+        const int* srk = sr + k * Lr;
+        const float* rrk = rr + k * Lr;
+        const uint32_t* plk = pl + k * Lp;
+        const uint32_t* prk = pr + k * Lr;
+        (void)glk, (void)grk, (void)slk, (void)rlk, (void)srk, (void)rrk, (void)plk, (void)prk;
+        if (!active) {
+        } else if (MODE == 0) {
+            int glw[3][10], grw[3][10], sli[8], srw[8];
+            float rli[8], rrw[8];
+    #pragma unroll
+            for (int j = 0; j < 3; ++j)
+    #pragma unroll
+                for (int c = 0; c < 10; ++c) glw[j][c] = glk[j * Ll + skew(xl + c)];
+    #pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                sli[i] = slk[skew(xl + i)];
+                rli[i] = rlk[skew(xl + i)];
+            }
+            // right block of (x, d) spans columns x-d-1 .. x-d+1: index (x - d - 1 + k) - rb
+            int base = xl - d0 - 1 + D + 8;
+    #pragma unroll
+            for (int j = 0; j < 3; ++j)
+    #pragma unroll
+                for (int c = 0; c < 10; ++c) grw[j][c] = grk[j * Lr + skew(base + c)];
+    #pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                srw[i] = srk[skew(base + 1 + i)];
+                rrw[i] = rrk[skew(base + 1 + i)];
+            }
+            // the normalisation of a pixel pair is one packed multiply and one packed
+            // FMA (per lane exactly ncc_cost); threads whose 8 pixels are inside the
+            // image and match inside it for all 8 disparities skip the two masks
+            const uint64_t ones2 = f2_pack(1.f, 1.f);
+            auto sweep = [&](auto masked) {
+    #pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    const int d = d0 + s;
+                    if (s > 0) {
+                        // d grew by one: the window slides one column to the left
+                        --base;
+    #pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+    #pragma unroll
+                            for (int c = 9; c > 0; --c) grw[j][c] = grw[j][c - 1];
+                            grw[j][0] = grk[j * Lr + skew(base)];
+                        }
+    #pragma unroll
+                        for (int i = 7; i > 0; --i) {
+                            srw[i] = srw[i - 1];
+                            rrw[i] = rrw[i - 1];
+                        }
+                        srw[0] = srk[skew(base + 1)];
+                        rrw[0] = rrk[skew(base + 1)];
+                    }
+                    int cp[10];
+    #pragma unroll
+                    for (int c = 0; c < 10; ++c)
+                        cp[c] = glw[0][c] * grw[0][c] + glw[1][c] * grw[1][c] + glw[2][c] * grw[2][c];
+                    int P = cp[0] + cp[1] + cp[2];
+                    int num[8];
+    #pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        if (i > 0) P += cp[i + 2] - cp[i - 1];
+                        num[i] = 9 * P - sli[i] * srw[i];
+                    }
+                    uint32_t w[4];
+    #pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint64_t t = f2_mul(f2_pack(rli[2 * q], rli[2 * q + 1]), f2_pack(rrw[2 * q], rrw[2 * q + 1]));
+                        const uint64_t nn = f2_pack(-__int2float_rn(num[2 * q]), -__int2float_rn(num[2 * q + 1]));
+                        float c0, c1;
+                        f2_unpack(f2_fma(nn, t, ones2), c0, c1);
+                        if (decltype(masked)::value) {
+                            const int x = xbase + 2 * q;
+                            c0 = x - d < 0 ? 2.f : c0;
+                            c1 = x + 1 - d < 0 ? 2.f : c1;
+                            c0 = x < W ? c0 : 0.f;
+                            c1 = x + 1 < W ? c1 : 0.f;
+                        }
+                        w[q] = pack_16x2<kBf16>(c0, c1);
+                    }
+                    mine[s] = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            };
+            if (xbase + 7 < W && xbase >= d0 + 7)
+                sweep(std::integral_constant<bool, false>{});
+            else
+                sweep(std::integral_constant<bool, true>{});
+        } else {
+            const float inv_c = 1.f / (float)C;
+            uint32_t pli[8], prw[8];
+    #pragma unroll
+            for (int i = 0; i < 8; ++i) pli[i] = plk[skew(xl + i)];
+            // right pixel of (x, d): index (x - d) - rb
+            int base = xl - d0 + D + 8;
+    #pragma unroll
+            for (int i = 0; i < 8; ++i) prw[i] = prk[skew(base + i)];
+    #pragma unroll
             for (int s = 0; s < 8; ++s) {
                 const int d = d0 + s;
                 if (s > 0) {
-                    // d grew by one: the window slides one column to the left
                     --base;
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-#pragma unroll
-                        for (int c = 9; c > 0; --c) grw[j][c] = grw[j][c - 1];
-                        grw[j][0] = gr[j * Lr + skew(base)];
-                    }
-#pragma unroll
-                    for (int i = 7; i > 0; --i) {
-                        srw[i] = srw[i - 1];
-                        rrw[i] = rrw[i - 1];
-                    }
-                    srw[0] = sr[skew(base + 1)];
-                    rrw[0] = rr[skew(base + 1)];
+    #pragma unroll
+                    for (int i = 7; i > 0; --i) prw[i] = prw[i - 1];
+                    prw[0] = prk[skew(base)];
                 }
-                int cp[10];
-#pragma unroll
-                for (int c = 0; c < 10; ++c)
-                    cp[c] = glw[0][c] * grw[0][c] + glw[1][c] * grw[1][c] + glw[2][c] * grw[2][c];
-                int P = cp[0] + cp[1] + cp[2];
-                int num[8];
-#pragma unroll
+                T v[8];
+    #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    if (i > 0) P += cp[i + 2] - cp[i - 1];
-                    num[i] = 9 * P - sli[i] * srw[i];
+                    const int x = xbase + i;
+                    const int sad = (int)__dp4a(__vabsdiffu4(pli[i], prw[i]), 0x01010101u, 0u);
+                    const float cst = x - d < 0 ? tau : fminf((float)sad * inv_c, tau);
+                    v[i] = to_out<T>(x < W ? cst : 0.f);
                 }
-                uint32_t w[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint64_t t = f2_mul(f2_pack(rli[2 * q], rli[2 * q + 1]), f2_pack(rrw[2 * q], rrw[2 * q + 1]));
-                    const uint64_t nn = f2_pack(-__int2float_rn(num[2 * q]), -__int2float_rn(num[2 * q + 1]));
-                    float c0, c1;
-                    f2_unpack(f2_fma(nn, t, ones2), c0, c1);
-                    if (decltype(masked)::value) {
-                        const int x = xbase + 2 * q;
-                        c0 = x - d < 0 ? 2.f : c0;
-                        c1 = x + 1 - d < 0 ? 2.f : c1;
-                        c0 = x < W ? c0 : 0.f;
-                        c1 = x + 1 < W ? c1 : 0.f;
-                    }
-                    w[q] = pack_16x2<kBf16>(c0, c1);
-                }
-                mine[s] = make_uint4(w[0], w[1], w[2], w[3]);
+                mine[s] = pack8(v);
             }
-        };
-        if (xbase + 7 < W && xbase >= d0 + 7)
-            sweep(std::integral_constant<bool, false>{});
-        else
-            sweep(std::integral_constant<bool, true>{});
-    } else {
-        const float inv_c = 1.f / (float)C;
-        uint32_t pli[8], prw[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) pli[i] = pl[skew(xl + i)];
-        // right pixel of (x, d): index (x - d) - rb
-        int base = xl - d0 + D + 8;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) prw[i] = pr[skew(base + i)];
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const int d = d0 + s;
-            if (s > 0) {
-                --base;
-#pragma unroll
-                for (int i = 7; i > 0; --i) prw[i] = prw[i - 1];
-                prw[0] = pr[skew(base)];
+        }
+        // write-out: entry e = 32k + lane is row s = e % 8 of lane e / 8 (its block
+        // xbl and group dg come by shuffle); rows d >= D and inactive lanes are skipped
+        __syncwarp();
+        const int Dp = tc_block_rows(D);
+        const int code = active ? (xbl << 8) | dg : -1;
+    #pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int e = 32 * k + lane;
+            const int src = __shfl_sync(0xffffffffu, code, e >> 3);
+            const int s = e & 7;
+            if (src >= 0 && 8 * (src & 255) + s < D) {
+                const int xbs = xb0 + (src >> 8);
+                const uint4 row = wbuf[e + (e >> 3)];
+                *(uint4*)(out + (((size_t)y * nxb + xbs) * Dp + 8 * (src & 255) + s) * 8) = row;
             }
-            T v[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int x = xbase + i;
-                const int sad = (int)__dp4a(__vabsdiffu4(pli[i], prw[i]), 0x01010101u, 0u);
-                const float cst = x - d < 0 ? tau : fminf((float)sad * inv_c, tau);
-                v[i] = to_out<T>(x < W ? cst : 0.f);
+        }
+        // rows D .. Dp-1 of the CTA's blocks: zero, except row round_up(D,16) all
+        // ones when the normaliser rides with the volume
+        const int extra = Dp - D;
+        if (extra > 0) {
+            const int n16 = (D + 15) / 16 * 16;
+            const T one1[2] = {to_out<T>(1.f), to_out<T>(1.f)};
+            const uint32_t ones = *reinterpret_cast<const uint32_t*>(one1);
+            const int nb = min(xbc, nxb - xb0);
+            for (int i = tid; i < nb * extra; i += nthr) {
+                const int b = i / extra, d = D + (i - b * extra);
+                const uint32_t v = (d == n16 && Dp > n16) ? ones : 0u;
+                *(uint4*)(out + (((size_t)y * nxb + xb0 + b) * Dp + d) * 8) = make_uint4(v, v, v, v);
             }
-            mine[s] = pack8(v);
         }
-    }
-    // write-out: entry e = 32k + lane is row s = e % 8 of lane e / 8 (its block
-    // xbl and group dg come by shuffle); rows d >= D and inactive lanes are skipped
-    __syncwarp();
-    const int Dp = tc_block_rows(D);
-    const int code = active ? (xbl << 8) | dg : -1;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int e = 32 * k + lane;
-        const int src = __shfl_sync(0xffffffffu, code, e >> 3);
-        const int s = e & 7;
-        if (src >= 0 && 8 * (src & 255) + s < D) {
-            const int xbs = xb0 + (src >> 8);
-            const uint4 row = wbuf[e + (e >> 3)];
-            *(uint4*)(out + (((size_t)y * nxb + xbs) * Dp + 8 * (src & 255) + s) * 8) = row;
-        }
-    }
-    // rows D .. Dp-1 of the CTA's blocks: zero, except row round_up(D,16) all
-    // ones when the normaliser rides with the volume
-    const int extra = Dp - D;
-    if (extra > 0) {
-        const int n16 = (D + 15) / 16 * 16;
-        const T one1[2] = {to_out<T>(1.f), to_out<T>(1.f)};
-        const uint32_t ones = *reinterpret_cast<const uint32_t*>(one1);
-        const int nb = min(xbc, nxb - xb0);
-        for (int i = tid; i < nb * extra; i += nthr) {
-            const int b = i / extra, d = D + (i - b * extra);
-            const uint32_t v = (d == n16 && Dp > n16) ? ones : 0u;
-            *(uint4*)(out + (((size_t)y * nxb + xb0 + b) * Dp + d) * 8) = make_uint4(v, v, v, v);
-        }
+        __syncwarp();   // the warp's buffer is read out before the next row's sweep refills it
     }
 }
 
@@ -753,7 +783,7 @@ cudaError_t launch_cost_xb(const CostScratch& sc, const uint8_t* left, const uin
     cudaError_t e = fbs::raise_smem_limit(cost_xb_kernel<MODE, T>, (int)smem);
     if (e != cudaSuccess) return e;
     const int nxb = (W + 7) / 8;
-    dim3 grid((nxb + xbc - 1) / xbc, H);
+    dim3 grid((nxb + xbc - 1) / xbc, (H + kXbRows - 1) / kXbRows);
     fbs::note_launch();
     const int nthr = (xbc * ndg + 31) / 32 * 32;   // whole warps (the write-out shuffles need all lanes)
     cost_xb_kernel<MODE, T><<<grid, nthr, smem, stream>>>(left, right, H, W, C, D, tau, out, sc.rgbx);
