@@ -37,6 +37,9 @@ constexpr int kTY = kAggTileY;   // tile height (rows)
 constexpr int kPX = 4;         // pixels per thread along x
 constexpr int kThreads = 256;  // 8 warps
 constexpr int kNPix = kTX * kTY;
+// 2^23 as an FP32 bit pattern: for 0 <= c < 2^23 the pattern kMagic + c is the
+// float 2^23 + c exactly.
+constexpr uint32_t kMagic = 0x4B000000u;
 
 __host__ __device__ inline int weight_stride(int rho)
 {
@@ -69,7 +72,7 @@ __host__ __device__ inline size_t smem_bytes(int rho)
     const size_t ring = (size_t)3 * NC * DC;
     const size_t stage = (size_t)kNPix * (DC + 1);
     const size_t a = ring > stage ? ring : stage;
-    return sizeof(float) * (a + 2 * (size_t)kTY * weight_stride(rho) + 2 * kNPix) + sizeof(float4) * 3 * NC;
+    return sizeof(float) * (a + 2 * (size_t)kTY * weight_stride(rho) + 2 * kNPix) + sizeof(uint2) * 3 * NC;
 }
 
 // Load cost row r, columns x0-rho .. x0-rho+NC-1, disparities dc0 .. dc0+DC-1;
@@ -103,22 +106,28 @@ __device__ __forceinline__ void load_cost_row(float* dst, const float* __restric
     }
 }
 
-__device__ __forceinline__ void load_guide_row(float4* dst, const uint8_t* __restrict__ guide, int W,
-                                               int C, int r, int x0, int rho, int NC)
+// A guide pixel as (R | G << 8 | B << 16, R^2 + G^2 + B^2); grey images use
+// the first channel only.
+__device__ __forceinline__ uint2 packed_colour(const uint8_t* p, int C)
+{
+    const uint32_t c = C == 3 ? (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) : (uint32_t)p[0];
+    return make_uint2(c, (uint32_t)__dp4a(c, c, 0u));
+}
+
+__device__ __forceinline__ void load_guide_row(uint2* dst, const uint8_t* __restrict__ guide, int W, int C, int r,
+                                               int x0, int rho, int NC)
 {
     for (int col = threadIdx.x; col < NC; col += kThreads) {
         const int gx = x0 - rho + col;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (gx >= 0 && gx < W) {
-            const uint8_t* p = guide + ((size_t)r * W + gx) * C;
-            v.x = (float)p[0];
-            if (C == 3) {
-                v.y = (float)p[1];
-                v.z = (float)p[2];
-            }
-        }
-        dst[col] = v;
+        dst[col] = (gx >= 0 && gx < W) ? packed_colour(guide + ((size_t)r * W + gx) * C, C) : make_uint2(0u, 0u);
     }
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // One 32 x 4 tile with top-left pixel (x0, y0), disparities [d_begin, d_end)
@@ -144,9 +153,10 @@ __device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, i
     const int NT = 2 * rho + 1;
     const int WS = weight_stride(rho);
 
-    // shared memory: guide ring [3][NC] float4 | cost ring [3][NC][DC] (aliased
-    // by the stage [kNPix][DC+1]) | weights [2][kTY][WS] | den [2][kNPix]
-    float4* const gring = smem_f4;
+    // shared memory: guide ring [3][NC] uint2 | cost ring [3][NC][DC] (aliased
+    // by the stage [kNPix][DC+1]) | weights [2][kTY][WS] | den [2][kNPix].  NC
+    // is even, so the cost ring starts 16-byte aligned.
+    uint2* const gring = (uint2*)smem_f4;
     float* const cring = (float*)(gring + 3 * NC);
     float* const stage = cring;
     const int cslot = NC * DC;
@@ -163,14 +173,13 @@ __device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, i
     const bool pvalid = py < H && pxg < W;
     const int dx_lo = half ? rho + 1 : 0;
     const int dx_hi = half ? NT : rho + 1;
-    float3 pc = make_float3(0.f, 0.f, 0.f);
+    // the pixel's colour and |p|^2 + 2^23 (so |q - p|^2 = |q|^2 + |p|^2 - 2 q.p,
+    // exact in integers and below 2^23, becomes the bit pattern of 2^23 + c)
+    uint32_t pcol = 0u, pnorm = kMagic;
     if (pvalid) {
-        const uint8_t* p = guide + ((size_t)py * W + pxg) * C;
-        pc.x = (float)p[0];
-        if (C == 3) {
-            pc.y = (float)p[1];
-            pc.z = (float)p[2];
-        }
+        const uint2 c = packed_colour(guide + ((size_t)py * W + pxg) * C, C);
+        pcol = c.x;
+        pnorm = c.y + kMagic;
     }
 
     // WTA role (tid < kNPix): state of pixel tid carried across chunks
@@ -235,19 +244,21 @@ __device__ __forceinline__ void aggregate_tile(const float* __restrict__ cost, i
             {
                 const int dy = r - py;
                 if (p_on && py < H && dy >= -rho && dy <= rho) {
-                    const float4* gr = gring + (s % 3) * NC;
+                    const uint2* gr = gring + (s % 3) * NC;
                     float* wrow = wring + (s & 1) * wslot + pyi * WS;
                     const int dy2 = dy * dy;
                     for (int dx = dx_lo; dx < dx_hi; ++dx) {
                         const int qx = pxg + dx - rho;
                         float w = 0.f;
                         if (pxg < W && qx >= 0 && qx < W) {
-                            const float4 q = gr[ppx + dx];
-                            const float e0 = q.x - pc.x, e1 = q.y - pc.y, e2 = q.z - pc.z;
-                            const float col2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+                            // Eq. (7)-(8) as one exp2: colour distance exact in
+                            // integers, then float(c) = (2^23 + c) - 2^23 exactly
+                            const uint2 q = gr[ppx + dx];
+                            const float col2 =
+                                __uint_as_float(q.y + pnorm - 2u * (uint32_t)__dp4a(q.x, pcol, 0u)) - 8388608.f;
                             const int ddx = dx - rho;
                             const float sp2 = (float)(ddx * ddx + dy2);
-                            w = exp2f(fmaf(col2, neg_kr, sp2 * neg_ks));
+                            w = ex2_approx(fmaf(col2, neg_kr, sp2 * neg_ks));
                         }
                         wrow[dx * kTX + ppx] = w;
                         den_part += w;
