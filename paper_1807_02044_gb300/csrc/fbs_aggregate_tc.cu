@@ -455,11 +455,19 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                     uint64_t ad = a_desc0 + ((s * a_stage) >> 4), bd = b_desc0 + ((s * b_stage) >> 4);
                     const int nk = nr * (KW / 16);
                     if (!ones_sep) {
-                        for (int k = 0; k < nk; ++k) {
-                            umma_f16(dacc, ad, bd, p.idesc, accumulate);
-                            accumulate = 1;
-                            ad += (2 * kALbo) >> 4;
-                            bd += (2 * lbo_b) >> 4;
+                        // the issuing thread shares its scheduler with five busy
+                        // warps: few instructions per MMA (the 14-bit address
+                        // fields never carry into the descriptors' high words)
+                        const uint64_t ahi = ad & 0xffffffff00000000ull, bhi = bd & 0xffffffff00000000ull;
+                        uint32_t alo = (uint32_t)ad, blo = (uint32_t)bd;
+                        const uint32_t astep = (2 * kALbo) >> 4, bstep = (2 * lbo_b) >> 4;
+                        umma_f16(dacc, ahi | alo, bhi | blo, p.idesc, accumulate);
+                        accumulate = 1;
+#pragma unroll 4
+                        for (int k = 1; k < nk; ++k) {
+                            alo += astep;
+                            blo += bstep;
+                            umma_f16(dacc, ahi | alo, bhi | blo, p.idesc, 1u);
                         }
                     } else {
                         for (int k = 0; k < nk; ++k) {

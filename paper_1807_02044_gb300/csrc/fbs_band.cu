@@ -550,7 +550,7 @@ fbs_status run_backward(fbs_ctx* ctx, const NetScratch& s, int H, int W, int D, 
         const __nv_bfloat16* X = l == 0 ? s.x0 : s.y[l - 1];
         {
             LaunchScope ls(ctx, FBS_KERNEL_NET, st);
-            e = launch_wgrad(l, X, s.g[l], Hq, Wq, s.partial, b->grad, st);
+            e = launch_wgrad(l, X, s.g[l], Hq, Wq, s.partial, b->grad, ctx->derr, ctx->num_sms, st);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "band weight-gradient launch");
         if (l == 0) break;

@@ -1,6 +1,6 @@
-// Kernels of the band-proposal network: 3x3 convolutions on the tensor cores
-// (forward and data gradient), weight gradients, loss, Adam and the packing
-// of FP32 master weights into BF16 MMA operands.
+// Kernels of the band-proposal network: 3x3 convolutions and weight gradients
+// on the tensor cores (forward, data gradient, weight gradient), loss, Adam and
+// the packing of FP32 master weights into BF16 MMA operands.
 //
 // Convolution as an implicit GEMM (one CTA = 128 consecutive quarter pixels
 // = the MMA's M; persistent over tiles):
@@ -193,63 +193,170 @@ cudaError_t launch_conv_t(const __nv_bfloat16* in, const __nv_bfloat16* image, c
     return cudaGetLastError();
 }
 
-// ---- weight gradients (FP32 on the CUDA cores) --------------------------------
-// One CTA = a 16 x 8 tile of quarter pixels; thread (tap, ci) accumulates the
-// COUT sums over the tile's pixels of X[p + offset(tap)][ci] * G[p][co] and
-// writes them, plus the bias sums, as the CTA's partial; a second kernel adds
-// the partials of all CTAs in a fixed order (deterministic).
-constexpr int kGTX = 16, kGTY = 8, kGPix = kGTX * kGTY;
+// ---- weight gradients on the tensor cores ---------------------------------------
+// dW[(t, ci)][co] = sum_p X[p + off(t)][ci] G[p][co] and the bias gradient
+// sum_p G[p][co] as one product D[M][N] += A[M][K] B[N][K] with K = pixels: A
+// row t * CIN + ci holds X[p + off(t)][ci] over the pixels p of a chunk (zero
+// where p + off(t) leaves the image), row 9 CIN is all ones (its result is the
+// bias gradient) and the rest zero; B row co holds G[p][co].  X and G are
+// pixel-major in memory, so a warp loads an 8-pixel x 8-channel block (4 bytes
+// per lane), transposes it in registers (movmatrix) and stores it as one
+// K-major core matrix -- the operand layout of the convolutions above.  A CTA
+// accumulates its chunks in TMEM (M-tiles of 128 rows) and writes one
+// partial; wgrad_reduce_kernel adds the partials in a fixed order.
+constexpr int kWgChunk = 128;        // pixels (K) per chunk
+constexpr int kWgThreads = 256;
+
+__device__ __forceinline__ uint32_t movmatrix_trans(uint32_t a)
+{
+    uint32_t d;
+    asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;" : "=r"(d) : "r"(a));
+    return d;
+}
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(9 * 32)
-wgrad_kernel(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ G, int Hq, int Wq,
-             float* __restrict__ partial)
+struct WgShape {
+    static constexpr int MR = 9 * CIN + 1;                 // rows in use: taps x channels, ones
+    static constexpr int MT = (MR + kM - 1) / kM;          // M-tiles of 128 rows
+    static constexpr int N = COUT < 16 ? 16 : COUT;        // MMA N (a multiple of 16 for M = 128)
+    static constexpr int KB = kWgChunk / 8;                // core matrices along K per chunk
+    static constexpr uint32_t LBO_A = MT * kM * 16, LBO_B = N * 16;
+    static constexpr int A_BYTES = KB * LBO_A, B_BYTES = KB * LBO_B;
+    static constexpr uint32_t TMEM_COLS = MT * N <= 32 ? 32 : MT * N <= 64 ? 64 : MT * N <= 128 ? 128 : 256;
+    static constexpr size_t SMEM = (size_t)A_BYTES + B_BYTES + 16;
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kWgThreads)
+wgrad_tc_kernel(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ G, int Hq, int Wq,
+                float* __restrict__ partial, int* __restrict__ err)
 {
-    constexpr int HX = kGTX + 2, HY = kGTY + 2;
-    constexpr int STRIDE = 9 * CIN * COUT + COUT;
-    __shared__ float Xs[HY * HX * CIN];
-    __shared__ __align__(16) float Gs[kGPix * COUT];
-    const int x0 = blockIdx.x * kGTX, y0 = blockIdx.y * kGTY;
-    const int nthr = 9 * CIN;
-    for (int i = threadIdx.x; i < HY * HX * CIN; i += nthr) {
-        const int c = i % CIN, q = i / CIN;
-        const int yy = y0 - 1 + q / HX, xx = x0 - 1 + q % HX;
-        Xs[i] = (yy >= 0 && yy < Hq && xx >= 0 && xx < Wq) ? __bfloat162float(X[((size_t)yy * Wq + xx) * CIN + c]) : 0.f;
+    using S = WgShape<CIN, COUT>;
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t* As = sm;
+    uint8_t* Bs = sm + S::A_BYTES;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + S::B_BYTES);
+    uint32_t* misc = reinterpret_cast<uint32_t*>(bar + 1);   // [0] TMEM address, [1] abort flag
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int P = Hq * Wq;
+    const int nchunks = (P + kWgChunk - 1) / kWgChunk;
+
+    // rows 9 CIN .. of A (the ones row, then zeros) and rows COUT .. of B never
+    // change: one 16-byte core-matrix row per store
+    constexpr int ROWS_FIXED = S::MT * kM - 9 * CIN;
+    const uint4 ones = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+    for (int i = tid; i < S::KB * ROWS_FIXED; i += kWgThreads) {
+        const int kb = i / ROWS_FIXED, r = 9 * CIN + i - kb * ROWS_FIXED;
+        *reinterpret_cast<uint4*>(As + kb * S::LBO_A + r * 16) = r == 9 * CIN ? ones : make_uint4(0u, 0u, 0u, 0u);
     }
-    for (int i = threadIdx.x; i < kGPix * COUT; i += nthr) {
-        const int c = i % COUT, q = i / COUT;
-        const int yy = y0 + q / kGTX, xx = x0 + q % kGTX;
-        Gs[i] = (yy < Hq && xx < Wq) ? __bfloat162float(G[((size_t)yy * Wq + xx) * COUT + c]) : 0.f;
+    if constexpr (S::N > COUT) {
+        for (int i = tid; i < S::KB * (S::N - COUT); i += kWgThreads) {
+            const int kb = i / (S::N - COUT), r = COUT + i - kb * (S::N - COUT);
+            *reinterpret_cast<uint4*>(Bs + kb * S::LBO_B + r * 16) = make_uint4(0u, 0u, 0u, 0u);
+        }
     }
+    if (tid == 0) {
+        mbar_init(smem_u32(bar), 1);
+        misc[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(smem_u32(&misc[0]), S::TMEM_COLS);
+    fence_proxy_async();
+    tc_fence_before();
     __syncthreads();
-    float* part = partial + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * STRIDE;
-    if (threadIdx.x < nthr) {
-        const int t = threadIdx.x / CIN, ci = threadIdx.x % CIN;
-        const int dy = t / 3, dx = t % 3;   // halo coordinates of the tap
-        float acc[COUT];
+    tc_fence_after();
+    const uint32_t tmem = misc[0];
+    const uint32_t idesc = idesc_f16(true, kM, S::N);
+    const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+    // lane -> (pixel of the 8-pixel group, channel pair of the 8-channel group),
+    // the movmatrix fragment of the [pixel][channel] block; after the
+    // transpose the lane holds channel lane/4 for pixels 2 (lane%4), + 1
+    const int lp = lane >> 2, lc = 2 * (lane & 3);
+
+    uint32_t phase = 0;
+    bool first = true, aborted = false;
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int p0 = c * kWgChunk;
+        // a warp fills the K columns of one 8-pixel group at a time: each lane
+        // locates its pixel once, then loads every tap and channel group
+        constexpr int CG = CIN / 8;
+        for (int pg = warp; pg < S::KB; pg += kWgThreads / 32) {
+            const int p = p0 + pg * 8 + lp;
+            const bool pin = p < P;
+            const int Y = pin ? p / Wq : 0, Xp = pin ? p - Y * Wq : 0;
+            uint8_t* arow = As + pg * S::LBO_A + lp * 16 + 2 * lc;
 #pragma unroll
-        for (int c = 0; c < COUT; ++c) acc[c] = 0.f;
-#pragma unroll 2
-        for (int q = 0; q < kGPix; ++q) {
-            const float x = Xs[((q / kGTX + dy) * HX + q % kGTX + dx) * CIN + ci];
-            const float4* g = reinterpret_cast<const float4*>(Gs + q * COUT);
+            for (int t = 0; t < 9; ++t) {
+                const int yy = Y + t / 3 - 1, xx = Xp + t % 3 - 1;
+                const bool ok = pin && yy >= 0 && yy < Hq && xx >= 0 && xx < Wq;
+                const __nv_bfloat16* src = X + (size_t)(ok ? yy * Wq + xx : 0) * CIN + lc;
+                uint32_t v[CG];
 #pragma unroll
-            for (int c = 0; c < COUT / 4; ++c) {
-                const float4 gv = g[c];
-                acc[4 * c] = fmaf(x, gv.x, acc[4 * c]);
-                acc[4 * c + 1] = fmaf(x, gv.y, acc[4 * c + 1]);
-                acc[4 * c + 2] = fmaf(x, gv.z, acc[4 * c + 2]);
-                acc[4 * c + 3] = fmaf(x, gv.w, acc[4 * c + 3]);
+                for (int cg = 0; cg < CG; ++cg) v[cg] = ok ? *reinterpret_cast<const uint32_t*>(src + cg * 8) : 0u;
+#pragma unroll
+                for (int cg = 0; cg < CG; ++cg)
+                    *reinterpret_cast<uint32_t*>(arow + (t * CIN + cg * 8) * 16) = movmatrix_trans(v[cg]);
+            }
+            uint8_t* brow = Bs + pg * S::LBO_B + lp * 16 + 2 * lc;
+#pragma unroll
+            for (int cg = 0; cg < COUT / 8; ++cg) {
+                const uint32_t v = pin ? *reinterpret_cast<const uint32_t*>(G + (size_t)p * COUT + cg * 8 + lc) : 0u;
+                *reinterpret_cast<uint32_t*>(brow + cg * 8 * 16) = movmatrix_trans(v);
             }
         }
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll 1
+            for (int m = 0; m < S::MT; ++m)
+#pragma unroll 1
+                for (int ks = 0; ks < S::KB / 2; ++ks) {
+                    const uint64_t ad = sdesc(a0 + m * kM * 16 + ks * 2 * S::LBO_A, S::LBO_A, 128);
+                    const uint64_t bd = sdesc(b0 + ks * 2 * S::LBO_B, S::LBO_B, 128);
+                    umma_f16(tmem + (uint32_t)(m * S::N), ad, bd, idesc, (first && ks == 0) ? 0u : 1u);
+                }
+            umma_commit(smem_u32(bar));
+        }
+        const bool ok = mbar_wait(smem_u32(bar), phase);
+        phase ^= 1u;
+        if (!ok) atomicExch(&misc[1], 1u);
+        tc_fence_before();
+        __syncthreads();   // A and B are free for the next chunk
+        if (misc[1] != 0) {
+            if (tid == 0) {
+                atomicCAS(err, 0, 22);
+                mbar_wait(smem_u32(bar), phase ^ 1u);   // once more, bounded, for the MMAs in flight
+            }
+            aborted = true;
+            break;
+        }
+        first = false;
+    }
+    if (!aborted && !first) {
+        // warp w reads TMEM lanes 32w .. 32w+31 of every M-tile: A rows m*128 + 32w + lane
+        tc_fence_after();
+        float* part = partial + (size_t)blockIdx.x * (9 * CIN * COUT + COUT);
+#pragma unroll 1
+        for (int m = 0; m < S::MT; ++m) {
+            const int r = m * kM + 32 * warp + lane;
 #pragma unroll
-        for (int c = 0; c < COUT; ++c) part[(t * CIN + ci) * COUT + c] = acc[c];
+            for (int cb = 0; cb < S::N; cb += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(m * S::N + cb), v);
+                if (r < S::MR) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (cb + i < COUT) part[r * COUT + cb + i] = v[i];
+                }
+            }
+        }
     }
-    if (threadIdx.x < COUT) {
-        float s = 0.f;
-        for (int q = 0; q < kGPix; ++q) s += Gs[q * COUT + threadIdx.x];
-        part[9 * CIN * COUT + threadIdx.x] = s;
-    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
 // grad[layer l] = sum over the nblk partials, dropping padded channels.
@@ -400,30 +507,42 @@ cudaError_t launch_conv3x3(int cin_ch, int n, const __nv_bfloat16* in, const __n
 
 size_t wgrad_partial_floats(int Hq, int Wq)
 {
-    const size_t nblk = (size_t)((Wq + kGTX - 1) / kGTX) * ((Hq + kGTY - 1) / kGTY);
-    return nblk * (9 * kWidth * kWidth + kWidth);
+    const size_t nchunks = ((size_t)Hq * Wq + kWgChunk - 1) / kWgChunk;
+    return nchunks * (9 * kWidth * kWidth + kWidth);
+}
+
+template <int CIN, int COUT>
+cudaError_t launch_wgrad_t(const __nv_bfloat16* X, const __nv_bfloat16* G, int Hq, int Wq, float* partial, int* err,
+                           int grid, cudaStream_t stream)
+{
+    const size_t smem = WgShape<CIN, COUT>::SMEM;
+    cudaError_t e = fbs::raise_smem_limit(wgrad_tc_kernel<CIN, COUT>, (int)smem);
+    if (e != cudaSuccess) return e;
+    fbs::note_launch();
+    wgrad_tc_kernel<CIN, COUT><<<grid, kWgThreads, smem, stream>>>(X, G, Hq, Wq, partial, err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_wgrad(int l, const __nv_bfloat16* X, const __nv_bfloat16* G, int Hq, int Wq, float* partial,
-                         float* grad, cudaStream_t stream)
+                         float* grad, int* err, int num_sms, cudaStream_t stream)
 {
-    dim3 grid((Wq + kGTX - 1) / kGTX, (Hq + kGTY - 1) / kGTY);
-    const int nblk = grid.x * grid.y;
+    const int nchunks = (Hq * Wq + kWgChunk - 1) / kWgChunk;
+    // every CTA takes at least one chunk, so every partial is written
+    const int grid = nchunks < 2 * num_sms ? nchunks : 2 * num_sms;
     const int cinp = cin_pad(l), coutp = cout_pad(l);
-    fbs::note_launch();
+    cudaError_t e;
     if (cinp == 8 && coutp == 32)
-        wgrad_kernel<8, 32><<<grid, 9 * 8, 0, stream>>>(X, G, Hq, Wq, partial);
+        e = launch_wgrad_t<8, 32>(X, G, Hq, Wq, partial, err, grid, stream);
     else if (cinp == 32 && coutp == 32)
-        wgrad_kernel<32, 32><<<grid, 9 * 32, 0, stream>>>(X, G, Hq, Wq, partial);
+        e = launch_wgrad_t<32, 32>(X, G, Hq, Wq, partial, err, grid, stream);
     else if (cinp == 32 && coutp == 8)
-        wgrad_kernel<32, 8><<<grid, 9 * 32, 0, stream>>>(X, G, Hq, Wq, partial);
+        e = launch_wgrad_t<32, 8>(X, G, Hq, Wq, partial, err, grid, stream);
     else
         return cudaErrorInvalidValue;
-    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int stride = 9 * cinp * coutp + coutp;
     fbs::note_launch();
-    wgrad_reduce_kernel<<<(stride + 255) / 256, 256, 0, stream>>>(partial, nblk, stride, cinp, coutp, cin(l), cout(l),
+    wgrad_reduce_kernel<<<(stride + 255) / 256, 256, 0, stream>>>(partial, grid, stride, cinp, coutp, cin(l), cout(l),
                                                                    grad + param_offset(l));
     return cudaGetLastError();
 }

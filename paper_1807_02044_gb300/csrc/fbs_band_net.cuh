@@ -65,9 +65,10 @@ cudaError_t launch_conv3x3(int cin_ch, int n, const __nv_bfloat16* in, const __n
                            int flip, int mode, int* err, int num_sms, cudaStream_t stream);
 // Weight and bias gradient of layer l: sum over pixels of X[p + offset] G[p],
 // X [P][cin_pad(l)], G [P][cout_pad(l)]; written into grad (flat vector).
+// On the tensor cores; err: device word set on a timeout.
 size_t wgrad_partial_floats(int Hq, int Wq);
 cudaError_t launch_wgrad(int l, const __nv_bfloat16* X, const __nv_bfloat16* G, int Hq, int Wq, float* partial,
-                         float* grad, cudaStream_t stream);
+                         float* grad, int* err, int num_sms, cudaStream_t stream);
 // Loss of readings B6 and its gradient G6 [P][kOutPad] (BF16); per-block loss
 // sums in loss_partial (loss_blocks(P) floats), reduced into *loss (sum / P).
 int loss_blocks(int P);
