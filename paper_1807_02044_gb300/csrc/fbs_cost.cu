@@ -25,9 +25,9 @@
 //     contiguous, so the tensor-core kernel's TMA reads contiguous blocks that
 //     land as K-major core matrices; columns x >= W of the last block are 0.
 //     One launch computes the statistics of the rows it stages (a CTA covers
-//     4 output rows and stages their 6 grey rows once), the costs (8 pixels x
-//     8 disparities per thread), the pad rows D .. Dp-1 and the left image's
-//     packed guide.
+//     up to 4 output rows and stages their grey rows once), the costs (8
+//     pixels x 8 disparities per thread), the pad rows D .. Dp-1 and the left
+//     image's packed guide.
 // Both round the normalisation the same way (ncc_cost), so the 16-bit volume
 // equals the FP32 volume rounded to 16 bits.
 //
@@ -472,25 +472,26 @@ __host__ __device__ inline int xb_blocks_per_cta(int D)
 // both when lanes write their 8 rows and when the warp reads 32 consecutive rows).
 constexpr int kXbWarpRows = 256 + 32;
 
-// Output rows per CTA: the CTA stages grey rows y0-1 .. y0+kXbRows once for all
-// of them (kXbRows + 2 rows of each image instead of 3 per output row).
-constexpr int kXbRows = 4;
+// Output rows per CTA (1, 2 or 4, chosen at launch): the CTA stages grey rows
+// y0-1 .. y0+rows once for all of them (rows + 2 rows of each image instead of
+// 3 per output row).
+constexpr int kXbMaxRows = 4;
 
-__host__ __device__ inline size_t cost_xb_stage_ints(int mode, int D)
+__host__ __device__ inline size_t cost_xb_stage_ints(int mode, int D, int rows)
 {
     const int npx = 8 * xb_blocks_per_cta(D);
     const int Ll = skew_len(npx + 2), Lr = skew_len(npx + D + 9), Lp = skew_len(npx);
     // NCC: grey rows of both images, then per output row the left and right
     // block statistics; TAD: per output row the packed pixels of both images
-    const size_t n = mode == 0 ? (size_t)((kXbRows + 2) * (Ll + Lr) + kXbRows * (2 * Lp + 2 * Lr))
-                               : (size_t)kXbRows * (Lp + Lr);
+    const size_t n = mode == 0 ? (size_t)((rows + 2) * (Ll + Lr) + rows * (2 * Lp + 2 * Lr))
+                               : (size_t)rows * (Lp + Lr);
     return (n + 3) & ~(size_t)3;   // the output buffers that follow are 16-byte aligned
 }
 
 template <int MODE, typename T>
 __global__ void __launch_bounds__(kXbThreads, 2)
 cost_xb_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int H, int W, int C, int D, float tau,
-               T* __restrict__ out, uint2* __restrict__ rgbx)
+               T* __restrict__ out, uint2* __restrict__ rgbx, int rows)
 {
     extern __shared__ int sm_xb[];
     // let a programmatically launched successor (the tensor-core aggregation)
@@ -502,8 +503,8 @@ cost_xb_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int
     const int xbc = xb_blocks_per_cta(D);
     const int nxb = (W + 7) >> 3;
     const int xb0 = blockIdx.x * xbc;
-    const int y0 = blockIdx.y * kXbRows;
-    const int nrows = min(kXbRows, H - y0);
+    const int y0 = blockIdx.y * rows;
+    const int nrows = min(rows, H - y0);
     const int x0 = xb0 * 8;
     const int npx = xbc * 8;
     const int nl = npx + 2;            // left grey columns x0-1 .. x0+npx
@@ -513,14 +514,14 @@ cost_xb_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int
     const int rb = x0 - D - 8;
     const int Ll = skew_len(nl), Lr = skew_len(nr), Lp = skew_len(npx);
 
-    int* gl = sm_xb;                             // [kXbRows + 2][Ll]: grey rows y0-1 ..
-    int* gr = gl + (kXbRows + 2) * Ll;           // [kXbRows + 2][Lr]
-    int* sl = gr + (kXbRows + 2) * Lr;           // [kXbRows][Lp]
-    float* rl = (float*)(sl + kXbRows * Lp);     // [kXbRows][Lp]
-    int* sr = (int*)(rl + kXbRows * Lp);         // [kXbRows][Lr]
-    float* rr = (float*)(sr + kXbRows * Lr);     // [kXbRows][Lr]
-    uint32_t* pl = (uint32_t*)sm_xb;             // TAD: left pixels [kXbRows][Lp]
-    uint32_t* pr = pl + kXbRows * Lp;            // TAD: right pixels [kXbRows][Lr], origin rb
+    int* gl = sm_xb;                             // [rows + 2][Ll]: grey rows y0-1 ..
+    int* gr = gl + (rows + 2) * Ll;              // [rows + 2][Lr]
+    int* sl = gr + (rows + 2) * Lr;              // [rows][Lp]
+    float* rl = (float*)(sl + rows * Lp);        // [rows][Lp]
+    int* sr = (int*)(rl + rows * Lp);            // [rows][Lr]
+    float* rr = (float*)(sr + rows * Lr);        // [rows][Lr]
+    uint32_t* pl = (uint32_t*)sm_xb;             // TAD: left pixels [rows][Lp]
+    uint32_t* pr = pl + rows * Lp;               // TAD: right pixels [rows][Lr], origin rb
 
     // staging: grey values (channel sums) of rows y0-1 .. y0+nrows at clamped
     // columns, then for each output row the statistics S, 1/sqrt(9Q - S^2) of
@@ -606,7 +607,7 @@ cost_xb_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int
     const int xbase = x0 + xl;
     const int lane = tid & 31;
     constexpr bool kBf16 = std::is_same<T, __nv_bfloat16>::value;
-    uint4* wbuf = (uint4*)(sm_xb + cost_xb_stage_ints(MODE, D)) + (size_t)(tid >> 5) * kXbWarpRows;
+    uint4* wbuf = (uint4*)(sm_xb + cost_xb_stage_ints(MODE, D, rows)) + (size_t)(tid >> 5) * kXbWarpRows;
     uint4* mine = wbuf + 9 * lane;     // rows 8*lane + s at 9*lane + s
 
     for (int k = 0; k < nrows; ++k) {
@@ -767,10 +768,10 @@ cost_xb_kernel(const uint8_t* __restrict__ L, const uint8_t* __restrict__ R, int
     }
 }
 
-size_t cost_xb_smem_bytes(int mode, int D)
+size_t cost_xb_smem_bytes(int mode, int D, int rows)
 {
     const int nwarps = (xb_blocks_per_cta(D) * ((D + 7) / 8) + 31) / 32;
-    return sizeof(int) * cost_xb_stage_ints(mode, D) + (size_t)nwarps * kXbWarpRows * 16;
+    return sizeof(int) * cost_xb_stage_ints(mode, D, rows) + (size_t)nwarps * kXbWarpRows * 16;
 }
 
 template <int MODE, typename T>
@@ -779,14 +780,23 @@ cudaError_t launch_cost_xb(const CostScratch& sc, const uint8_t* left, const uin
 {
     const int ndg = (D + 7) / 8;
     const int xbc = xb_blocks_per_cta(D);
-    const size_t smem = cost_xb_smem_bytes(MODE, D);
-    cudaError_t e = fbs::raise_smem_limit(cost_xb_kernel<MODE, T>, (int)smem);
-    if (e != cudaSuccess) return e;
     const int nxb = (W + 7) / 8;
-    dim3 grid((nxb + xbc - 1) / xbc, (H + kXbRows - 1) / kXbRows);
+    const int gx = (nxb + xbc - 1) / xbc;
+    // the most rows per CTA that still leave about four CTAs per SM (small
+    // images need the CTAs more than the shared staging)
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    int rows = kXbMaxRows;
+    while (rows > 1 && (long long)gx * ((H + rows - 1) / rows) < 4LL * sms) rows /= 2;
+    const size_t smem = cost_xb_smem_bytes(MODE, D, rows);
+    e = fbs::raise_smem_limit(cost_xb_kernel<MODE, T>, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(gx, (H + rows - 1) / rows);
     fbs::note_launch();
     const int nthr = (xbc * ndg + 31) / 32 * 32;   // whole warps (the write-out shuffles need all lanes)
-    cost_xb_kernel<MODE, T><<<grid, nthr, smem, stream>>>(left, right, H, W, C, D, tau, out, sc.rgbx);
+    cost_xb_kernel<MODE, T><<<grid, nthr, smem, stream>>>(left, right, H, W, C, D, tau, out, sc.rgbx, rows);
     return cudaGetLastError();
 }
 
