@@ -217,7 +217,7 @@ typedef struct {
  *   fbs_compute_disparity) in one graph of 1, 2 or 4 concurrent branches.
  *   Every pair needs D <= 256 and radius <= 24 (FBS_ERR_UNSUPPORTED
  *   otherwise).  Scratch: every pair's 16-bit volume at once (sum of
- *   H*ceil(W/8)*8*Dp*2 bytes, Dp = round_up(D,16) (+16 when that stays <= 256),
+ *   H*ceil(W/8)*8*Dp*2 bytes, Dp = round_up(D,16) + 16,
  *   plus the packed guide).
  *   A branched graph holds the pairs' addresses: a new set of buffers
  *   captures a new graph (the context keeps up to 32).

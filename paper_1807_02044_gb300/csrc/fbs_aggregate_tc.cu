@@ -49,26 +49,26 @@ using namespace tca;
 
 struct TcParams {
     int H, W, C, D;
-    int N;          // round_up(D, 16): disparity rows the TMA box loads
-    int Nb;         // rows of a B stage: N, plus 16 normaliser rows when they share the MMA
-    int ones_sep;   // normaliser by a separate N=16 MMA (when N + 16 > 256)
+    int N;          // round_up(D, 16): disparity rows
+    int Nb;         // rows of a B stage: N, plus 16 normaliser rows (the ones row and 15 zero rows)
+    int split;      // Nb > 256: two MMAs per K-step, B rows 0..127 and 128..Nb-1
     int rho, rho8, KW, NH, ntx, ntiles;
     int R;          // window rows per pipeline stage
     int S;          // pipeline stages (weights and cost rows share the stage index)
     int nacc;       // accumulator buffers in TMEM (2 = epilogue overlaps the next tile)
     uint32_t acc_stride, den_col, tmem_cols;
     float neg_ks, neg_kr;
-    uint32_t idesc, idesc16;
+    uint32_t idesc, idesc2;   // the (first) MMA's instruction descriptor; the second MMA's when split
     long long wait_cycles;   // limit of one pipeline wait (on another role's progress)
 };
 
 struct TcSmem {
-    size_t a_off, b_off, ones_off, g_off, bar_off, misc_off, sy_off, total;
+    size_t a_off, b_off, g_off, bar_off, misc_off, sy_off, total;
 };
 
 // Per stage: R window rows of weights (A, (KW/8) x kALbo bytes each) and R
 // rows of costs (B, (KW/8) x Nb x 16 bytes each).
-__host__ __device__ inline TcSmem tc_smem_layout(int KW, int Nb, int NH, int R, int S, bool ones_sep)
+__host__ __device__ inline TcSmem tc_smem_layout(int KW, int Nb, int NH, int R, int S)
 {
     TcSmem s;
     size_t o = 0;
@@ -76,8 +76,6 @@ __host__ __device__ inline TcSmem tc_smem_layout(int KW, int Nb, int NH, int R, 
     o += (size_t)S * R * (KW / 8) * kALbo;
     s.b_off = o;
     o += (size_t)S * R * (KW / 8) * Nb * 16;
-    s.ones_off = o;
-    o += ones_sep ? (size_t)(KW / 8) * 16 * 16 : 0;
     o = (o + 127) & ~(size_t)127;
     s.g_off = o;
     o += (size_t)2 * NH * KW * 8;
@@ -136,8 +134,7 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
     // align by an offset from the __shared__ array itself (not an integer round
     // trip), so the compiler keeps every operand access a 32-bit shared one
     uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    const bool ones_sep = p.ones_sep != 0;
-    const TcSmem L = tc_smem_layout(p.KW, p.Nb, p.NH, p.R, p.S, ones_sep);
+    const TcSmem L = tc_smem_layout(p.KW, p.Nb, p.NH, p.R, p.S);
     uint8_t* a_base = sm + L.a_off;
     uint8_t* b_base = sm + L.b_off;
     uint2* gtile = (uint2*)(sm + L.g_off);   // [2][NH][KW] of (RGBX, |colour|^2)
@@ -183,18 +180,6 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
         sytab[i] = f2_pack(sy, sy);
     }
     for (int i = tid; i < (int)(S * a_stage / 16); i += kThreads) ((uint4*)a_base)[i] = make_uint4(0, 0, 0, 0);
-    {
-        // with D + 16 > 256 the normaliser is a separate N=16 MMA against this
-        // block (row 0 all ones, rows 1..15 zero); otherwise the ones row comes
-        // with the cost volume (see launch_cost_build_xblock16)
-        const uint16_t one = BF16 ? (uint16_t)0x3F80 : (uint16_t)0x3C00;
-        if (ones_sep) {
-            for (int i = tid; i < (KW / 8) * 16 * 8; i += kThreads) {
-                const int row = (i >> 3) & 15;
-                ((uint16_t*)(sm + L.ones_off))[i] = row == 0 ? one : (uint16_t)0;
-            }
-        }
-    }
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -426,7 +411,6 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
             // byte offset >> 4 to the 14-bit start-address field
             const uint64_t a_desc0 = sdesc(smem_u32(a_base), kALbo, 128);
             const uint64_t b_desc0 = sdesc(smem_u32(b_base), lbo_b, 128);
-            const uint64_t o_desc0 = sdesc(smem_u32(sm + L.ones_off), 256, 128);
             bool stop = false;
             for (TileWalk tw(p.ntx); tw.tile < p.ntiles && !stop; tw.next(), ++t) {
                 const uint32_t ab = p.nacc == 2 ? (t & 1) : 0, u = p.nacc == 2 ? (t >> 1) : t;
@@ -454,13 +438,13 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                     // steps of 2 core-matrix columns in both operands
                     uint64_t ad = a_desc0 + ((s * a_stage) >> 4), bd = b_desc0 + ((s * b_stage) >> 4);
                     const int nk = nr * (KW / 16);
-                    if (!ones_sep) {
-                        // the issuing thread shares its scheduler with five busy
-                        // warps: few instructions per MMA (the 14-bit address
-                        // fields never carry into the descriptors' high words)
-                        const uint64_t ahi = ad & 0xffffffff00000000ull, bhi = bd & 0xffffffff00000000ull;
-                        uint32_t alo = (uint32_t)ad, blo = (uint32_t)bd;
-                        const uint32_t astep = (2 * kALbo) >> 4, bstep = (2 * lbo_b) >> 4;
+                    // the 14-bit address fields never carry into the descriptors'
+                    // high words: few instructions per MMA for the issuing thread,
+                    // which shares its scheduler with five busy warps
+                    const uint64_t ahi = ad & 0xffffffff00000000ull, bhi = bd & 0xffffffff00000000ull;
+                    uint32_t alo = (uint32_t)ad, blo = (uint32_t)bd;
+                    const uint32_t astep = (2 * kALbo) >> 4, bstep = (2 * lbo_b) >> 4;
+                    if (!p.split) {
                         umma_f16(dacc, ahi | alo, bhi | blo, p.idesc, accumulate);
                         accumulate = 1;
 #pragma unroll 4
@@ -470,13 +454,17 @@ aggregate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_const
                             umma_f16(dacc, ahi | alo, bhi | blo, p.idesc, 1u);
                         }
                     } else {
+                        // B rows 0..127 into accumulator columns 0..127, rows
+                        // 128..Nb-1 (with the ones row) into columns 128..Nb-1:
+                        // an MMA of N <= 128 costs the same ~88 cycles as one of
+                        // N = 16, so 128 + 144 beats 256 + a separate 16
+                        const uint32_t b2 = (128 * 16) >> 4;
                         for (int k = 0; k < nk; ++k) {
-                            const int j = k % (KW / 16);
-                            umma_f16(dacc, ad, bd, p.idesc, accumulate);
-                            umma_f16(dacc + p.den_col, ad, o_desc0 + ((j * 2 * 256) >> 4), p.idesc16, accumulate);
+                            umma_f16(dacc, ahi | alo, bhi | blo, p.idesc, accumulate);
+                            umma_f16(dacc + 128, ahi | alo, bhi | (blo + b2), p.idesc2, accumulate);
                             accumulate = 1;
-                            ad += (2 * kALbo) >> 4;
-                            bd += (2 * lbo_b) >> 4;
+                            alo += astep;
+                            blo += bstep;
                         }
                     }
                     umma_commit(empty0 + 8 * s);
@@ -593,8 +581,8 @@ bool tc_plan(int H, int W, int C, int D, int radius, float sigma_s, float sigma_
     p.C = C;
     p.D = D;
     p.N = round_up(D, 16);
-    p.ones_sep = p.N + 16 > 256 ? 1 : 0;
-    p.Nb = p.ones_sep ? p.N : p.N + 16;
+    p.Nb = tc_block_rows(D);
+    p.split = p.Nb > 256 ? 1 : 0;
     p.rho = radius;
     p.rho8 = round_up(radius, 8);
     p.KW = round_up(16 + p.rho8 + radius, 16);
@@ -611,15 +599,15 @@ bool tc_plan(int H, int W, int C, int D, int radius, float sigma_s, float sigma_
     uint32_t cols = 32;
     while (cols < p.nacc * total_n) cols <<= 1;
     p.tmem_cols = cols;
-    p.idesc = tc_idesc(bf16, p.ones_sep ? p.N : p.Nb);
-    p.idesc16 = tc_idesc(bf16, 16);
+    p.idesc = tc_idesc(bf16, p.split ? 128 : p.Nb);
+    p.idesc2 = tc_idesc(bf16, p.split ? p.Nb - 128 : 16);
     // R window rows per stage and S stages: the largest R (<= kMaxR) with at least
     // 2 stages in 227 KB, then as many stages (<= 6) as fit.  Fewer, larger
     // stages per tile measured faster than deeper pipelines of small stages:
     // each stage costs the producers a wait, a proxy fence and an arrival
     for (p.R = max_rows < 1 || max_rows > kMaxR ? kMaxR : max_rows; p.R >= 1; --p.R) {
         for (p.S = 6; p.S >= 2; --p.S) {
-            L = tc_smem_layout(p.KW, p.Nb, p.NH, p.R, p.S, p.ones_sep != 0);
+            L = tc_smem_layout(p.KW, p.Nb, p.NH, p.R, p.S);
             if (L.total <= 227 * 1024) return true;
         }
     }

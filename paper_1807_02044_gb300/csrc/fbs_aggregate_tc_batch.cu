@@ -44,27 +44,27 @@ using namespace tca;
 struct TcBatchPair {   // 128-byte aligned, as its tensor maps
     CUtensorMap tmap;       // 16-bit x-blocked cost volume; box 128 x Nb/16 x KW/8 x R
     CUtensorMap gmap;       // packed guide; box KW x NH
-    int H, W, D, N, Nb, ones_sep, rho, rho8, KW, NH, ntx, R, variant;
+    int H, W, D, N, Nb, split, rho, rho8, KW, NH, ntx, R, variant;   // split: Nb > 256, two MMAs per K-step
     int item0, items;       // the member's tiles: work items item0 .. item0 + items - 1
     float neg_ks, neg_kr;
-    uint32_t idesc, idesc16;
+    uint32_t idesc, idesc2;   // the (first) MMA's instruction descriptor; the second one's when split
     int32_t* disp_int;
     float* disp_sub;
 };
 
 struct TcBatchArgs {
     const TcBatchPair* pairs;
-    int npairs, nitems, S, nacc, kw_max, nh_max, any_ones;
+    int npairs, nitems, S, nacc, kw_max, nh_max;
     uint32_t a_stage, b_stage, acc_stride, tmem_cols;
     long long wait_cycles;
 };
 
 struct BatchSmem {
-    size_t a_off, b_off, ones_off, g_off, bar_off, misc_off, own_off, total;
+    size_t a_off, b_off, g_off, bar_off, misc_off, own_off, total;
 };
 
 __host__ __device__ inline BatchSmem batch_smem_layout(int S, uint32_t a_stage, uint32_t b_stage, int kw_max,
-                                                       int nh_max, bool any_ones)
+                                                       int nh_max)
 {
     BatchSmem s;
     size_t o = 0;
@@ -72,8 +72,6 @@ __host__ __device__ inline BatchSmem batch_smem_layout(int S, uint32_t a_stage, 
     o += (size_t)S * a_stage;
     s.b_off = o;
     o += (size_t)S * b_stage;
-    s.ones_off = o;
-    o += any_ones ? (size_t)(kw_max / 8) * 16 * 16 : 0;
     o = (o + 127) & ~(size_t)127;
     s.g_off = o;
     o += (size_t)2 * nh_max * kw_max * 8;
@@ -119,8 +117,8 @@ __device__ __forceinline__ int member_of(const TcBatchPair* pairs, int npairs, i
 // the table once per member (not once per tile).
 struct MemberView {
     const TcBatchPair* p;
-    int index, item0, end, ntx, H, W, D, N, Nb, ones_sep, rho, rho8, KW, NH, R;
-    uint32_t idesc, idesc16;
+    int index, item0, end, ntx, H, W, D, N, Nb, split, rho, rho8, KW, NH, R;
+    uint32_t idesc, idesc2;
     int32_t* disp_int;
     float* disp_sub;
 };
@@ -137,14 +135,14 @@ __device__ __forceinline__ void view_member(MemberView& v, const TcBatchPair* pa
     v.D = P.D;
     v.N = P.N;
     v.Nb = P.Nb;
-    v.ones_sep = P.ones_sep;
+    v.split = P.split;
     v.rho = P.rho;
     v.rho8 = P.rho8;
     v.KW = P.KW;
     v.NH = P.NH;
     v.R = P.R;
     v.idesc = P.idesc;
-    v.idesc16 = P.idesc16;
+    v.idesc2 = P.idesc2;
     v.disp_int = P.disp_int;
     v.disp_sub = P.disp_sub;
 }
@@ -187,7 +185,7 @@ __device__ __forceinline__ ProducerState produce_run(const TcBatchPair* __restri
                                                   const TcBatchArgs* __restrict__ a, int* __restrict__ err)
 {
     uint8_t* sm = batch_smem();
-    const BatchSmem L = batch_smem_layout(a->S, a->a_stage, a->b_stage, a->kw_max, a->nh_max, a->any_ones != 0);
+    const BatchSmem L = batch_smem_layout(a->S, a->a_stage, a->b_stage, a->kw_max, a->nh_max);
     uint8_t* a_base = sm + L.a_off;
     const uint8_t* g_base = sm + L.g_off;
     const int S = a->S;
@@ -325,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 aggregate_tc_batch_kernel(const __grid_constant__ TcBatchArgs a, int* __restrict__ err)
 {
     uint8_t* sm = batch_smem();
-    const BatchSmem L = batch_smem_layout(a.S, a.a_stage, a.b_stage, a.kw_max, a.nh_max, a.any_ones != 0);
+    const BatchSmem L = batch_smem_layout(a.S, a.a_stage, a.b_stage, a.kw_max, a.nh_max);
     uint8_t* a_base = sm + L.a_off;
     uint8_t* b_base = sm + L.b_off;
     uint8_t* g_base = sm + L.g_off;
@@ -361,14 +359,6 @@ aggregate_tc_batch_kernel(const __grid_constant__ TcBatchArgs a, int* __restrict
     }
     if (warp == 0) tmem_alloc(smem_u32(&misc[0]), a.tmem_cols);
     if (tid < kProducerWarps * 8) owners[tid] = -1;   // no slot holds a member's layout yet
-    if (a.any_ones) {
-        // the normaliser block of members with D + 16 > 256: row 0 all ones, rows 1..15 zero
-        const uint16_t one = BF16 ? (uint16_t)0x3F80 : (uint16_t)0x3C00;
-        for (int i = tid; i < (a.kw_max / 8) * 16 * 8; i += kThreads) {
-            const int row = (i >> 3) & 15;
-            ((uint16_t*)(sm + L.ones_off))[i] = row == 0 ? one : (uint16_t)0;
-        }
-    }
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -496,7 +486,6 @@ aggregate_tc_batch_kernel(const __grid_constant__ TcBatchArgs a, int* __restrict
         if (lane == 0) {
             uint32_t gs = 0, gu = 0, t = 0;
             const uint64_t a_desc0 = sdesc(smem_u32(a_base), kALbo, 128);
-            const uint64_t o_desc0 = sdesc(smem_u32(sm + L.ones_off), 256, 128);
             MemberView P;
             P.end = -1;
             P.index = 0;
@@ -521,8 +510,8 @@ aggregate_tc_batch_kernel(const __grid_constant__ TcBatchArgs a, int* __restrict
                 const int hr_lo = max(0, P.rho - ty0);
                 const int hr_hi = min(P.NH, P.H - ty0 + P.rho);
                 const int ksteps = P.KW / 16;
-                const uint32_t idesc = P.idesc, idesc16 = P.idesc16, den = (uint32_t)P.N;
-                const bool ones_sep = P.ones_sep != 0;
+                const uint32_t idesc = P.idesc, idesc2 = P.idesc2;
+                const bool split = P.split != 0;
                 uint32_t accumulate = 0;
                 for (int h0 = hr_lo; h0 < hr_hi; h0 += P.R) {
                     const int nr = min(P.R, hr_hi - h0);
@@ -537,11 +526,10 @@ aggregate_tc_batch_kernel(const __grid_constant__ TcBatchArgs a, int* __restrict
                     uint64_t ad = a_desc0 + ((s * a.a_stage) >> 4), bd = b_desc0 + ((s * a.b_stage) >> 4);
                     const int nk = nr * ksteps;
                     for (int k = 0; k < nk; ++k) {
+                        // split: B rows 0..127 into columns 0..127, rows 128..Nb-1 (with
+                        // the ones row) into columns 128..Nb-1
                         umma_f16(dacc, ad, bd, idesc, accumulate);
-                        if (ones_sep) {
-                            const int j = k % ksteps;
-                            umma_f16(dacc + den, ad, o_desc0 + ((j * 2 * 256) >> 4), idesc16, accumulate);
-                        }
+                        if (split) umma_f16(dacc + 128, ad, bd + ((128 * 16) >> 4), idesc2, accumulate);
                         accumulate = 1;
                         ad += (2 * kALbo) >> 4;
                         bd += (2 * lbo_b) >> 4;
@@ -579,7 +567,7 @@ cudaError_t tc_batch_prepare(int n, const TcBatchMember* m, bool bf16, void* hos
     if (!enc) return cudaErrorNotSupported;
     if (n < 1 || !m || !host_table || !out) return cudaErrorInvalidValue;
     struct Geo {
-        int N, Nb, ones, rho8, KW, NH, ntx, ntiles, variant;
+        int N, Nb, split, rho8, KW, NH, ntx, ntiles, variant;
         uint32_t a_row, b_row;
         double tile_work;
     };
@@ -589,8 +577,8 @@ cudaError_t tc_batch_prepare(int n, const TcBatchMember* m, bool bf16, void* hos
         if (q.D < 1 || q.D > 256 || q.radius < 0 || q.radius > 24 || q.H < 1 || q.W < 1) return cudaErrorInvalidValue;
         Geo& e = g[i];
         e.N = round_up(q.D, 16);
-        e.ones = e.N + 16 > 256 ? 1 : 0;
-        e.Nb = e.ones ? e.N : e.N + 16;
+        e.Nb = tc_block_rows(q.D);
+        e.split = e.Nb > 256 ? 1 : 0;
         e.rho8 = round_up(q.radius, 8);
         e.KW = round_up(16 + e.rho8 + q.radius, 16);
         e.NH = kTH + 2 * q.radius;
@@ -619,13 +607,12 @@ cudaError_t tc_batch_prepare(int n, const TcBatchMember* m, bool bf16, void* hos
         // the group's stage layout: the largest R (<= kMaxR) whose stages of R
         // rows of its largest member fit at least twice in 227 KB, then as many
         // stages (<= 6) as fit
-        int kw_max = 0, nh_max = 0, any_ones = 0;
+        int kw_max = 0, nh_max = 0;
         uint32_t a_max = 0, b_max = 0, acc_stride = 0;
         for (int k = k0; k < k1; ++k) {
             const Geo& e = g[order[k]];
             kw_max = std::max(kw_max, e.KW);
             nh_max = std::max(nh_max, e.NH);
-            any_ones |= e.ones;
             a_max = std::max(a_max, e.a_row);
             b_max = std::max(b_max, e.b_row);
             acc_stride = std::max(acc_stride, (uint32_t)e.N + 16);
@@ -634,7 +621,7 @@ cudaError_t tc_batch_prepare(int n, const TcBatchMember* m, bool bf16, void* hos
         BatchSmem L{};
         for (int r = kMaxR; r >= 1 && !R; --r)
             for (int s = 6; s >= 2; --s) {
-                L = batch_smem_layout(s, (uint32_t)r * a_max, (uint32_t)r * b_max, kw_max, nh_max, any_ones != 0);
+                L = batch_smem_layout(s, (uint32_t)r * a_max, (uint32_t)r * b_max, kw_max, nh_max);
                 if (L.total <= 227 * 1024) {
                     R = r;
                     S = s;
@@ -653,7 +640,7 @@ cudaError_t tc_batch_prepare(int n, const TcBatchMember* m, bool bf16, void* hos
             b.D = q.D;
             b.N = e.N;
             b.Nb = e.Nb;
-            b.ones_sep = e.ones;
+            b.split = e.split;
             b.rho = q.radius;
             b.rho8 = e.rho8;
             b.KW = e.KW;
@@ -667,8 +654,8 @@ cudaError_t tc_batch_prepare(int n, const TcBatchMember* m, bool bf16, void* hos
             items += e.ntiles;
             b.neg_ks = (float)(-log2e / ((double)q.sigma_s * q.sigma_s));
             b.neg_kr = (float)(-log2e / ((double)q.sigma_r * q.sigma_r));
-            b.idesc = tc_idesc(bf16, e.ones ? e.N : e.Nb);
-            b.idesc16 = tc_idesc(bf16, 16);
+            b.idesc = tc_idesc(bf16, e.split ? 128 : e.Nb);
+            b.idesc2 = tc_idesc(bf16, e.split ? e.Nb - 128 : 16);
             b.disp_int = q.disp_int;
             b.disp_sub = q.disp_sub;
             if (encode_cost_map(enc, &b.tmap, q.cost, q.H, q.W, e.Nb, e.KW, b.R, bf16) != CUDA_SUCCESS ||
@@ -685,7 +672,6 @@ cudaError_t tc_batch_prepare(int n, const TcBatchMember* m, bool bf16, void* hos
         G.nacc = 2 * acc_stride <= 512 ? 2 : 1;
         G.kw_max = kw_max;
         G.nh_max = nh_max;
-        G.any_ones = any_ones;
         G.a_stage = a_stage;
         G.b_stage = b_stage;
         G.acc_stride = acc_stride;
@@ -738,7 +724,6 @@ cudaError_t launch_aggregate_tc_batch(const void* dev_table, const TcBatchLaunch
         a.nacc = G.nacc;
         a.kw_max = G.kw_max;
         a.nh_max = G.nh_max;
-        a.any_ones = G.any_ones;
         a.a_stage = G.a_stage;
         a.b_stage = G.b_stage;
         a.acc_stride = G.acc_stride;

@@ -57,18 +57,14 @@ cudaError_t launch_cost_build_lr(const CostScratch& sc, const uint8_t* left, con
                                  cudaStream_t stream);
 
 // 16-bit x-blocked volume cost[((y*ceil(W/8) + x/8)*Dp + d)*8 + x%8] with
-// Dp = tc_block_rows(D) rows per block: d < D the cost, D <= d < round_up(D,16)
-// zero, and (when Dp > round_up(D,16)) row round_up(D,16) all ones followed by
-// zero rows -- the ones row lets the tensor-core product also form the sum of
-// the weights.  Columns x >= W of the last block are 0.  bf16 selects
+// Dp = tc_block_rows(D) = round_up(D,16) + 16 rows per block: d < D the cost,
+// D <= d < round_up(D,16) zero, row round_up(D,16) all ones and the 15 rows
+// after it zero -- the ones row lets the tensor-core product also form the sum
+// of the weights.  Columns x >= W of the last block are 0.  bf16 selects
 // __nv_bfloat16, otherwise __half.  One kernel, which also writes the left
 // image's packed guide to sc.rgbx (required; the statistics planes of sc are
-// not used).  D <= 256.
-__host__ __device__ inline int tc_block_rows(int D)
-{
-    const int n = (D + 15) / 16 * 16;
-    return n + 16 <= 256 ? n + 16 : n;
-}
+// not used).  D <= 256 (Dp <= 272).
+__host__ __device__ inline int tc_block_rows(int D) { return (D + 15) / 16 * 16 + 16; }
 inline size_t xblock16_bytes(int H, int W, int D) { return (size_t)H * ((W + 7) / 8) * tc_block_rows(D) * 8 * 2; }
 cudaError_t launch_cost_build_xblock16(const CostScratch& sc, const uint8_t* left, const uint8_t* right, int H,
                                        int W, int C, int D, int mode, float tau, bool bf16, void* cost,
@@ -114,7 +110,7 @@ struct TcBatchMember {
 };
 struct TcBatchGroup {
     int variant, first, npairs, nitems;    // members first .. first + npairs - 1 of the table
-    int R, S, nacc, kw_max, nh_max, any_ones;
+    int R, S, nacc, kw_max, nh_max;
     uint32_t a_stage, b_stage, acc_stride, tmem_cols;
     size_t smem;
 };
