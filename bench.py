@@ -274,11 +274,11 @@ def _config(p, args, impl):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def _traffic_for(kernel_file, kernel_name):
+def _traffic_for(kernel_file, kernel_name, workload):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of the kernel (else None).  kernel_file is one path
-    or a list of paths (the kernel's .cu and the headers holding its code),
-    hashed in order."""
+    on the current source of the kernel and on this workload (else None).
+    kernel_file is one path or a list of paths (the kernel's .cu and the
+    headers holding its code), hashed in order."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     files = [kernel_file] if isinstance(kernel_file, str) else list(kernel_file)
     try:
@@ -292,7 +292,7 @@ def _traffic_for(kernel_file, kernel_name):
     except (OSError, ValueError):
         return None
     ent = t.get(kernel_name)
-    if not ent or ent.get("source_sha256_16") != h:
+    if not ent or ent.get("source_sha256_16") != h or ent.get("workload") != workload:
         return None
     return ent.get("dram_bytes_per_launch_full_size")
 
@@ -455,7 +455,8 @@ def run_ours(args):
                     "achieved": flops / (agg_launch_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                     "peak_source": f"derived: {sms} SMs (cudaDeviceProp) x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
                                    f"{peaks['sm_max_mhz']:.0f} MHz (max SM clock, {peak_src})",
-                    "traffic": _traffic_for(os.path.join(csrc, "fbs_aggregate_f32.cu"), "aggregate_f32_kernel")}
+                    "traffic": _traffic_for(os.path.join(csrc, "fbs_aggregate_f32.cu"), "aggregate_f32_kernel",
+                                           args.workload)}
     else:
         agg_ms, agg_n = kt["aggregate_tc"]
         agg_launch_ms = agg_ms / max(1, agg_n)
@@ -471,7 +472,7 @@ def run_ours(args):
                     "issued_dense_tflops": issued / (agg_launch_ms * 1e-3) / 1e12,
                     "issued_over_algorithmic": issued / flops,
                     "traffic": _traffic_for([os.path.join(csrc, "fbs_aggregate_tc.cu"), os.path.join(csrc, "tc_aggregate.cuh")],
-                                           "aggregate_tc_kernel")}
+                                           "aggregate_tc_kernel", args.workload)}
     roofline.update({"algorithmic": "2 flop per tap (one multiply-add per window tap per disparity), "
                                     "H*W*D*(2r+1)^2 taps", "avg_launch_ms": agg_launch_ms, "launches": agg_n})
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
@@ -495,7 +496,7 @@ def run_ours(args):
                      "achieved": cost_bytes / (cost_launch_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "avg_launch_ms": cost_launch_ms, "launches": cost_n,
                      "algorithmic": "read both images once, write the cost volume once",
-                     "traffic": _traffic_for(os.path.join(csrc, "fbs_cost.cu"), cost_kernel)}
+                     "traffic": _traffic_for(os.path.join(csrc, "fbs_cost.cu"), cost_kernel, args.workload)}
     roofline_cost["frac"] = roofline_cost["achieved"] / roofline_cost["peak"]
 
     e2e = None
