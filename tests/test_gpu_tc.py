@@ -40,11 +40,12 @@ def _dev(a):
 
 
 @pytest.mark.parametrize("prec", ["bf16", "f16"])
-@pytest.mark.parametrize("H,W,D", [(8, 16, 16), (13, 37, 20), (24, 50, 64)])
+@pytest.mark.parametrize("H,W,D", [(8, 16, 16), (13, 37, 20), (24, 50, 64), (9, 40, 250), (10, 24, 256)])
 def test_radius_zero_returns_the_rounded_cost_exactly(fbs, prec, H, W, D):
     """With radius 0 every pixel's only weight is 1, so the tensor-core product
     must reproduce the 16-bit cost bit for bit: this pins the operand layouts,
-    the TMA box, the instruction descriptor and the accumulator read-out."""
+    the TMA box, the instruction descriptor and the accumulator read-out
+    (D > 240: the two MMAs of N = 128 and N - 128 per K-step)."""
     rng = np.random.default_rng(H * W + D)
     cost = (rng.random((H, W, D)) * 2).astype(np.float32)
     G = rng.integers(0, 256, size=(H, W, 3)).astype(np.uint8)
@@ -56,7 +57,8 @@ def test_radius_zero_returns_the_rounded_cost_exactly(fbs, prec, H, W, D):
 
 
 @pytest.mark.parametrize("prec", ["bf16", "f16"])
-@pytest.mark.parametrize("H,W,C,D,r", [(16, 24, 3, 16, 2), (21, 45, 3, 40, 7), (9, 70, 1, 64, 4), (30, 33, 3, 100, 9)])
+@pytest.mark.parametrize("H,W,C,D,r", [(16, 24, 3, 16, 2), (21, 45, 3, 40, 7), (9, 70, 1, 64, 4), (30, 33, 3, 100, 9),
+                                       (18, 300, 3, 256, 9), (11, 270, 1, 245, 5)])
 def test_tc_aggregation_within_rounding_bound(fbs, oracle_mod, prec, H, W, C, D, r):
     rng = np.random.default_rng(7 * H + W)
     L = rng.integers(0, 256, size=(H, W, C)).astype(np.uint8)
