@@ -523,17 +523,34 @@ aggregate_tc_batch_kernel(const __grid_constant__ TcBatchArgs a, int* __restrict
                         break;
                     }
                     tc_fence_after();
-                    uint64_t ad = a_desc0 + ((s * a.a_stage) >> 4), bd = b_desc0 + ((s * a.b_stage) >> 4);
+                    const uint64_t ad = a_desc0 + ((s * a.a_stage) >> 4), bd = b_desc0 + ((s * a.b_stage) >> 4);
                     const int nk = nr * ksteps;
-                    for (int k = 0; k < nk; ++k) {
-                        // split: B rows 0..127 into columns 0..127, rows 128..Nb-1 (with
-                        // the ones row) into columns 128..Nb-1
-                        umma_f16(dacc, ad, bd, idesc, accumulate);
-                        if (split) umma_f16(dacc + 128, ad, bd + ((128 * 16) >> 4), idesc2, accumulate);
-                        accumulate = 1;
-                        ad += (2 * kALbo) >> 4;
-                        bd += (2 * lbo_b) >> 4;
+                    // the 14-bit address fields never carry into the descriptors'
+                    // high words: few instructions per MMA for the issuing thread
+                    const uint64_t ahi = ad & 0xffffffff00000000ull, bhi = bd & 0xffffffff00000000ull;
+                    uint32_t alo = (uint32_t)ad, blo = (uint32_t)bd;
+                    const uint32_t astep = (2 * kALbo) >> 4, bstep = (2 * lbo_b) >> 4;
+                    if (!split) {
+                        umma_f16(dacc, ahi | alo, bhi | blo, idesc, accumulate);
+#pragma unroll 4
+                        for (int k = 1; k < nk; ++k) {
+                            alo += astep;
+                            blo += bstep;
+                            umma_f16(dacc, ahi | alo, bhi | blo, idesc, 1u);
+                        }
+                    } else {
+                        // B rows 0..127 into columns 0..127, rows 128..Nb-1 (with the
+                        // ones row) into columns 128..Nb-1
+                        const uint32_t b2 = (128 * 16) >> 4;
+                        for (int k = 0; k < nk; ++k) {
+                            umma_f16(dacc, ahi | alo, bhi | blo, idesc, accumulate);
+                            umma_f16(dacc + 128, ahi | alo, bhi | (blo + b2), idesc2, accumulate);
+                            accumulate = 1;
+                            alo += astep;
+                            blo += bstep;
+                        }
                     }
+                    accumulate = 1;
                     umma_commit(empty0 + 8 * s);
                     if (++gs == (uint32_t)S) {
                         gs = 0;
