@@ -6,17 +6,19 @@
 // bilateral weight of Eq. (7)-(8) (zero outside pixel m's window) and
 // C[k][d] the cost volume.  The K dimension is walked one window row at a
 // time: for window row hr the CTA
-//   * loads C[row hr, KW columns][N disparities] with TMA from the 16-bit
-//     x-blocked cost volume [H][W/8][D][8] (B operand, K-major): one box per
-//     block of 8 columns, each a contiguous D x 16-byte block that lands as N/8
-//     core matrices; out-of-image columns/rows and d >= D are zero-filled;
+//   * loads C[row hr, KW columns][Nb rows] with TMA from the 16-bit x-blocked
+//     cost volume [H][W/8][Nb][8] (B operand, K-major; Nb = round_up(D,16) + 16
+//     rows per block: the costs, zero rows up to round_up(D,16), a row of ones
+//     and 15 zero rows): one box per block of 8 columns, each a contiguous
+//     Nb x 16-byte block that lands as Nb/8 core matrices; out-of-image columns
+//     and rows are zero-filled;
 //   * computes the weights of every tile pixel whose window contains row hr
 //     (A operand, K-major, 128 rows x KW columns) into shared memory: each
-//     weight is one exp2 in FP32, rounded to BF16 or FP16; the rounded values
-//     are also summed in FP32 for the normaliser, so numerator and denominator
-//     use the same weights;
-//   * issues KW/16 tcgen05.mma (kind::f16, M=128, N=round_up(D,16), K=16)
-//     accumulating in FP32 in tensor memory.
+//     weight is one exp2 in FP32, rounded to BF16 or FP16;
+//   * issues KW/16 tcgen05.mma (kind::f16, M=128, N=Nb, K=16; two of N = 128
+//     and Nb - 128 when Nb > 256) accumulating in FP32 in tensor memory.  The
+//     ones row makes the same product also sum the rounded weights, so the
+//     numerator and the normaliser use the same weights.
 // A ring of S stages of R rows each (S >= 2) lets the threads produce the
 // next stage while the tensor core works on the current one; TMA runs ahead.  After the last row,
 // four warps read the accumulator rows (one pixel per TMEM lane), normalise
